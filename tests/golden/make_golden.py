@@ -1,0 +1,79 @@
+"""Writes the stored inputs and expected values under tests/golden/.
+
+Calls only the FP64 oracle (``oracle/``) and the seeded input generators; nothing here
+touches the CUDA path. Run from the repository root:
+
+    python tests/golden/make_golden.py chi          # solvent susceptibility tables
+    python tests/golden/make_golden.py solute50_128 # full-size reference (slow, ~minutes)
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+from oracle import rism1d, rism3d, closure as cl   # noqa: E402
+from paper_2403_01039_gb300 import synth           # noqa: E402
+
+
+def make_chi():
+    for name in ("water3", "water_nacl"):
+        s = synth.solvent_sites(name)
+        t0 = time.time()
+        r = rism1d.xrism_solvent(s["q"], s["sigma"], s["eps"], s["rho"], s["species"],
+                                 s["coords"], s["temperature"])
+        np.savez_compressed(os.path.join(HERE, "chi_%s.npz" % name), chi=r["chi"], dk=r["dk"], h=r["h"],
+                            n=2048, dr=0.05, iterations=r["iterations"], rms=r["rms"])
+        print(name, "iterations", r["iterations"], "rms %.2e" % r["rms"], "%.1f s" % (time.time() - t0))
+
+
+def sample_points(n, count, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.integers(0, n, size=(count, 3))
+
+
+def make_full(workload, closures=((cl.KH, 3, "kh"), (cl.PSE, 3, "pse3")), tols=(1e-6, 1e-10)):
+    """Oracle solves of a full-size workload; stores the solution at 1024 seeded grid points
+    (all sites) plus SFEs and iteration counts in tests/golden/<workload>_reference.npz."""
+    w = synth.WORKLOADS[workload]
+    s = synth.solvent_sites(w["solvent"])
+    chi = np.load(os.path.join(HERE, "chi_%s.npz" % w["solvent"]))
+    solv = dict(q=s["q"], sigma=s["sigma"], eps=s["eps"], rho=s["rho"],
+                temperature=s["temperature"], chi=chi["chi"], dk=float(chi["dk"]))
+    grid = synth.cubic_grid(w["n"], w["spacing"])
+    P = rism3d.Problem(solv, grid, synth.workload_solute(workload))
+    pts = sample_points(w["n"], 1024, 7)
+    idx = (slice(None), pts[:, 0], pts[:, 1], pts[:, 2])
+    out = dict(points=pts)
+    for kind, order, tag in closures:
+        for tol in tols:
+            t0 = time.time()
+            sol = rism3d.solve(P, kind, order, tol=tol, mdiis_nvec=w["mdiis_nvec"], verbose=True)
+            sfe_kind = {cl.KH: cl.SFE_KH, cl.HNC: cl.SFE_HNC, cl.PSE: cl.SFE_PSE}[kind]
+            tot, per = rism3d.sfe(P, sol, sfe_kind, order)
+            gf, _ = rism3d.sfe(P, sol, cl.SFE_GF, order)
+            key = "%s_%g" % (tag, tol)
+            out[key + "_iterations"] = sol["iterations"]
+            out[key + "_rms"] = sol["rms"]
+            out[key + "_sfe"] = tot
+            out[key + "_sfe_per_site"] = per
+            out[key + "_sfe_gf"] = gf
+            out[key + "_g"] = sol["g"][idx]
+            out[key + "_c"] = sol["c"][idx]
+            out[key + "_t"] = sol["t"][idx]
+            out[key + "_g_max"] = float(sol["g"].max())
+            print(workload, tag, tol, sol["iterations"], sol["converged"], tot,
+                  "%.0f s" % (time.time() - t0), flush=True)
+            np.savez_compressed(os.path.join(HERE, "%s_reference.npz" % workload), **out)
+
+
+if __name__ == "__main__":
+    what = sys.argv[1] if len(sys.argv) > 1 else "chi"
+    if what == "chi":
+        make_chi()
+    else:
+        make_full(what)
