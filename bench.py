@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark: converged 3D-RISM solves/s (and site-gridpoint-iterations/s) at 1e-6 residual.
+
+Workload (default ``solute50_128``): a seeded 50-atom synthetic solute (10 A sphere, net
+charge 0) in 3-site water + 0.1 M NaCl (5 sites), 128^3 grid at 0.5 A, KH closure, MDIIS
+with 5 vectors, FP32 form, tolerance 1e-6. One step is one whole solve through the C ABI:
+rism3d_set_solute (potential + long-range field + initial guess), rism3d_solve (all
+iterations), rism3d_get_sfe. The solvent susceptibility comes from the library's own 1D
+solver (rism1d_xrism) once, before timing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own copy of the workload (independent solves,
+no collective on the data path: "replicas only"); value = all ranks' solves / the slowest
+rank's time. ``--impl reference`` times the FP64 CPU oracle on the host cores instead
+(rank 0 only), on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "converged 3D-RISM solves/s & site-gridpoint-iters/s at 1e-6 residual"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="solute50_128")
+    p.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    p.add_argument("--closure", default="kh", choices=["kh", "pse", "hnc"])
+    p.add_argument("--pse-order", type=int, default=3)
+    p.add_argument("--tol", type=float, default=1e-6)
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--cpu-sample-iters", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_inputs(name, chi_source):
+    from paper_2403_01039_gb300 import synth
+    w = synth.WORKLOADS[name]
+    sites = synth.solvent_sites(w["solvent"])
+    chi, dk = chi_source(sites)
+    solv = dict(sites)
+    solv.update(chi=chi, dk=dk)
+    grid = synth.cubic_grid(w["n"], w["spacing"])
+    solute = synth.workload_solute(name)
+    return w, solv, grid, solute
+
+
+def product_chi(sites):
+    from paper_2403_01039_gb300 import capi
+    chi, dk, _, _ = capi.xrism(sites)
+    return chi, dk
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            out_dir = os.path.join(ROOT, "gpurun_out")
+            os.makedirs(out_dir, exist_ok=True)
+            self.path = os.path.join(out_dir, "bench_clocks_rank%d.csv" % self.index)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits", "-lms",
+                 "200", "-i", str(self.index)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), samples=len(sm),
+                    reasons=sorted(reasons))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel, workload):
+    """dram bytes per launch from a committed ncu summary, if it was taken on the current
+    kernel source (its hash is stored beside the figure); else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    src = os.path.join(ROOT, "paper_2403_01039_gb300", "csrc", "rism3d_kernels.cu")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("kernels_sha") != h:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(args, w, solv, grid, solute, n_iter_gpu):
+    """The FP64 oracle as it stands, timed on a bounded sample of the same workload: the
+    once-per-solute setup (direct potential sums, long-range fields, X on the grid) plus
+    a few iterations of steps 2-6; extrapolated to a whole solve with the iteration count
+    the oracle needs for this workload (stored reference), else the GPU solve's count."""
+    import numpy as np
+    from oracle import rism3d as orc, closure as cl
+    kinds = {"kh": cl.KH, "pse": cl.PSE, "hnc": cl.HNC}
+    t0 = time.perf_counter()
+    P = orc.Problem(solv, grid, solute)
+    t_setup = time.perf_counter() - t0
+    n = args.cpu_sample_iters
+    t0 = time.perf_counter()
+    orc.solve(P, kinds[args.closure], args.pse_order, tol=1e-300, max_iter=n,
+              mdiis_nvec=w["mdiis_nvec"])
+    t_iter = (time.perf_counter() - t0) / n
+    ref = os.path.join(ROOT, "tests", "golden", "%s_reference.npz" % args.workload)
+    key = "%s_%g_iterations" % ({"kh": "kh", "pse": "pse3"}.get(args.closure, args.closure), args.tol)
+    n_full, src = n_iter_gpu, "the GPU solve's iteration count"
+    if os.path.exists(ref):
+        d = np.load(ref)
+        if key in d:
+            n_full, src = int(d[key]), "the oracle's own iteration count (stored reference)"
+    t_solve = t_setup + n_full * t_iter
+    return dict(value=1.0 / t_solve, unit="solves/s", cores=1, kind="oracle",
+                sample="oracle setup (%.1f s) + %d iterations (%.2f s each) of %s on 1 host "
+                       "thread, extrapolated to %d iterations (%s)"
+                       % (t_setup, n, t_iter, args.workload, n_full, src),
+                site_gridpoint_iters_per_s=len(solv["q"]) * float(np.prod(grid["n"])) / t_iter)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import rism3d as orc, closure as cl
+    import numpy as np
+    from paper_2403_01039_gb300 import synth
+    w = synth.WORKLOADS[args.workload]
+    sites = synth.solvent_sites(w["solvent"])
+    # the oracle's own 1D solver provides its susceptibility
+    from oracle import rism1d
+    r1 = rism1d.xrism_solvent(sites["q"], sites["sigma"], sites["eps"], sites["rho"], sites["species"],
+                              sites["coords"], sites["temperature"])
+    solv = dict(sites)
+    solv.update(chi=r1["chi"], dk=r1["dk"])
+    grid = synth.cubic_grid(w["n"], w["spacing"])
+    solute = synth.workload_solute(args.workload)
+    kinds = {"kh": cl.KH, "pse": cl.PSE, "hnc": cl.HNC}
+    t0 = time.perf_counter()
+    P = orc.Problem(solv, grid, solute)
+    t_setup = time.perf_counter() - t0
+    # one step = one iteration of steps 2-6 (a bounded sample of the solve)
+    orc.solve(P, kinds[args.closure], args.pse_order, tol=1e-300, max_iter=args.warmup,
+              mdiis_nvec=w["mdiis_nvec"])
+    t0 = time.perf_counter()
+    orc.solve(P, kinds[args.closure], args.pse_order, tol=1e-300, max_iter=args.steps,
+              mdiis_nvec=w["mdiis_nvec"])
+    t_iter = (time.perf_counter() - t0) / args.steps
+    ref = os.path.join(ROOT, "tests", "golden", "%s_reference.npz" % args.workload)
+    key = "%s_%g_iterations" % ({"kh": "kh", "pse": "pse3"}.get(args.closure, args.closure), args.tol)
+    n_full = int(np.load(ref)[key]) if os.path.exists(ref) and key in np.load(ref) else 127
+    value = 1.0 / (t_setup + n_full * t_iter)
+    sample = ("oracle setup %.1f s + %d timed iterations (%.2f s each) on 1 host thread, "
+              "extrapolated to the %d iterations of a converged solve" % (t_setup, args.steps, t_iter, n_full))
+    line = dict(impl="reference", metric=METRIC, value=value, unit="solves/s", n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=t_iter * 1e3, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=args.workload, grid="%d^3 x %.3g A" % (w["n"], w["spacing"]),
+                            sites=len(sites["q"]), atoms=len(solute["q"]), closure=args.closure,
+                            tol=args.tol, mdiis=w["mdiis_nvec"]),
+                site_gridpoint_iters_per_s=len(sites["q"]) * float(np.prod(grid["n"])) / t_iter,
+                cpu_baseline=dict(value=value, unit="solves/s", cores=1, kind="oracle", sample=sample),
+                e2e=dict(value=value, unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2403_01039_gb300 import build, capi
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    w, solv, grid, solute = workload_inputs(args.workload, product_chi)
+    G = int(np.prod(grid["n"]))
+    nv = len(solv["q"])
+    S = capi.Solver(solv, grid, precision=args.precision, mdiis_nvec=w["mdiis_nvec"], timing=True)
+
+    def step():
+        S.set_solute(solute["xyz"], solute["q"], solute["sigma"], solute["eps"])
+        rep = S.solve(args.closure, args.pse_order, args.tol)
+        S.sfe(args.closure, args.pse_order)
+        return rep
+
+    for _ in range(args.warmup):
+        step()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    S.reset_stats()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(S.stream)
+    reps = [step() for _ in range(args.steps)]
+    ev1.record(S.stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    stats = S.stats()
+    iters = sum(r["iterations"] for r in reps)
+    t = torch.tensor([ms / 1e3, float(iters)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        tsum = t.clone()
+        torch.distributed.all_reduce(tsum[1:], op=torch.distributed.ReduceOp.SUM)
+        secs, iters_all = float(tmax[0]), float(tsum[1])
+    else:
+        secs, iters_all = float(t[0]), float(t[1])
+    value = world * args.steps / secs
+    sgi = iters_all * nv * G / secs
+
+    # end to end through the C ABI with host buffers: atoms in from pinned host memory,
+    # g (all sites, FP64) and the SFE back to pinned host memory, every step
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(solute[k], dtype=np.float64)).pin_memory()
+              for k in ("xyz", "q", "sigma", "eps")}
+    g_host = torch.empty(S.field_shape, dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        S.set_solute(pinned["xyz"].numpy(), pinned["q"].numpy(), pinned["sigma"].numpy(),
+                     pinned["eps"].numpy())
+        S.solve(args.closure, args.pse_order, args.tol)
+        S.sfe(args.closure, args.pse_order)
+        S.get("g", out=g_host.numpy())
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * args.e2e_steps / e2e_s if world == 1 else None
+    if world > 1:
+        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        e2e_val = world * args.e2e_steps / float(te[0])
+    h2d = int(len(solute["q"]) * (3 + 3) * 8)
+    d2h = int(nv * G * 8 + nv * 152 * 8)
+
+    # roofline of the dominant kernel (largest share of device time in the timed region)
+    peak, peak_src = measured_peaks()
+    kern = stats["kernels"]
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    kd = kern[dom]
+    per_launch_s = kd["ms"] / 1e3 / max(kd["timed"], 1)
+    bytes_per_launch = kd["bytes"] / max(kd["timed"], 1)
+    achieved = bytes_per_launch / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+    total_ms = sum(k["ms"] for k in kern.values())
+    roofline = dict(bound="hbm", kernel=dom, achieved=achieved, peak=peak, unit="GB/s",
+                    frac=achieved / peak, peak_source=peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+                    traffic=ncu_traffic(dom, args.workload),
+                    algorithmic_bytes_per_launch=bytes_per_launch, avg_launch_ms=per_launch_s * 1e3,
+                    share=kd["ms"] / total_ms if total_ms else None)
+    launches = int(sum(k["launches"] for k in kern.values()))
+    kernels_out = {k: dict(launches=v["launches"], ms_per_launch=(v["ms"] / v["timed"]) if v["timed"] else None,
+                           GBps=(v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] else None,
+                           share=(v["ms"] / total_ms) if total_ms else None)
+                   for k, v in kern.items() if v["launches"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, w, solv, grid, solute, reps[-1]["iterations"])
+
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit="solves/s", n_gpus=world, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=secs * 1e3 / args.steps, higher_is_better=True,
+                    scaling="weak", vs_baseline=None, dtype="f32" if args.precision == 32 else "f64",
+                    data="synthetic",
+                    config=dict(workload=args.workload, grid="%d^3 x %.3g A" % (w["n"], w["spacing"]),
+                                sites=nv, atoms=len(solute["q"]), closure=args.closure, tol=args.tol,
+                                mdiis=w["mdiis_nvec"], parallelism="replicas" if world > 1 else "single",
+                                l2="inputs larger than L2 (working set %.2f GB)" % (S.workspace.numel() / 1e9)),
+                    site_gridpoint_iters_per_s=sgi, iterations_per_solve=iters_all / (world * args.steps),
+                    roofline=roofline, cpu_baseline=cpu,
+                    e2e=dict(value=e2e_val, unit="solves/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+                    gpu_launches=launches, clocks=clk, kernels=kernels_out)
+        print(json.dumps(line), flush=True)
+    S.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * rism3d.h - C ABI of the GB300 3D-RISM solver (RISMiCal, arXiv 2403.01039).
+ *
+ * The library solves the 3D-RISM equation h_g = sum_a c_a * X_ag (Eq. 13) closed by
+ * KH (Eqs. 15-16, read as the Kovalenko-Hirata form), HNC (Eq. 14) or PSE-n, with the
+ * long-range Coulomb split of Eqs. 29-32, by the fixed-point procedure of the
+ * "Numerical procedure" section (steps 1-7) accelerated by MDIIS (Eq. 40), and reports
+ * the solvation free energy (Eqs. 17-18, GF, PSE-n). Every step runs in the library's
+ * own CUDA kernels on one GPU; the host side only validates, marshals and schedules.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units: Angstrom, kcal/mol, elementary charges, Kelvin.
+ * Grid: point (i, j, k) sits at origin + (i dx, j dy, k dz); fields are C-ordered
+ *   [site][i][j][k] with k fastest. Nz must be even; Nx, Ny and Nz/2 must factor into
+ *   2, 3 and 5.
+ * Transform: c~(k) = dV sum_n c(r_n) exp(-i k.(r_n - r0)) on the periodic integer grid
+ *   k_m = 2 pi m / (N d), m in [-N/2, N/2) (the paper does not fix a discrete convention).
+ * Ownership: the library copies every input array during the call; the caller keeps its
+ *   arrays. Outputs go to caller buffers. A context is owned by the library until
+ *   rism3d_destroy.
+ * Errors: every call returns a status; nothing throws across the ABI. After a failure
+ *   rism3d_last_error(ctx) (or rism3d_last_error(NULL) when no context exists) gives a
+ *   one-line message. RISM3D_ENOTCONV and RISM3D_EDIVERGED leave the last iterate readable.
+ * Threads: one context per host thread; every kernel of a context runs on its stream.
+ * Pointers: "host" arrays are ordinary host memory; "device" arrays are device memory of
+ *   the current CUDA device (for example a torch CUDA tensor's data_ptr()).
+ */
+#ifndef RISM3D_PUBLIC_API_H_
+#define RISM3D_PUBLIC_API_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rism3d_ctx rism3d_ctx;
+
+typedef enum {
+    RISM3D_OK = 0,
+    RISM3D_EINVAL = 1,      /* bad argument (size, pointer, non-positive rho or T, ...) */
+    RISM3D_ENOMEM = 2,      /* device allocation failed or workspace too small */
+    RISM3D_ECUDA = 3,       /* a CUDA runtime call failed */
+    RISM3D_ESTATE = 4,      /* call out of order (e.g. solve before set_solute) */
+    RISM3D_ENOTCONV = 5,    /* max_iter reached before the tolerance */
+    RISM3D_EDIVERGED = 6,   /* a non-finite residual appeared */
+    RISM3D_ETIMEOUT = 7,    /* a bounded device wait expired */
+    RISM3D_EUNSUPPORTED = 8 /* grid or option outside what the kernels implement */
+} rism3d_status;
+
+/* Closures: KH (Eqs. 15-16, read g = exp(d) for d <= 0, 1 + d for d > 0), HNC (Eq. 14),
+ * PSE-n (partial series expansion of order n; PSE-1 is KH). PSE-n and HNC are reached by
+ * closure continuation: KH, PSE-2, ..., PSE-n (or KH, HNC), each stage started from the
+ * previous solution and converged to 1e-4 (or the requested tolerance if looser), the last
+ * stage to the requested tolerance. */
+enum { RISM3D_KH = 1, RISM3D_HNC = 2, RISM3D_PSE = 3 };
+
+/* SFE expressions: KH (Eq. 18), HNC (Eq. 17), GF (Gaussian fluctuation), PSE-n. */
+enum { RISM3D_SFE_KH = 1, RISM3D_SFE_HNC = 2, RISM3D_SFE_GF = 3, RISM3D_SFE_PSE = 4 };
+
+/* Fields readable with rism3d_get. G, H = g - 1 and C = h - t come from the closure of the
+ * current iterate t; U is beta*u (Eq. 22); PHI is the shared long-range field
+ * phi(r) = 332.0637 sum_a q_a (1 - exp(-r_a)) / r_a so that f_g = beta q_g phi (Eq. 29);
+ * R is the residual t' - t of the last iteration (Eq. 33). */
+enum { RISM3D_G = 1, RISM3D_C = 2, RISM3D_H = 3, RISM3D_T = 4, RISM3D_U = 5,
+       RISM3D_PHI = 6, RISM3D_R = 7 };
+
+typedef struct {
+    int n_sites;              /* solvent sites n_v, 1..8 */
+    const double *q;          /* [n_sites] partial charges (host) */
+    const double *sigma;      /* [n_sites] LJ sigma (host) */
+    const double *eps;        /* [n_sites] LJ epsilon (host) */
+    const double *rho;        /* [n_sites] site number densities, > 0 (host) */
+    double temperature;       /* > 0 */
+    int n_k;                  /* >= 2 entries of the susceptibility table */
+    double dk;                /* table spacing; entry j is at k = j * dk */
+    const double *chi;        /* [n_sites][n_sites][n_k] X_ag(k_j) = omega_ag + rho_a h_ag
+                                 (the solvent susceptibility defined under Eq. 8), host.
+                                 Linearly interpolated in |k|; past the end the last entry
+                                 is used. */
+} rism3d_solvent;
+
+typedef struct {
+    int n[3];                 /* Nx, Ny, Nz */
+    double spacing[3];        /* dx, dy, dz > 0 */
+    double origin[3];         /* position of grid point (0, 0, 0) */
+} rism3d_grid;
+
+typedef struct {
+    int precision;            /* 64: every step in FP64. 32: FFTs, contraction, closure and
+                                 the stored fields in FP32; Gram matrix, MDIIS solve, SFE and
+                                 the Coulomb/long-range sums accumulated in FP64. */
+    int mdiis_nvec;           /* M, stored iterates, 1..16 (1 = damped Picard) */
+    double mdiis_damp;        /* eta of t_new = sum c_i (t_i + eta R_i), in (0, 2] */
+    int dynamic_damp;         /* 1: eta = clamp(-0.2 log10(RMS), 0.1, 1) (Modified DIIS
+                                 passage, log base read as 10) */
+    int max_iter;             /* iteration limit over all closure stages, >= 1 */
+    int check_every;          /* iterations per CUDA-graph launch between status polls */
+    int max_atoms;            /* capacity for rism3d_set_solute */
+    int timing;               /* 1: record CUDA events around every kernel of the solve so
+                                 rism3d_get_stats reports measured per-kernel device time */
+    void *cuda_stream;        /* cudaStream_t to run on; NULL: the library creates one */
+    void *workspace;          /* device buffer of >= rism3d_workspace_bytes bytes, 256-byte
+                                 aligned, owned by the caller and kept alive until
+                                 rism3d_destroy; NULL: the library allocates it */
+    size_t workspace_bytes;
+} rism3d_options;
+
+typedef struct {
+    int iterations;           /* iterations over all closure stages */
+    int converged;            /* 1 if the final stage reached the tolerance */
+    double rms_residual;      /* RMS of R = t' - t of the last iteration, read of Eq. 41 */
+    double seconds_iter;      /* wall time of the solve call */
+} rism3d_report;
+
+/* Per-kernel counters of a context, accumulated since creation or the last
+ * rism3d_reset_stats. Kernel index: 0 plane_fwd (MDIIS update + closure + forward z/y FFT),
+ * 1 pencil (x FFT + Eq. 13 contraction + inverse x FFT), 2 plane_inv (inverse y/z FFT +
+ * residual + Gram partials), 3 mdiis (Gram reduction + bordered solve), 4 potential
+ * (Eqs. 22, 29), 5 long_range (Eq. 30), 6 sfe, 7 other (guess, conversions, field output). */
+#define RISM3D_N_KERNELS 8
+typedef struct {
+    long long launches[RISM3D_N_KERNELS];   /* kernels launched (including ones that found the
+                                               solve finished and returned at once) */
+    long long timed[RISM3D_N_KERNELS];      /* launches that did work and were timed */
+    double ms[RISM3D_N_KERNELS];            /* summed CUDA-event time of the timed launches */
+    double bytes[RISM3D_N_KERNELS];         /* algorithmic HBM bytes of the launches that did
+                                               work (the byte model of the kernel's docs) */
+    long long iterations;
+    long long solves;
+} rism3d_stats;
+
+/* Library version string, static storage. */
+const char *rism3d_version(void);
+
+/* Fill *opt with the defaults: precision 32, M = 5, eta = 0.7, static damping,
+ * max_iter 10000, check_every 8, max_atoms 100000, timing off, NULL stream and workspace. */
+void rism3d_options_default(rism3d_options *opt);
+
+/* Bytes of device workspace a context with these inputs needs. EINVAL on bad input,
+ * EUNSUPPORTED if the grid cannot be handled. */
+rism3d_status rism3d_workspace_bytes(const rism3d_solvent *solvent, const rism3d_grid *grid,
+                                     const rism3d_options *opt, size_t *bytes);
+
+/* Create a context for one solvent and one grid (the solvent's 1D part is computed once
+ * per solvent and reused, Package Features section). Copies the susceptibility table to
+ * the device as the interpolation table of Eq. 13. On success *out is a new context. */
+rism3d_status rism3d_create(const rism3d_solvent *solvent, const rism3d_grid *grid,
+                            const rism3d_options *opt, rism3d_ctx **out);
+
+/* Set the solute (the paper's "initialization"): builds beta*u_g (Eq. 22, Lorentz-Berthelot
+ * mixing, r^2 floored at 1e-8 A^2, beta*u capped above at 1e4), the long-range field phi
+ * (Eq. 29) and its analytic transform (Eq. 30, zero at k = 0 and on Nyquist planes), and
+ * sets the initial guess t = f (step 1). xyz is [n_atoms][3], q/sigma/eps are [n_atoms],
+ * all host arrays. 1 <= n_atoms <= max_atoms. */
+rism3d_status rism3d_set_solute(rism3d_ctx *ctx, int n_atoms, const double *xyz,
+                                const double *q, const double *sigma, const double *eps);
+
+/* Replace the initial guess t by a caller field [n_sites][Nx][Ny][Nz] (warm start). */
+rism3d_status rism3d_set_guess(rism3d_ctx *ctx, const double *t, int on_device);
+
+/* Run steps 2-7 from the current guess until RMS(R) < tol (read of Eq. 41), max_iter, or a
+ * non-finite residual. closure is RISM3D_KH / RISM3D_HNC / RISM3D_PSE, pse_order >= 1 for
+ * PSE. Returns OK, ENOTCONV or EDIVERGED (the report is filled in every case), or an
+ * error. The converged iterate replaces the guess, so a second call continues from it. */
+rism3d_status rism3d_solve(rism3d_ctx *ctx, int closure, int pse_order, double tol,
+                           rism3d_report *report);
+
+/* One application of steps 2-5 to a caller field t (FP64, [n_sites][Nx][Ny][Nz]):
+ * writes R = t' - t = h + 1 - g (Eq. 33) into R. Both arrays host or both device
+ * (on_device). Overwrites the context's iterate and history. */
+rism3d_status rism3d_residual(rism3d_ctx *ctx, int closure, int pse_order, const double *t,
+                              double *R, int on_device);
+
+/* Copy one field (see RISM3D_G ...) of every site, converted to FP64, into dst
+ * ([n_sites][Nx][Ny][Nz], or [Nx][Ny][Nz] for PHI). count is the capacity of dst in
+ * elements. G, H and C use the closure of the last solve (KH before any solve). */
+rism3d_status rism3d_get(rism3d_ctx *ctx, int field, double *dst, size_t count, int on_device);
+
+/* Solvation free energy in kcal/mol of the current iterate: k_B T sum_g rho_g dV
+ * sum_grid (integrand of kind), Eqs. 17-18, GF and PSE-n (pse_order >= 1). Accumulated in
+ * FP64. per_site ([n_sites], host) may be NULL. */
+rism3d_status rism3d_get_sfe(rism3d_ctx *ctx, int kind, int pse_order, double *total,
+                             double *per_site);
+
+/* Copy the counters; timing fields are zero unless the context was created with timing = 1. */
+rism3d_status rism3d_get_stats(const rism3d_ctx *ctx, rism3d_stats *out);
+
+/* Zero the counters. */
+rism3d_status rism3d_reset_stats(rism3d_ctx *ctx);
+
+/* Message of the last failure on ctx (or of the last failed create when ctx is NULL). */
+const char *rism3d_last_error(const rism3d_ctx *ctx);
+
+/* Free the context and everything the library allocated for it. NULL is accepted. */
+void rism3d_destroy(rism3d_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RISM3D_PUBLIC_API_H_ */

@@ -146,6 +146,8 @@ def solve(problem, kind=cl.KH, pse_order=3, tol=1e-6, max_iter=10000, mdiis_nvec
             if rms < stol:
                 converged = True
                 break
+            if total >= max_iter:
+                break
             # step 6: MDIIS
             hist_t.append(t)
             hist_R.append(R)

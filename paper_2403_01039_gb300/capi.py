@@ -1,0 +1,344 @@
+"""ctypes binding of the C ABI in include/rism3d.h (argument marshalling only).
+
+Every step of the solve runs in the library's CUDA kernels. PyTorch supplies the device
+memory of the workspace and the CUDA stream the library runs on. Importing this module
+does not load the library; the first use does, and fails loudly (``RuntimeError``) when the
+compiled library is missing - there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "librism3d.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENOTCONV, EDIVERGED, ETIMEOUT, EUNSUPPORTED = range(9)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESTATE", "ENOTCONV", "EDIVERGED", "ETIMEOUT",
+                "EUNSUPPORTED"]
+CLOSURES = {"kh": 1, "hnc": 2, "pse": 3}
+SFE_KINDS = {"kh": 1, "hnc": 2, "gf": 3, "pse": 4}
+FIELDS = {"g": 1, "c": 2, "h": 3, "t": 4, "u": 5, "phi": 6, "r": 7}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Solvent(ctypes.Structure):
+    _fields_ = [("n_sites", ctypes.c_int), ("q", _dp), ("sigma", _dp), ("eps", _dp), ("rho", _dp),
+                ("temperature", ctypes.c_double), ("n_k", ctypes.c_int), ("dk", ctypes.c_double),
+                ("chi", _dp)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("spacing", ctypes.c_double * 3),
+                ("origin", ctypes.c_double * 3)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("mdiis_nvec", ctypes.c_int),
+                ("mdiis_damp", ctypes.c_double), ("dynamic_damp", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("max_atoms", ctypes.c_int), ("timing", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+N_KERNELS = 8
+KERNEL_NAMES = ["plane_fwd", "pencil", "plane_inv", "mdiis", "potential", "long_range", "sfe", "other"]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong * N_KERNELS), ("timed", ctypes.c_longlong * N_KERNELS),
+                ("ms", ctypes.c_double * N_KERNELS), ("bytes", ctypes.c_double * N_KERNELS),
+                ("iterations", ctypes.c_longlong), ("solves", ctypes.c_longlong)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("rms_residual", ctypes.c_double), ("seconds_iter", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load the compiled library (once). Raises RuntimeError when it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("the CUDA library %s is missing: run __graft_entry__.build() "
+                           "(or python -m paper_2403_01039_gb300.build) first" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+    sig = {
+        "rism3d_version": (ctypes.c_char_p, []),
+        "rism3d_options_default": (None, [P(Options)]),
+        "rism3d_workspace_bytes": (c_int, [P(Solvent), P(Grid), P(Options), P(c_size_t)]),
+        "rism3d_create": (c_int, [P(Solvent), P(Grid), P(Options), P(c_void_p)]),
+        "rism3d_set_solute": (c_int, [c_void_p, c_int, _dp, _dp, _dp, _dp]),
+        "rism3d_set_guess": (c_int, [c_void_p, c_void_p, c_int]),
+        "rism3d_solve": (c_int, [c_void_p, c_int, c_int, c_double, P(Report)]),
+        "rism3d_residual": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),
+        "rism3d_get": (c_int, [c_void_p, c_int, c_void_p, c_size_t, c_int]),
+        "rism3d_get_sfe": (c_int, [c_void_p, c_int, c_int, P(c_double), _dp]),
+        "rism3d_get_stats": (c_int, [c_void_p, P(Stats)]),
+        "rism3d_reset_stats": (c_int, [c_void_p]),
+        "rism3d_last_error": (ctypes.c_char_p, [c_void_p]),
+        "rism3d_destroy": (None, [c_void_p]),
+    }
+    sig.update({
+        "rism1d_options_default": (None, [P(Rism1dOptions)]),
+        "rism1d_xrism": (c_int, [P(Rism1dSolvent), P(Rism1dOptions), _dp, _dp, P(c_int), _dp]),
+        "rism1d_last_error": (ctypes.c_char_p, []),
+    })
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class Rism1dSolvent(ctypes.Structure):
+    _fields_ = [("n_sites", ctypes.c_int), ("q", _dp), ("sigma", _dp), ("eps", _dp), ("rho", _dp),
+                ("species", ctypes.POINTER(ctypes.c_int)), ("coords", _dp),
+                ("temperature", ctypes.c_double)]
+
+
+class Rism1dOptions(ctypes.Structure):
+    _fields_ = [("n_r", ctypes.c_int), ("dr", ctypes.c_double), ("closure", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mdiis_nvec", ctypes.c_int),
+                ("mdiis_damp", ctypes.c_double), ("charge_steps", ctypes.c_int)]
+
+
+class RismError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__("%s: %s" % (name, message))
+
+
+def _arr(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def make_solvent(sites):
+    """Marshal a solvent dict (q, sigma, eps, rho, temperature, chi [n,n,nk], dk)."""
+    keep = {}
+    for k in ("q", "sigma", "eps", "rho", "chi"):
+        keep[k] = _arr(sites[k])
+    n = len(keep["q"][0])
+    chi = keep["chi"][0]
+    if chi.shape[:2] != (n, n):
+        raise ValueError("chi must be [n_sites][n_sites][n_k]")
+    s = Solvent(n, keep["q"][1], keep["sigma"][1], keep["eps"][1], keep["rho"][1],
+                float(sites["temperature"]), chi.shape[2], float(sites["dk"]), keep["chi"][1])
+    return s, keep
+
+
+def make_grid(grid):
+    g = Grid()
+    for d in range(3):
+        g.n[d] = int(grid["n"][d])
+        g.spacing[d] = float(grid["spacing"][d])
+        g.origin[d] = float(grid["origin"][d])
+    return g
+
+
+def default_options():
+    o = Options()
+    load().rism3d_options_default(ctypes.byref(o))
+    return o
+
+
+def _check(lib, ctx, st):
+    if st != OK:
+        raise RismError(st, lib.rism3d_last_error(ctx).decode())
+
+
+def xrism(sites, n_r=2048, dr=0.05, closure="kh", tol=1e-10, charge_steps=10):
+    """Solvent susceptibility X_ag(k_j), k_j = j dk, of a pure solvent (Eq. 4) from the
+    library's host 1D-RISM solver. Returns (chi [n][n][n_r], dk, iterations, rms)."""
+    lib = load()
+    keep = {k: _arr(sites[k]) for k in ("q", "sigma", "eps", "rho")}
+    species = np.ascontiguousarray(sites["species"], dtype=np.int32)
+    coords, pc = _arr(np.asarray(sites["coords"], dtype=np.float64).reshape(-1, 3))
+    n = len(keep["q"][0])
+    sv = Rism1dSolvent(n, keep["q"][1], keep["sigma"][1], keep["eps"][1], keep["rho"][1],
+                       species.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), pc,
+                       float(sites["temperature"]))
+    o = Rism1dOptions()
+    lib.rism1d_options_default(ctypes.byref(o))
+    o.n_r, o.dr, o.tol, o.charge_steps = int(n_r), float(dr), float(tol), int(charge_steps)
+    o.closure = {"kh": 1, "hnc": 2}[closure]
+    chi = np.zeros((n, n, n_r))
+    dk = ctypes.c_double()
+    its = ctypes.c_int()
+    rms = ctypes.c_double()
+    st = lib.rism1d_xrism(ctypes.byref(sv), ctypes.byref(o), chi.ctypes.data_as(_dp), ctypes.byref(dk),
+                          ctypes.byref(its), ctypes.byref(rms))
+    if st != 0:
+        raise RuntimeError("rism1d_xrism failed (%d): %s" % (st, lib.rism1d_last_error().decode()))
+    return chi, dk.value, its.value, rms.value
+
+
+class Solver:
+    """One solvent on one grid (``rism3d_create``); solutes are set and solved in turn."""
+
+    def __init__(self, solvent, grid, precision=32, mdiis_nvec=5, mdiis_damp=0.7,
+                 dynamic_damp=False, max_iter=10000, check_every=8, max_atoms=100000,
+                 timing=False, stream=None, device=None):
+        import torch
+        self._torch = torch
+        lib = load()
+        self.lib = lib
+        self.device = torch.device("cuda" if device is None else device)
+        self.n = tuple(int(v) for v in grid["n"])
+        self.n_sites = len(solvent["q"])
+        self.precision = precision
+        self._solv, self._keep = make_solvent(solvent)
+        self._grid = make_grid(grid)
+        o = default_options()
+        o.precision = precision
+        o.mdiis_nvec = mdiis_nvec
+        o.mdiis_damp = mdiis_damp
+        o.dynamic_damp = int(bool(dynamic_damp))
+        o.max_iter = max_iter
+        o.check_every = check_every
+        o.max_atoms = max_atoms
+        o.timing = int(bool(timing))
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
+            nbytes = ctypes.c_size_t()
+            _check(lib, None, lib.rism3d_workspace_bytes(ctypes.byref(self._solv), ctypes.byref(self._grid),
+                                                         ctypes.byref(o), ctypes.byref(nbytes)))
+            self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+            o.workspace = ctypes.c_void_p(self.workspace.data_ptr())
+            o.workspace_bytes = nbytes.value
+            self._opt = o
+            ctx = ctypes.c_void_p()
+            _check(lib, None, lib.rism3d_create(ctypes.byref(self._solv), ctypes.byref(self._grid),
+                                                ctypes.byref(o), ctypes.byref(ctx)))
+        self.ctx = ctx
+
+    # -- helpers
+    @property
+    def field_shape(self):
+        return (self.n_sites,) + self.n
+
+    def _field_arg(self, x):
+        """(pointer, on_device, keepalive) for a full field [n_sites][Nx][Ny][Nz] given as a
+        numpy array or a contiguous float64 CUDA tensor; the size is checked here because
+        the library cannot check a raw pointer."""
+        torch = self._torch
+        need = int(np.prod(self.field_shape))
+        if isinstance(x, torch.Tensor):
+            if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous():
+                raise ValueError("device arrays must be contiguous float64 CUDA tensors")
+            if x.numel() != need:
+                raise ValueError("field has %d values, expected %d" % (x.numel(), need))
+            return ctypes.c_void_p(x.data_ptr()), 1, x
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        if a.size != need:
+            raise ValueError("field has %d values, expected %d" % (a.size, need))
+        return ctypes.c_void_p(a.ctypes.data), 0, a
+
+    def _sync_torch(self):
+        # device inputs produced on torch's current stream must be ready for the library stream
+        self.stream.wait_stream(self._torch.cuda.current_stream(self.device))
+
+    # -- API
+    def set_solute(self, xyz, q, sigma, eps):
+        xyz, pxyz = _arr(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+        q, pq = _arr(q)
+        s, ps = _arr(sigma)
+        e, pe = _arr(eps)
+        _check(self.lib, self.ctx, self.lib.rism3d_set_solute(self.ctx, len(q), pxyz, pq, ps, pe))
+
+    def set_guess(self, t):
+        p, dev, keep = self._field_arg(t)
+        if dev:
+            self._sync_torch()
+        _check(self.lib, self.ctx, self.lib.rism3d_set_guess(self.ctx, p, dev))
+
+    def solve(self, closure="kh", pse_order=3, tol=1e-6, check=True):
+        rep = Report()
+        st = self.lib.rism3d_solve(self.ctx, CLOSURES[closure], int(pse_order), float(tol),
+                                   ctypes.byref(rep))
+        out = dict(status=st, iterations=rep.iterations, converged=bool(rep.converged),
+                   rms=rep.rms_residual, seconds=rep.seconds_iter)
+        if check and st not in (OK,):
+            raise RismError(st, self.lib.rism3d_last_error(self.ctx).decode())
+        return out
+
+    def residual(self, t, closure="kh", pse_order=3):
+        torch = self._torch
+        p, dev, keep = self._field_arg(t)
+        if dev:
+            out = torch.empty_like(t)
+            self._sync_torch()
+            st = self.lib.rism3d_residual(self.ctx, CLOSURES[closure], int(pse_order), p,
+                                          ctypes.c_void_p(out.data_ptr()), 1)
+        else:
+            out = np.empty(keep.shape, dtype=np.float64)
+            st = self.lib.rism3d_residual(self.ctx, CLOSURES[closure], int(pse_order), p,
+                                          ctypes.c_void_p(out.ctypes.data), 0)
+        _check(self.lib, self.ctx, st)
+        return out
+
+    def get(self, field, out=None):
+        """Field as a float64 numpy array, or into ``out`` (numpy or CUDA tensor)."""
+        shape = self.n if field == "phi" else self.field_shape
+        if out is None:
+            out = np.empty(shape, dtype=np.float64)
+        torch = self._torch
+        if isinstance(out, torch.Tensor):
+            if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
+                raise ValueError("out must be a contiguous float64 CUDA tensor")
+            st = self.lib.rism3d_get(self.ctx, FIELDS[field], ctypes.c_void_p(out.data_ptr()), out.numel(), 1)
+        else:
+            if out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"]:
+                raise ValueError("out must be a contiguous float64 numpy array")
+            st = self.lib.rism3d_get(self.ctx, FIELDS[field], ctypes.c_void_p(out.ctypes.data), out.size, 0)
+        _check(self.lib, self.ctx, st)
+        return out
+
+    def sfe(self, kind="kh", pse_order=3):
+        tot = ctypes.c_double()
+        per = np.zeros(self.n_sites)
+        _check(self.lib, self.ctx, self.lib.rism3d_get_sfe(self.ctx, SFE_KINDS[kind], int(pse_order),
+                                                           ctypes.byref(tot), per.ctypes.data_as(_dp)))
+        return tot.value, per
+
+    def stats(self):
+        st = Stats()
+        _check(self.lib, self.ctx, self.lib.rism3d_get_stats(self.ctx, ctypes.byref(st)))
+        out = dict(iterations=st.iterations, solves=st.solves, kernels={})
+        for k, name in enumerate(KERNEL_NAMES):
+            out["kernels"][name] = dict(launches=st.launches[k], timed=st.timed[k], ms=st.ms[k],
+                                        bytes=st.bytes[k])
+        return out
+
+    def reset_stats(self):
+        _check(self.lib, self.ctx, self.lib.rism3d_reset_stats(self.ctx))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.rism3d_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,899 @@
+// Host layer of the C ABI declared in include/rism3d.h: validation, device workspace layout,
+// transform plans, the interpolation table of Eq. 13, and the CUDA-graph iteration loop.
+// All arithmetic of the method runs in rism3d_kernels.cu; this file only prepares inputs
+// (unit conversion, table scaling, twiddle factors) and schedules launches.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rism3d.h"
+#include "rism3d_internal.h"
+
+using namespace rism;
+
+namespace {
+
+constexpr double kKB = 0.0019872041;      // kcal / (mol K)
+constexpr double kCoulomb = 332.0637;     // kcal A / (mol e^2)
+constexpr double kPi = 3.14159265358979323846;
+constexpr size_t kMaxSmem = 227 * 1024;
+constexpr size_t kPencilSmemTarget = 100 * 1024;
+
+thread_local std::string g_create_error;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Factor L into radices 8/4/2 (powers of two, largest first, without a trailing 2 when a
+// 4 can absorb it) and 3/5. Returns false if L has another prime factor.
+bool make_plan(int L, FftPlan &p) {
+    p.L = L;
+    p.nst = 0;
+    int n = L, twos = 0;
+    while (n % 2 == 0) {
+        n /= 2;
+        ++twos;
+    }
+    std::vector<int> r;
+    while (n % 3 == 0) {
+        n /= 3;
+        r.push_back(3);
+    }
+    while (n % 5 == 0) {
+        n /= 5;
+        r.push_back(5);
+    }
+    if (n != 1 || L < 1) return false;
+    int eights = twos / 3, rem = twos % 3;
+    std::vector<int> t;
+    if (rem == 1 && eights > 0) {
+        --eights;
+        t.push_back(4);
+        t.push_back(4);
+    } else if (rem == 1) {
+        t.push_back(2);
+    } else if (rem == 2) {
+        t.push_back(4);
+    }
+    for (int i = 0; i < eights; ++i) t.insert(t.begin(), 8);
+    for (int v : r) t.push_back(v);
+    if ((int)t.size() > kMaxRadixStages) return false;
+    for (size_t i = 0; i < t.size(); ++i) p.radix[i] = t[i];
+    p.nst = (int)t.size();
+    return true;
+}
+
+// Largest batch chunk for which every stage keeps at most MAXC / R butterflies per thread.
+int fft_chunk(const FftPlan &p, int nthreads, int maxc) {
+    int chunk = 1 << 30;
+    for (int s = 0; s < p.nst; ++s) {
+        const int R = p.radix[s];
+        const int per = maxc / R;                  // butterflies a thread can hold
+        const int lr = p.L / R;                    // butterflies per sequence
+        const int c = (int)((long long)nthreads * per / lr);
+        chunk = c < chunk ? c : chunk;
+    }
+    return chunk;
+}
+
+}  // namespace
+
+struct rism3d_ctx {
+    int device = 0;
+    int precision = 32;
+    rism3d_options opt{};
+    int nv = 0, Nx = 0, Ny = 0, Nz = 0, Kz = 0;
+    long long G = 0;
+    double spacing[3] = {0, 0, 0}, origin[3] = {0, 0, 0};
+    std::vector<double> q, sig, eps, rho;
+    double temperature = 0, beta = 0, dV = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *ws = nullptr;
+    bool own_ws = false;
+    size_t ws_bytes = 0;
+    // device pointers inside the workspace
+    Ctrl *ctrl = nullptr;
+    double *atoms = nullptr, *site_sig = nullptr, *site_eps = nullptr, *site_q = nullptr;
+    double *sfe_part = nullptr, *staging = nullptr;
+    Fields<float> f32{};
+    Fields<double> f64{};
+    Ctrl *ctrl_host = nullptr;                 // pinned
+    cudaGraphExec_t graph = nullptr;
+    bool has_solute = false;
+    int cur_slot = 0;
+    int last_kind = kKH, last_order = 1;
+    std::vector<double> atom_host;
+    std::string err;
+    rism3d_stats stats{};
+    std::vector<cudaEvent_t> ev;               // [check_every][5] around the iteration kernels
+    cudaEvent_t ev_aux[2] = {nullptr, nullptr};
+
+    bool fp32() const { return precision == 32; }
+};
+
+static rism3d_status fail(rism3d_ctx *ctx, rism3d_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx)
+        ctx->err = buf;
+    else
+        g_create_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(ctx, call)                                                                      \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail((ctx), RISM3D_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                        __FILE__, __LINE__);                                                     \
+    } while (0)
+
+// ------------------------------------------------------------------ layout
+namespace {
+
+struct Layout {
+    size_t ctrl, bu, phi, psi, spec, X, R, anchor, table, tw, partials, sfe, atoms, sites, staging, total;
+};
+
+struct Geometry {
+    int nv, Nx, Ny, Nz, Kz, M, nk, max_atoms, s;   // s = bytes per real
+    long long G;
+    FftPlan px, py, ph;
+    int pitch, W, pencil_pitch, chunk_rows, chunk_cols, chunk_x;
+    size_t plane_smem, pencil_smem;
+};
+
+Layout make_layout(const Geometry &g) {
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    const size_t c = 2 * (size_t)g.s;
+    const size_t specN = (size_t)g.Nx * g.Ny * g.Kz + (size_t)g.Nx * g.Ny;
+    L.ctrl = take(sizeof(Ctrl));
+    L.bu = take((size_t)g.nv * g.G * g.s);
+    L.phi = take((size_t)g.G * g.s);
+    L.psi = take(specN * c);
+    L.spec = take((size_t)g.nv * specN * c);
+    L.X = take((size_t)g.M * g.nv * g.G * g.s);
+    L.R = take((size_t)g.M * g.nv * g.G * g.s);
+    L.anchor = take((size_t)2 * g.nv * g.G * g.s);
+    L.table = take((size_t)g.nk * (g.nv + 1) * g.nv * g.s);
+    L.tw = take((size_t)(g.Nx + g.Ny + g.Kz + g.Kz + 1) * c);
+    L.partials = take((size_t)g.nv * g.Nx * (kMaxHist + 1) * sizeof(double));
+    L.sfe = take((size_t)g.nv * kSfeBlocksPerSite * sizeof(double));
+    L.atoms = take((size_t)g.max_atoms * kAtomStride * sizeof(double));
+    L.sites = take((size_t)3 * kMaxSites * sizeof(double));
+    L.staging = take((size_t)g.nv * g.G * sizeof(double));
+    L.total = o;
+    return L;
+}
+
+rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, const rism3d_options *op,
+                           Geometry &g) {
+    if (!sv || !gr || !op) return fail(nullptr, RISM3D_EINVAL, "null solvent, grid or options");
+    if (sv->n_sites < 1 || sv->n_sites > kMaxSites)
+        return fail(nullptr, RISM3D_EINVAL, "n_sites must be in 1..%d", kMaxSites);
+    if (!sv->q || !sv->sigma || !sv->eps || !sv->rho || !sv->chi)
+        return fail(nullptr, RISM3D_EINVAL, "null solvent array");
+    for (int i = 0; i < sv->n_sites; ++i)
+        if (!(sv->rho[i] > 0.0) || !std::isfinite(sv->rho[i]))
+            return fail(nullptr, RISM3D_EINVAL, "rho[%d] must be positive", i);
+    if (!(sv->temperature > 0.0)) return fail(nullptr, RISM3D_EINVAL, "temperature must be positive");
+    if (sv->n_k < 2 || !(sv->dk > 0.0)) return fail(nullptr, RISM3D_EINVAL, "need n_k >= 2 and dk > 0");
+    for (int d = 0; d < 3; ++d) {
+        if (gr->n[d] < 2) return fail(nullptr, RISM3D_EINVAL, "grid n[%d] must be >= 2", d);
+        if (!(gr->spacing[d] > 0.0)) return fail(nullptr, RISM3D_EINVAL, "spacing[%d] must be > 0", d);
+    }
+    if (gr->n[2] % 2) return fail(nullptr, RISM3D_EUNSUPPORTED, "Nz must be even");
+    if (op->precision != 32 && op->precision != 64)
+        return fail(nullptr, RISM3D_EINVAL, "precision must be 32 or 64");
+    if (op->mdiis_nvec < 1 || op->mdiis_nvec > kMaxHist)
+        return fail(nullptr, RISM3D_EINVAL, "mdiis_nvec must be in 1..%d", kMaxHist);
+    if (!(op->mdiis_damp > 0.0 && op->mdiis_damp <= 2.0))
+        return fail(nullptr, RISM3D_EINVAL, "mdiis_damp must be in (0, 2]");
+    if (op->max_iter < 1 || op->check_every < 1 || op->max_atoms < 1)
+        return fail(nullptr, RISM3D_EINVAL, "max_iter, check_every and max_atoms must be >= 1");
+    g.nv = sv->n_sites;
+    g.Nx = gr->n[0];
+    g.Ny = gr->n[1];
+    g.Nz = gr->n[2];
+    g.Kz = g.Nz / 2;
+    g.G = (long long)g.Nx * g.Ny * g.Nz;
+    g.M = op->mdiis_nvec;
+    g.nk = sv->n_k;
+    g.max_atoms = op->max_atoms;
+    g.s = op->precision == 32 ? 4 : 8;
+    if (!make_plan(g.Nx, g.px) || !make_plan(g.Ny, g.py) || !make_plan(g.Kz, g.ph))
+        return fail(nullptr, RISM3D_EUNSUPPORTED, "Nx, Ny and Nz/2 must factor into 2, 3 and 5");
+    const int maxc = g.s == 4 ? 16 : 8;
+    const size_t c = 2 * (size_t)g.s;
+    g.pitch = g.Kz + 1;
+    if (g.pitch % 2 == 0) g.pitch += 1;        // odd pitch: column access without bank conflicts
+    g.plane_smem = c * ((size_t)g.Ny * g.pitch + g.Kz + g.Ny + g.Kz + 1) + 32 * sizeof(double) + 16;
+    if (g.plane_smem > kMaxSmem)
+        return fail(nullptr, RISM3D_EUNSUPPORTED,
+                    "a y-z plane (%d x %d) needs %zu bytes of shared memory (limit %zu)", g.Ny,
+                    g.Kz + 1, g.plane_smem, kMaxSmem);
+    g.pencil_pitch = g.Nx + 1;
+    g.W = 1;
+    for (int w = 16; w >= 1; w /= 2) {
+        size_t b = c * ((size_t)g.nv * w * g.pencil_pitch + g.Nx);
+        if (b <= kPencilSmemTarget || w == 1) {
+            g.W = w;
+            break;
+        }
+    }
+    g.pencil_smem = c * ((size_t)g.nv * g.W * g.pencil_pitch + g.Nx);
+    if (g.pencil_smem > kMaxSmem)
+        return fail(nullptr, RISM3D_EUNSUPPORTED, "x pencils of %d points do not fit in shared memory",
+                    g.Nx);
+    g.chunk_rows = fft_chunk(g.ph, kThreadsPlane, maxc);
+    g.chunk_cols = fft_chunk(g.py, kThreadsPlane, maxc);
+    g.chunk_x = fft_chunk(g.px, kThreadsPencil, maxc);
+    if (g.chunk_rows < 1 || g.chunk_cols < 1 || g.chunk_x < 1)
+        return fail(nullptr, RISM3D_EUNSUPPORTED, "transform length too long for one block");
+    return RISM3D_OK;
+}
+
+template <typename T>
+void fill_fields(rism3d_ctx *ctx, const Geometry &g, const Layout &L, Fields<T> &f) {
+    typedef typename Cx<T>::type C;
+    char *b = static_cast<char *>(ctx->ws);
+    f.nv = g.nv;
+    f.Nx = g.Nx;
+    f.Ny = g.Ny;
+    f.Nz = g.Nz;
+    f.Kz = g.Kz;
+    f.G = g.G;
+    f.specN = (long long)g.Nx * g.Ny * g.Kz;
+    f.bu = reinterpret_cast<T *>(b + L.bu);
+    f.phi = reinterpret_cast<T *>(b + L.phi);
+    f.psi = reinterpret_cast<C *>(b + L.psi);
+    f.psi_nyq = f.psi + f.specN;
+    f.spec = reinterpret_cast<C *>(b + L.spec);
+    f.spec_nyq = f.spec + (long long)g.nv * f.specN;
+    f.X = reinterpret_cast<T *>(b + L.X);
+    f.R = reinterpret_cast<T *>(b + L.R);
+    f.csr_a = reinterpret_cast<T *>(b + L.anchor);
+    f.h_a = f.csr_a + (long long)g.nv * g.G;
+    f.table = reinterpret_cast<T *>(b + L.table);
+    f.nk = g.nk;
+    C *tw = reinterpret_cast<C *>(b + L.tw);
+    f.tw_x = tw;
+    f.tw_y = f.tw_x + g.Nx;
+    f.tw_h = f.tw_y + g.Ny;
+    f.tw_z = f.tw_h + g.Kz;
+    f.px = g.px;
+    f.py = g.py;
+    f.ph = g.ph;
+    f.chunk_rows = g.chunk_rows;
+    f.chunk_cols_fwd = g.chunk_cols;
+    f.chunk_x = g.chunk_x;
+    f.pitch = g.pitch;
+    f.W = g.W;
+    f.pencil_pitch = g.pencil_pitch;
+    f.tiles_main = g.Ny * ((g.Kz + g.W - 1) / g.W);
+    f.tiles_nyq = (g.Ny + g.W - 1) / g.W;
+    for (int i = 0; i < kMaxSites; ++i) f.bq[i] = i < g.nv ? ctx->beta * ctx->q[i] : 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const int N = d == 0 ? g.Nx : (d == 1 ? g.Ny : g.Nz);
+        f.ks[d] = 2.0 * kPi / (N * ctx->spacing[d]);
+    }
+    f.partials = reinterpret_cast<double *>(b + L.partials);
+    f.ctrl = reinterpret_cast<Ctrl *>(b + L.ctrl);
+}
+
+// Interpolation table of Eq. 13 scaled for the unnormalised inverse transform:
+// A[j][a][g] = X_ag(k_j) / (Nx Ny Nz) for a < n_v, and the charge row
+// A[j][n_v][g] = -sum_a q_a X_ag(k_j) / (Nx Ny Nz), which multiplies beta Phi~ / dV.
+template <typename T>
+std::vector<T> make_table(const rism3d_solvent *sv, long long G) {
+    const int nv = sv->n_sites, nk = sv->n_k;
+    std::vector<T> A((size_t)nk * (nv + 1) * nv);
+    const double inv = 1.0 / (double)G;
+    for (int j = 0; j < nk; ++j) {
+        for (int g = 0; g < nv; ++g) {
+            double Q = 0.0;
+            for (int a = 0; a < nv; ++a) {
+                const double x = sv->chi[((size_t)a * nv + g) * nk + j];
+                A[((size_t)j * (nv + 1) + a) * nv + g] = (T)(x * inv);
+                Q += sv->q[a] * x;
+            }
+            A[((size_t)j * (nv + 1) + nv) * nv + g] = (T)(-Q * inv);
+        }
+    }
+    return A;
+}
+
+// exp(-2 pi i m / L), m < L, from the host libm in FP64, rounded to the working precision.
+template <typename T>
+void push_twiddles(std::vector<typename Cx<T>::type> &v, int L, int count) {
+    typedef typename Cx<T>::type C;
+    for (int m = 0; m < count; ++m) {
+        const double a = -2.0 * kPi * (double)m / (double)L;
+        C c;
+        c.x = (T)std::cos(a);
+        c.y = (T)std::sin(a);
+        v.push_back(c);
+    }
+}
+
+template <typename T>
+rism3d_status upload_tables(rism3d_ctx *ctx, const rism3d_solvent *sv, const Layout &L, Fields<T> &f) {
+    typedef typename Cx<T>::type C;
+    std::vector<T> A = make_table<T>(sv, ctx->G);
+    char *b = static_cast<char *>(ctx->ws);
+    CUDA_TRY(ctx, cudaMemcpy(b + L.table, A.data(), A.size() * sizeof(T), cudaMemcpyHostToDevice));
+    std::vector<C> tw;
+    push_twiddles<T>(tw, ctx->Nx, ctx->Nx);
+    push_twiddles<T>(tw, ctx->Ny, ctx->Ny);
+    push_twiddles<T>(tw, ctx->Kz, ctx->Kz);
+    push_twiddles<T>(tw, ctx->Nz, ctx->Kz + 1);
+    CUDA_TRY(ctx, cudaMemcpy(b + L.tw, tw.data(), tw.size() * sizeof(C), cudaMemcpyHostToDevice));
+    f.inv_dk = 1.0 / sv->dk;
+    CUDA_TRY(ctx, prepare_kernels<T>(f));
+    return RISM3D_OK;
+}
+
+void closure_stages(int kind, int order, double tol, Ctrl &c) {
+    const double stage_tol = tol > 1e-4 ? tol : 1e-4;
+    int n = 0;
+    if (kind == kKH) {
+        c.stage_kind[n] = kKH, c.stage_order[n++] = 1;
+    } else if (kind == kHNC) {
+        c.stage_kind[n] = kKH, c.stage_order[n++] = 1;
+        c.stage_kind[n] = kHNC, c.stage_order[n++] = 0;
+    } else {
+        c.stage_kind[n] = kKH, c.stage_order[n++] = 1;
+        for (int o = 2; o <= order && n < kMaxClosureStages; ++o) c.stage_kind[n] = kPSE, c.stage_order[n++] = o;
+    }
+    c.n_stages = n;
+    for (int i = 0; i < n; ++i) c.stage_tol[i] = (i == n - 1) ? tol : stage_tol;
+}
+
+template <typename T>
+rism3d_status run_iteration_kernels(rism3d_ctx *ctx, const Fields<T> &f, bool with_mdiis) {
+    CUDA_TRY(ctx, launch_plane_fwd<T>(f, ctx->stream));
+    CUDA_TRY(ctx, launch_pencil<T>(f, ctx->stream));
+    CUDA_TRY(ctx, launch_plane_inv<T>(f, ctx->stream));
+    if (with_mdiis) CUDA_TRY(ctx, launch_mdiis<T>(f, ctx->stream));
+    return RISM3D_OK;
+}
+
+rism3d_status iteration(rism3d_ctx *ctx, bool with_mdiis) {
+    return ctx->fp32() ? run_iteration_kernels<float>(ctx, ctx->f32, with_mdiis)
+                       : run_iteration_kernels<double>(ctx, ctx->f64, with_mdiis);
+}
+
+// Algorithmic HBM bytes of the iterations that ran (from the device counters): per
+// site-point (P = n_v Nx Ny Nz of them, s bytes per real, z = (Kz + 1) / Kz for the half
+// spectrum) plane_fwd moves the history it combines (2 per stored pair + 1 for t, or 1 to
+// load t), beta*u (1), phi (1/n_v), the spectrum it writes (z) and the anchor (1 read, 1
+// write on refresh); pencil reads and writes the spectrum (2 z) plus Psi (z/n_v) until the
+// first anchor; plane_inv reads the spectrum (z), t and beta*u (2), the history residuals,
+// the anchor h_a, and writes R (1) and h_a on refresh.
+void account_iterations(rism3d_ctx *ctx, const Ctrl &c) {
+    const double P = (double)ctx->nv * (double)ctx->G;
+    const double s = ctx->fp32() ? 4.0 : 8.0;
+    const double z = (double)(ctx->Kz + 1) / (double)ctx->Kz;
+    const double it = (double)c.acc_iters;
+    ctx->stats.iterations += c.acc_iters;
+    ctx->stats.bytes[0] += P * s * ((double)c.acc_fwd_units + it * (1.0 + 1.0 / ctx->nv + z) +
+                                    (double)c.acc_anchor + (double)c.acc_refresh);
+    ctx->stats.bytes[1] += P * s * z * (2.0 * it + (double)c.acc_psi / ctx->nv);
+    ctx->stats.bytes[2] += P * s * (it * (z + 3.0) + (double)c.acc_hist + (double)c.acc_anchor +
+                                    (double)c.acc_refresh);
+    ctx->stats.bytes[3] += 8.0 * ctx->nv * ctx->Nx * (it + (double)c.acc_hist);
+}
+
+// Event pair around a direct (non-graph) launch of kernel k, when timing is on.
+struct AuxTimer {
+    rism3d_ctx *ctx;
+    int k;
+    bool on;
+    AuxTimer(rism3d_ctx *c, int kernel) : ctx(c), k(kernel), on(c->opt.timing != 0) {
+        if (on) cudaEventRecord(ctx->ev_aux[0], ctx->stream);
+    }
+    void stop(double bytes) {
+        ctx->stats.launches[k] += 1;
+        ctx->stats.bytes[k] += bytes;
+        if (!on) return;
+        cudaEventRecord(ctx->ev_aux[1], ctx->stream);
+        cudaEventSynchronize(ctx->ev_aux[1]);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev_aux[0], ctx->ev_aux[1]) == cudaSuccess) {
+            ctx->stats.ms[k] += ms;
+            ctx->stats.timed[k] += 1;
+        }
+    }
+};
+
+template <typename T>
+rism3d_status timed_iteration(rism3d_ctx *ctx, const Fields<T> &f, cudaEvent_t *e) {
+    CUDA_TRY(ctx, cudaEventRecord(e[0], ctx->stream));
+    CUDA_TRY(ctx, launch_plane_fwd<T>(f, ctx->stream));
+    CUDA_TRY(ctx, cudaEventRecord(e[1], ctx->stream));
+    CUDA_TRY(ctx, launch_pencil<T>(f, ctx->stream));
+    CUDA_TRY(ctx, cudaEventRecord(e[2], ctx->stream));
+    CUDA_TRY(ctx, launch_plane_inv<T>(f, ctx->stream));
+    CUDA_TRY(ctx, cudaEventRecord(e[3], ctx->stream));
+    CUDA_TRY(ctx, launch_mdiis<T>(f, ctx->stream));
+    CUDA_TRY(ctx, cudaEventRecord(e[4], ctx->stream));
+    return RISM3D_OK;
+}
+
+rism3d_status build_graph(rism3d_ctx *ctx) {
+    if (ctx->graph) return RISM3D_OK;
+    cudaGraph_t g = nullptr;
+    const int K = ctx->opt.check_every;
+    if (ctx->opt.timing && ctx->ev.empty()) {
+        ctx->ev.assign((size_t)K * 5, nullptr);
+        for (auto &e : ctx->ev) CUDA_TRY(ctx, cudaEventCreate(&e));
+    }
+    CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    rism3d_status st = RISM3D_OK;
+    for (int i = 0; i < K && st == RISM3D_OK; ++i) {
+        if (ctx->opt.timing)
+            st = ctx->fp32() ? timed_iteration<float>(ctx, ctx->f32, &ctx->ev[(size_t)i * 5])
+                             : timed_iteration<double>(ctx, ctx->f64, &ctx->ev[(size_t)i * 5]);
+        else
+            st = iteration(ctx, true);
+    }
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (st != RISM3D_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(ctx, RISM3D_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->graph = nullptr;
+        return fail(ctx, RISM3D_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    return RISM3D_OK;
+}
+
+void reset_ctrl(rism3d_ctx *ctx, Ctrl &c) {
+    std::memset(&c, 0, sizeof(Ctrl));
+    c.status = kRunning;
+    c.max_iter = ctx->opt.max_iter;
+    c.M = ctx->opt.mdiis_nvec;
+    c.dynamic = ctx->opt.dynamic_damp ? 1 : 0;
+    c.damp = ctx->opt.mdiis_damp;
+    c.inv_count = 1.0 / ((double)ctx->nv * (double)ctx->G);
+    c.cur = ctx->cur_slot;
+    c.anchor_valid = 0;
+    c.refresh = 0;
+    c.next_refresh = 1e-2;
+}
+
+template <typename T> Fields<T> &fields(rism3d_ctx *ctx);
+template <> Fields<float> &fields<float>(rism3d_ctx *ctx) { return ctx->f32; }
+template <> Fields<double> &fields<double>(rism3d_ctx *ctx) { return ctx->f64; }
+
+rism3d_status to_working(rism3d_ctx *ctx, const double *src, int on_device, int slot) {
+    const long long n = (long long)ctx->nv * ctx->G;
+    const double *dsrc = src;
+    if (!on_device) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->staging, src, n * sizeof(double), cudaMemcpyHostToDevice,
+                                      ctx->stream));
+        dsrc = ctx->staging;
+    }
+    if (ctx->fp32())
+        CUDA_TRY(ctx, launch_from_double<float>(ctx->f32.X + (long long)slot * n, dsrc, n, ctx->stream));
+    else
+        CUDA_TRY(ctx, launch_from_double<double>(ctx->f64.X + (long long)slot * n, dsrc, n, ctx->stream));
+    return RISM3D_OK;
+}
+
+rism3d_status field_out(rism3d_ctx *ctx, int field, int slot, int kind, int order, double *dst,
+                        size_t count, int on_device) {
+    const long long n = field == RISM3D_PHI ? ctx->G : (long long)ctx->nv * ctx->G;
+    if ((long long)count < n) return fail(ctx, RISM3D_EINVAL, "dst holds %zu values, need %lld", count, n);
+    double *d = on_device ? dst : ctx->staging;
+    if (ctx->fp32())
+        CUDA_TRY(ctx, launch_get_field<float>(ctx->f32, field, slot, kind, order, d, ctx->stream));
+    else
+        CUDA_TRY(ctx, launch_get_field<double>(ctx->f64, field, slot, kind, order, d, ctx->stream));
+    if (!on_device)
+        CUDA_TRY(ctx, cudaMemcpyAsync(dst, ctx->staging, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return RISM3D_OK;
+}
+
+bool valid_closure(int kind, int order) {
+    if (kind == kKH || kind == kHNC) return true;
+    return kind == kPSE && order >= 1 && order < kMaxClosureStages;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ public entry points
+extern "C" {
+
+const char *rism3d_version(void) { return "rism3d-gb300 0.1 (sm_103a)"; }
+
+void rism3d_options_default(rism3d_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = 32;
+    opt->mdiis_nvec = 5;
+    opt->mdiis_damp = 0.7;
+    opt->dynamic_damp = 0;
+    opt->max_iter = 10000;
+    opt->check_every = 8;
+    opt->max_atoms = 100000;
+}
+
+rism3d_status rism3d_workspace_bytes(const rism3d_solvent *solvent, const rism3d_grid *grid,
+                                     const rism3d_options *opt, size_t *bytes) {
+    Geometry g{};
+    rism3d_status st = check_inputs(solvent, grid, opt, g);
+    if (st != RISM3D_OK) return st;
+    if (!bytes) return fail(nullptr, RISM3D_EINVAL, "null bytes");
+    *bytes = make_layout(g).total;
+    return RISM3D_OK;
+}
+
+rism3d_status rism3d_create(const rism3d_solvent *sv, const rism3d_grid *gr, const rism3d_options *op,
+                            rism3d_ctx **out) {
+    if (!out) return fail(nullptr, RISM3D_EINVAL, "null out");
+    *out = nullptr;
+    Geometry g{};
+    rism3d_status st = check_inputs(sv, gr, op, g);
+    if (st != RISM3D_OK) return st;
+    Layout L = make_layout(g);
+    if (op->workspace && op->workspace_bytes < L.total)
+        return fail(nullptr, RISM3D_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed",
+                    op->workspace_bytes, L.total);
+    if (op->workspace && (reinterpret_cast<uintptr_t>(op->workspace) & 255))
+        return fail(nullptr, RISM3D_EINVAL, "workspace must be 256-byte aligned");
+
+    rism3d_ctx *ctx = new rism3d_ctx();
+    cudaGetDevice(&ctx->device);
+    ctx->precision = op->precision;
+    ctx->opt = *op;
+    ctx->nv = g.nv;
+    ctx->Nx = g.Nx;
+    ctx->Ny = g.Ny;
+    ctx->Nz = g.Nz;
+    ctx->Kz = g.Kz;
+    ctx->G = g.G;
+    for (int d = 0; d < 3; ++d) {
+        ctx->spacing[d] = gr->spacing[d];
+        ctx->origin[d] = gr->origin[d];
+    }
+    ctx->q.assign(sv->q, sv->q + g.nv);
+    ctx->sig.assign(sv->sigma, sv->sigma + g.nv);
+    ctx->eps.assign(sv->eps, sv->eps + g.nv);
+    ctx->rho.assign(sv->rho, sv->rho + g.nv);
+    ctx->temperature = sv->temperature;
+    ctx->beta = 1.0 / (kKB * sv->temperature);
+    ctx->dV = gr->spacing[0] * gr->spacing[1] * gr->spacing[2];
+    auto bail = [&](rism3d_status s) {
+        g_create_error = ctx->err;
+        rism3d_destroy(ctx);
+        return s;
+    };
+    if (op->cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(op->cuda_stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(fail(ctx, RISM3D_ECUDA, "stream: %s", cudaGetErrorString(e)));
+        ctx->own_stream = true;
+    }
+    if (op->workspace) {
+        ctx->ws = op->workspace;
+        ctx->ws_bytes = op->workspace_bytes;
+    } else {
+        cudaError_t e = cudaMalloc(&ctx->ws, L.total);
+        if (e != cudaSuccess) {
+            ctx->ws = nullptr;
+            return bail(fail(ctx, RISM3D_ENOMEM, "cudaMalloc(%zu): %s", L.total, cudaGetErrorString(e)));
+        }
+        ctx->own_ws = true;
+        ctx->ws_bytes = L.total;
+    }
+    if (cudaMallocHost(reinterpret_cast<void **>(&ctx->ctrl_host), sizeof(Ctrl)) != cudaSuccess) {
+        ctx->ctrl_host = nullptr;
+        return bail(fail(ctx, RISM3D_ENOMEM, "pinned host allocation failed"));
+    }
+    if (op->timing)
+        for (auto &e : ctx->ev_aux)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                e = nullptr;
+                return bail(fail(ctx, RISM3D_ECUDA, "event creation failed"));
+            }
+    char *b = static_cast<char *>(ctx->ws);
+    ctx->ctrl = reinterpret_cast<Ctrl *>(b + L.ctrl);
+    ctx->atoms = reinterpret_cast<double *>(b + L.atoms);
+    ctx->site_sig = reinterpret_cast<double *>(b + L.sites);
+    ctx->site_eps = ctx->site_sig + kMaxSites;
+    ctx->site_q = ctx->site_eps + kMaxSites;
+    ctx->sfe_part = reinterpret_cast<double *>(b + L.sfe);
+    ctx->staging = reinterpret_cast<double *>(b + L.staging);
+    double sites[3 * kMaxSites] = {0};
+    for (int i = 0; i < g.nv; ++i) {
+        sites[i] = ctx->sig[i];
+        sites[kMaxSites + i] = ctx->eps[i];
+        sites[2 * kMaxSites + i] = ctx->q[i];
+    }
+    if (cudaMemcpy(ctx->site_sig, sites, sizeof(sites), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(ctx, RISM3D_ECUDA, "upload of solvent sites failed"));
+    if (ctx->fp32()) {
+        fill_fields<float>(ctx, g, L, ctx->f32);
+        st = upload_tables<float>(ctx, sv, L, ctx->f32);
+    } else {
+        fill_fields<double>(ctx, g, L, ctx->f64);
+        st = upload_tables<double>(ctx, sv, L, ctx->f64);
+    }
+    if (st != RISM3D_OK) return bail(st);
+    Ctrl c;
+    reset_ctrl(ctx, c);
+    c.status = kConverged;       // idle until a solve
+    if (cudaMemcpy(ctx->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(ctx, RISM3D_ECUDA, "upload of the control block failed"));
+    *out = ctx;
+    return RISM3D_OK;
+}
+
+rism3d_status rism3d_set_solute(rism3d_ctx *ctx, int n_atoms, const double *xyz, const double *q,
+                                const double *sigma, const double *eps) {
+    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+    if (n_atoms < 1 || n_atoms > ctx->opt.max_atoms)
+        return fail(ctx, RISM3D_EINVAL, "n_atoms must be in 1..%d", ctx->opt.max_atoms);
+    if (!xyz || !q || !sigma || !eps) return fail(ctx, RISM3D_EINVAL, "null solute array");
+    DeviceGuard dg(ctx->device);
+    const double L[3] = {ctx->Nx * ctx->spacing[0], ctx->Ny * ctx->spacing[1], ctx->Nz * ctx->spacing[2]};
+    ctx->atom_host.assign((size_t)n_atoms * kAtomStride, 0.0);
+    for (int a = 0; a < n_atoms; ++a) {
+        double *at = &ctx->atom_host[(size_t)a * kAtomStride];
+        for (int d = 0; d < 3; ++d) {
+            at[d] = xyz[3 * a + d];
+            at[6 + d] = (xyz[3 * a + d] - ctx->origin[d]) / L[d];
+            if (!std::isfinite(at[d])) return fail(ctx, RISM3D_EINVAL, "atom %d has a non-finite position", a);
+        }
+        at[3] = q[a];
+        at[4] = sigma[a];
+        at[5] = eps[a];
+        if (!(sigma[a] >= 0.0) || !(eps[a] >= 0.0) || !std::isfinite(q[a]))
+            return fail(ctx, RISM3D_EINVAL, "atom %d: sigma, eps must be >= 0 and q finite", a);
+    }
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->atoms, ctx->atom_host.data(), ctx->atom_host.size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+    const double amp0 = 4.0 * kPi * kCoulomb * ctx->beta / ctx->dV;
+    const double P = (double)ctx->nv * ctx->G, sb = ctx->fp32() ? 4.0 : 8.0;
+    const double z = (double)(ctx->Kz + 1) / ctx->Kz;
+    {
+        AuxTimer tm(ctx, 4);
+        if (ctx->fp32())
+            CUDA_TRY(ctx, launch_potential<float>(ctx->f32, ctx->atoms, n_atoms, ctx->site_sig, ctx->site_eps,
+                                                  ctx->site_q, ctx->beta, ctx->origin, ctx->spacing, ctx->stream));
+        else
+            CUDA_TRY(ctx, launch_potential<double>(ctx->f64, ctx->atoms, n_atoms, ctx->site_sig, ctx->site_eps,
+                                                   ctx->site_q, ctx->beta, ctx->origin, ctx->spacing, ctx->stream));
+        tm.stop((P + ctx->G) * sb);
+    }
+    {
+        AuxTimer tm(ctx, 5);
+        if (ctx->fp32())
+            CUDA_TRY(ctx, launch_longrange<float>(ctx->f32, ctx->atoms, n_atoms, amp0, ctx->stream));
+        else
+            CUDA_TRY(ctx, launch_longrange<double>(ctx->f64, ctx->atoms, n_atoms, amp0, ctx->stream));
+        tm.stop(ctx->G * sb * z);
+    }
+    {
+        AuxTimer tm(ctx, 7);
+        if (ctx->fp32())
+            CUDA_TRY(ctx, launch_init_guess<float>(ctx->f32, 0, ctx->stream));
+        else
+            CUDA_TRY(ctx, launch_init_guess<double>(ctx->f64, 0, ctx->stream));
+        tm.stop((P + ctx->G) * sb);
+    }
+    ctx->cur_slot = 0;
+    ctx->has_solute = true;
+    ctx->last_kind = kKH;
+    ctx->last_order = 1;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return RISM3D_OK;
+}
+
+rism3d_status rism3d_set_guess(rism3d_ctx *ctx, const double *t, int on_device) {
+    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+    if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "set_guess before set_solute");
+    if (!t) return fail(ctx, RISM3D_EINVAL, "null t");
+    DeviceGuard dg(ctx->device);
+    ctx->cur_slot = 0;
+    rism3d_status st = to_working(ctx, t, on_device, 0);
+    if (st != RISM3D_OK) return st;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return RISM3D_OK;
+}
+
+rism3d_status rism3d_solve(rism3d_ctx *ctx, int closure, int pse_order, double tol, rism3d_report *rep) {
+    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+    if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "solve before set_solute");
+    if (!valid_closure(closure, pse_order)) return fail(ctx, RISM3D_EINVAL, "bad closure %d / order %d", closure, pse_order);
+    if (!(tol > 0.0)) return fail(ctx, RISM3D_EINVAL, "tol must be positive");
+    DeviceGuard dg(ctx->device);
+    auto t0 = std::chrono::steady_clock::now();
+    rism3d_status st = build_graph(ctx);
+    if (st != RISM3D_OK) return st;
+    Ctrl &c = *ctx->ctrl_host;
+    reset_ctrl(ctx, c);
+    closure_stages(closure, pse_order, tol, c);
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, ctx->stream));
+    const int K = ctx->opt.check_every;
+    int iter_before = 0;
+    for (;;) {
+        CUDA_TRY(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(&c, ctx->ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        const int ran = c.iter - iter_before;
+        iter_before = c.iter;
+        for (int k = 0; k < 4; ++k) ctx->stats.launches[k] += K;
+        if (ctx->opt.timing) {
+            for (int i = 0; i < ran && i < K; ++i)
+                for (int k = 0; k < 4; ++k) {
+                    float ms = 0.f;
+                    CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev[(size_t)i * 5 + k], ctx->ev[(size_t)i * 5 + k + 1]));
+                    ctx->stats.ms[k] += ms;
+                    ctx->stats.timed[k] += 1;
+                }
+        }
+        if (c.status != kRunning) break;
+    }
+    CUDA_TRY(ctx, cudaMemcpyAsync(&c, ctx->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    auto t1 = std::chrono::steady_clock::now();
+    account_iterations(ctx, c);
+    ctx->stats.solves += 1;
+    ctx->cur_slot = c.cur;
+    ctx->last_kind = closure;
+    ctx->last_order = closure == kPSE ? pse_order : (closure == kKH ? 1 : 0);
+    if (rep) {
+        rep->iterations = c.iter;
+        rep->converged = c.status == kConverged;
+        rep->rms_residual = c.rms;
+        rep->seconds_iter = std::chrono::duration<double>(t1 - t0).count();
+    }
+    if (c.status == kDiverged) return fail(ctx, RISM3D_EDIVERGED, "non-finite residual at iteration %d", c.iter);
+    if (c.status == kMaxIter)
+        return fail(ctx, RISM3D_ENOTCONV, "not converged after %d iterations (rms %.3e)", c.iter, c.rms);
+    return RISM3D_OK;
+}
+
+rism3d_status rism3d_residual(rism3d_ctx *ctx, int closure, int pse_order, const double *t, double *R,
+                              int on_device) {
+    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+    if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "residual before set_solute");
+    if (!valid_closure(closure, pse_order)) return fail(ctx, RISM3D_EINVAL, "bad closure");
+    if (!t || !R) return fail(ctx, RISM3D_EINVAL, "null t or R");
+    DeviceGuard dg(ctx->device);
+    ctx->cur_slot = 0;
+    rism3d_status st = to_working(ctx, t, on_device, 0);
+    if (st != RISM3D_OK) return st;
+    Ctrl &c = *ctx->ctrl_host;
+    reset_ctrl(ctx, c);
+    c.n_stages = 1;
+    c.stage_kind[0] = closure;
+    c.stage_order[0] = closure == kPSE ? pse_order : (closure == kKH ? 1 : 0);
+    c.stage_tol[0] = 0.0;
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, ctx->stream));
+    st = iteration(ctx, false);
+    if (st != RISM3D_OK) return st;
+    for (int kk = 0; kk < 3; ++kk) ctx->stats.launches[kk] += 1;
+    const int k = c.stage_kind[0], o = c.stage_order[0];
+    st = field_out(ctx, RISM3D_R, 0, k, o, R, (size_t)ctx->nv * ctx->G, on_device);
+    // leave the device idle
+    c.status = kConverged;
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ctrl, &c, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return st;
+}
+
+rism3d_status rism3d_get(rism3d_ctx *ctx, int field, double *dst, size_t count, int on_device) {
+    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+    if (field < RISM3D_G || field > RISM3D_R) return fail(ctx, RISM3D_EINVAL, "bad field %d", field);
+    if (!dst) return fail(ctx, RISM3D_EINVAL, "null dst");
+    if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "get before set_solute");
+    DeviceGuard dg(ctx->device);
+    return field_out(ctx, field, ctx->cur_slot, ctx->last_kind, ctx->last_order, dst, count, on_device);
+}
+
+rism3d_status rism3d_get_sfe(rism3d_ctx *ctx, int kind, int pse_order, double *total, double *per_site) {
+    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+    if (kind < RISM3D_SFE_KH || kind > RISM3D_SFE_PSE) return fail(ctx, RISM3D_EINVAL, "bad SFE kind %d", kind);
+    if (kind == RISM3D_SFE_PSE && pse_order < 1) return fail(ctx, RISM3D_EINVAL, "PSE order must be >= 1");
+    if (!total) return fail(ctx, RISM3D_EINVAL, "null total");
+    if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "get_sfe before set_solute");
+    DeviceGuard dg(ctx->device);
+    {
+        AuxTimer tm(ctx, 6);
+        if (ctx->fp32())
+            CUDA_TRY(ctx, launch_sfe<float>(ctx->f32, ctx->cur_slot, ctx->last_kind, ctx->last_order, kind,
+                                            pse_order, ctx->sfe_part, kSfeBlocksPerSite, ctx->stream));
+        else
+            CUDA_TRY(ctx, launch_sfe<double>(ctx->f64, ctx->cur_slot, ctx->last_kind, ctx->last_order, kind,
+                                             pse_order, ctx->sfe_part, kSfeBlocksPerSite, ctx->stream));
+        tm.stop(2.0 * ctx->nv * ctx->G * (ctx->fp32() ? 4.0 : 8.0));
+    }
+    std::vector<double> part((size_t)ctx->nv * kSfeBlocksPerSite);
+    CUDA_TRY(ctx, cudaMemcpyAsync(part.data(), ctx->sfe_part, part.size() * sizeof(double),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    const double kT = kKB * ctx->temperature;
+    double tot = 0.0;
+    for (int g = 0; g < ctx->nv; ++g) {
+        double s = 0.0;
+        for (int b = 0; b < kSfeBlocksPerSite; ++b) s += part[(size_t)g * kSfeBlocksPerSite + b];
+        const double v = kT * ctx->rho[g] * ctx->dV * s;
+        if (per_site) per_site[g] = v;
+        tot += v;
+    }
+    *total = tot;
+    return RISM3D_OK;
+}
+
+rism3d_status rism3d_get_stats(const rism3d_ctx *ctx, rism3d_stats *out) {
+    if (!ctx || !out) return fail(nullptr, RISM3D_EINVAL, "null context or stats");
+    *out = ctx->stats;
+    return RISM3D_OK;
+}
+
+rism3d_status rism3d_reset_stats(rism3d_ctx *ctx) {
+    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+    std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+    return RISM3D_OK;
+}
+
+const char *rism3d_last_error(const rism3d_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+void rism3d_destroy(rism3d_ctx *ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard dg(ctx->device);
+        if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+        if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+        for (auto e : ctx->ev)
+            if (e) cudaEventDestroy(e);
+        for (auto e : ctx->ev_aux)
+            if (e) cudaEventDestroy(e);
+        if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
+        if (ctx->ctrl_host) cudaFreeHost(ctx->ctrl_host);
+        if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    }
+    delete ctx;
+}
+
+}  // extern "C"

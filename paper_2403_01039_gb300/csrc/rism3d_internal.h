@@ -1,0 +1,134 @@
+// Internal declarations shared by the kernels (rism3d_kernels.cu) and the host layer
+// (rism3d_capi.cu). Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rism {
+
+constexpr int kMaxSites = 8;      // solvent sites n_v
+constexpr int kMaxHist = 16;      // MDIIS vectors M
+constexpr int kMaxRadixStages = 10;
+constexpr int kMaxClosureStages = 12;
+constexpr int kThreadsPlane = 512;
+constexpr int kThreadsPencil = 256;
+
+// Solver status words written by the device (Ctrl::status).
+enum { kRunning = 0, kConverged = 1, kDiverged = 2, kMaxIter = 3 };
+enum { kKH = 1, kHNC = 2, kPSE = 3 };
+
+// Mixed-radix plan of one transform length: L = prod(radix[0..nst)).
+struct FftPlan {
+    int L;
+    int nst;
+    int radix[kMaxRadixStages];
+};
+
+// Device-resident solver state. The iteration kernels read it on every launch, so one
+// captured CUDA graph serves every iteration; the MDIIS kernel rewrites it.
+struct Ctrl {
+    int status;
+    int iter;                       // iterations done (all stages)
+    int max_iter;
+    int n_stages;
+    int stage;
+    int stage_kind[kMaxClosureStages];
+    int stage_order[kMaxClosureStages];
+    double stage_tol[kMaxClosureStages];
+    int M;                          // history capacity
+    int dynamic;
+    double damp;
+    double inv_count;               // 1 / (n_v * Nx * Ny * Nz)
+    int n_partials;                 // blocks that wrote Gram partials
+    // iterate bookkeeping
+    int cur;                        // ring slot of the current input t (and its R)
+    int do_update;                  // plane_fwd forms t = sum c_i (X_i + eta R_i) into slot cur
+    int upd_n;
+    int upd_slot[kMaxHist];
+    double upd_coef[kMaxHist];
+    double eta;
+    int hist_n;                     // history slots (oldest first) paired with R_cur in the Gram
+    int hist_slot[kMaxHist];
+    double rms;                     // RMS of the last residual
+    // defect-correction anchor: h = h_a + L(c^sr - c^sr_a) with L the linear map of
+    // steps 3-5; refreshed (c^sr_a = c^sr, h_a = h) whenever the RMS falls below next_refresh
+    int anchor_valid;
+    int refresh;
+    double next_refresh;
+    // work counters for the byte model, summed over the iterations that ran
+    long long acc_iters;
+    long long acc_fwd_units;        // fields read + written by plane_fwd's t (update or load)
+    long long acc_hist;             // history residuals read by plane_inv
+    long long acc_anchor;           // iterations that read the anchor (plane_fwd and plane_inv)
+    long long acc_refresh;          // iterations that wrote the anchor
+    long long acc_psi;              // iterations whose pencil pass read Psi
+    double B[kMaxHist * kMaxHist];  // Gram matrix indexed by ring slot
+};
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { typedef float2 type; };
+template <> struct Cx<double> { typedef double2 type; };
+
+// Everything one iteration kernel needs, passed by value.
+template <typename T>
+struct Fields {
+    typedef typename Cx<T>::type C;
+    int nv, Nx, Ny, Nz, Kz;         // Kz = Nz / 2
+    long long G;                    // Nx * Ny * Nz
+    long long specN;                // Nx * Ny * Kz complex values per site (kz < Kz)
+    T *bu;                          // [nv][G] beta * u
+    T *phi;                         // [G] long-range field phi (f_g = beta q_g phi)
+    C *psi, *psi_nyq;               // beta Phi~ / dV on [Nx][Ny][Kz] and the kz = Kz plane [Nx][Ny]
+    C *spec, *spec_nyq;             // [nv][Nx][Ny][Kz], [nv][Nx][Ny]
+    T *X, *R;                       // ring [M][nv][G]
+    T *csr_a, *h_a;                 // anchor fields [nv][G]
+    T *table;                       // [nk][nv + 1][nv]: X_ag / G and the charge row -Q_g / G
+    int nk;
+    double inv_dk;
+    C *tw_x, *tw_y, *tw_h, *tw_z;   // exp(-2 pi i m / L) for L = Nx, Ny, Kz, Nz
+    FftPlan px, py, ph;
+    int chunk_rows, chunk_cols_fwd, chunk_x;   // batch chunk sizes of the in-place FFTs
+    int pitch;                      // complex row pitch of a plane in shared memory
+    int W;                          // columns per pencil tile
+    int tiles_main, tiles_nyq;
+    int pencil_pitch;
+    double bq[kMaxSites];           // beta * q_gamma
+    double ks[3];                   // 2 pi / (N d) per axis
+    double *partials;               // [nv * Nx][kMaxHist + 1]
+    Ctrl *ctrl;
+};
+
+// ---- launchers (explicitly instantiated for float and double) ----
+// Sets the dynamic shared-memory limits of the iteration kernels; call before launching or
+// capturing them.
+template <typename T> cudaError_t prepare_kernels(const Fields<T> &f);
+template <typename T> size_t plane_smem_bytes(const Fields<T> &f);
+template <typename T> size_t pencil_smem_bytes(const Fields<T> &f);
+template <typename T> cudaError_t launch_plane_fwd(const Fields<T> &f, cudaStream_t s);
+template <typename T> cudaError_t launch_pencil(const Fields<T> &f, cudaStream_t s);
+template <typename T> cudaError_t launch_plane_inv(const Fields<T> &f, cudaStream_t s);
+template <typename T> cudaError_t launch_mdiis(const Fields<T> &f, cudaStream_t s);
+// atoms: [n][8] doubles: x, y, z (absolute), q, sigma, eps, ux, uy, uz with u = (R - r0) / L
+template <typename T>
+cudaError_t launch_potential(const Fields<T> &f, const double *atoms, int n_atoms,
+                             const double *site_sig, const double *site_eps, const double *site_q,
+                             double beta, const double *origin, const double *spacing,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_longrange(const Fields<T> &f, const double *atoms, int n_atoms, double amp0,
+                             cudaStream_t s);
+template <typename T> cudaError_t launch_init_guess(const Fields<T> &f, int slot, cudaStream_t s);
+template <typename T>
+cudaError_t launch_from_double(T *dst, const double *src, long long n, cudaStream_t s);
+// field: 1 g, 2 c, 3 h, 4 t, 5 beta u, 6 phi, 7 R
+template <typename T>
+cudaError_t launch_get_field(const Fields<T> &f, int field, int slot, int kind, int order,
+                             double *dst, cudaStream_t s);
+template <typename T>
+cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sfe_kind,
+                       int sfe_order, double *partials, int blocks_per_site, cudaStream_t s);
+
+constexpr int kSfeBlocksPerSite = 152;
+constexpr size_t kAtomStride = 9;
+
+}  // namespace rism

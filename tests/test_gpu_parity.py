@@ -1,0 +1,252 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: FP64 path max|dg| <= 1e-6 and |dSFE| <= 1e-4 kcal/mol against the oracle run with the
+same algorithm and tolerance; FP32 path max|dg| <= 1e-3 and |dSFE| <= 0.05 kcal/mol against
+the oracle converged to 1e-10. Element-wise checks of single steps use tolerances derived
+from the working precision (see each test)."""
+import os
+
+import numpy as np
+import pytest
+
+from conftest import GOLDEN
+from oracle import rism3d as orc, closure as cl
+from paper_2403_01039_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2403_01039_gb300 import build, capi  # noqa: E402
+
+build.build()
+
+
+def solver(solv, grid, precision=64, **kw):
+    return capi.Solver(solv, grid, precision=precision, **kw)
+
+
+def charged_solute(n_atoms=8, radius=3.0, seed=11, net=1.0):
+    return synth.random_solute(n_atoms, radius, seed, net_charge=net)
+
+
+GRIDS = [
+    dict(n=(32, 32, 32), spacing=(0.5, 0.5, 0.5), origin=(-8.0, -8.0, -8.0)),
+    # ragged tiles (Kz = 15, Ny = 20), radices 3 and 5, anisotropic spacing
+    dict(n=(24, 20, 30), spacing=(0.55, 0.6, 0.5), origin=(-6.6, -6.0, -7.5)),
+    dict(n=(40, 36, 48), spacing=(0.45, 0.5, 0.4), origin=(-9.0, -9.0, -9.6)),
+]
+
+
+# ------------------------------------------------------------------ potential builder
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("gi", [0, 1])
+def test_potential_and_long_range_field(water_nacl, precision, gi):
+    grid = GRIDS[gi]
+    sol = charged_solute()
+    P = orc.Problem(water_nacl, grid, sol)
+    with solver(water_nacl, grid, precision) as S:
+        S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+        bu = S.get("u")
+        phi = S.get("phi")
+        t0 = S.get("t")
+    if precision == 64:
+        assert np.max(np.abs(bu - P.bu) / np.maximum(1.0, np.abs(P.bu))) < 1e-11
+        assert np.max(np.abs(phi - P.phi)) < 1e-10 * np.max(np.abs(P.phi))
+        assert np.max(np.abs(t0 - P.f)) < 1e-10 * np.max(np.abs(P.f))
+    else:
+        # FP32 Lennard-Jones terms: where LJ repulsion and Coulomb attraction cancel near a
+        # charged atom (beta*u ~ 30 from terms of ~1e3) the rounding of the position
+        # differences shows; there g = exp(-beta*u) < 1e-13, so judge the Boltzmann factor
+        m = P.bu < 20.0
+        assert np.max(np.abs(bu - P.bu)[m] / np.maximum(1.0, np.abs(P.bu[m]))) < 1e-5
+        assert np.max(np.abs(np.exp(-bu) - np.exp(-P.bu))) < 1e-5
+        assert np.max(np.abs(phi - P.phi)) < 1e-5 * np.max(np.abs(P.phi))
+
+
+# ------------------------------------------------------------------ steps 2-5 element-wise
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("gi", [0, 1, 2])
+@pytest.mark.parametrize("closure,order", [("kh", 1), ("pse", 3), ("hnc", 0)])
+def test_residual_elementwise(water_nacl, precision, gi, closure, order):
+    grid = GRIDS[gi]
+    sol = charged_solute()
+    P = orc.Problem(water_nacl, grid, sol)
+    rng = np.random.default_rng(gi * 7 + order)
+    t = P.f + 0.3 * rng.standard_normal(P.f.shape)
+    kind = {"kh": cl.KH, "pse": cl.PSE, "hnc": cl.HNC}[closure]
+    if closure == "hnc":
+        t = np.minimum(t, P.bu + 5.0)          # keep exp(d) finite in FP32
+    ref, g, _ = P.residual(t, kind, max(order, 1))
+    with solver(water_nacl, grid, precision) as S:
+        S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+        got = S.residual(t, closure, max(order, 1))
+    scale = max(1.0, float(np.max(np.abs(g))), float(np.max(np.abs(ref))))
+    err = float(np.max(np.abs(got - ref)))
+    # FP64: rounding of ~log2(N^3) FFT stages; FP32: the same at 6e-8 unit roundoff
+    assert err < (1e-10 if precision == 64 else 2e-4) * scale, (err, scale)
+
+
+def test_residual_device_pointers(water3):
+    grid = GRIDS[0]
+    P = orc.Problem(water3, grid, synth.lj_sphere())
+    t = np.random.default_rng(3).standard_normal(P.bu.shape) * 0.2
+    with solver(water3, grid, 64) as S:
+        S.set_solute(np.zeros((1, 3)), [0.0], [3.73], [0.294])
+        host = S.residual(t)
+        dev = S.residual(torch.from_numpy(t).cuda())
+        g_dev = torch.empty(S.field_shape, dtype=torch.float64, device="cuda")
+        S.get("g", out=g_dev)
+        g_host = S.get("g")
+    assert np.array_equal(host, dev.cpu().numpy())
+    assert np.array_equal(g_host, g_dev.cpu().numpy())
+
+
+# ------------------------------------------------------------------ whole solves
+def _oracle(solv, grid, solute, kind, order, tol, M=5):
+    P = orc.Problem(solv, grid, solute)
+    s = orc.solve(P, kind, order, tol=tol, mdiis_nvec=M)
+    return P, s
+
+
+def _sfe_kind(kind):
+    return {cl.KH: "kh", cl.HNC: "hnc", cl.PSE: "pse"}[kind]
+
+
+@pytest.mark.parametrize("kind,order", [(cl.KH, 1), (cl.HNC, 0)])
+def test_solve_fp64_sphere_32(water3, kind, order):
+    """32^3 LJ sphere in 3-site water, MDIIS 5, tol 1e-6, FP64 (KH: the sphere_32 workload)."""
+    grid = synth.cubic_grid(32, 0.5)
+    P, ref = _oracle(water3, grid, synth.lj_sphere(), kind, order, 1e-6)
+    name = _sfe_kind(kind)
+    with solver(water3, grid, 64) as S:
+        S.set_solute(np.zeros((1, 3)), [0.0], [3.73], [0.294])
+        rep = S.solve(name, tol=1e-6)
+        g = S.get("g")
+        c = S.get("c")
+        sfe, per = S.sfe(name)
+        gf, _ = S.sfe("gf")
+    assert rep["converged"] and abs(rep["iterations"] - ref["iterations"]) <= 1
+    assert np.max(np.abs(g - ref["g"])) <= 1e-6
+    assert np.max(np.abs(c - ref["c"])) <= 1e-6
+    sk = {cl.KH: cl.SFE_KH, cl.HNC: cl.SFE_HNC}[kind]
+    assert abs(sfe - orc.sfe(P, ref, sk)[0]) <= 1e-4
+    assert abs(gf - orc.sfe(P, ref, cl.SFE_GF)[0]) <= 1e-4
+
+
+@pytest.mark.parametrize("kind,order", [(cl.KH, 1), (cl.PSE, 3)])
+def test_solve_fp64_charged(water_nacl, kind, order):
+    """Charged 8-atom solute in water + NaCl (long-range path), 32^3, tol 1e-6, FP64."""
+    grid = GRIDS[0]
+    sol = charged_solute()
+    P, ref = _oracle(water_nacl, grid, sol, kind, order, 1e-6)
+    assert ref["converged"]
+    with solver(water_nacl, grid, 64) as S:
+        S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+        rep = S.solve(_sfe_kind(kind), pse_order=order, tol=1e-6)
+        g = S.get("g")
+        sfe, _ = S.sfe(_sfe_kind(kind), order)
+    assert rep["converged"]
+    assert abs(rep["iterations"] - ref["iterations"]) <= 2
+    assert np.max(np.abs(g - ref["g"])) <= 1e-6
+    sref = orc.sfe(P, ref, {cl.KH: cl.SFE_KH, cl.HNC: cl.SFE_HNC, cl.PSE: cl.SFE_PSE}[kind], order)[0]
+    assert abs(sfe - sref) <= 1e-4
+
+
+@pytest.mark.parametrize("kind,order", [(cl.KH, 1), (cl.PSE, 3)])
+def test_solve_fp32_charged(water_nacl, kind, order):
+    """FP32 form against the oracle converged to 1e-10."""
+    grid = GRIDS[2]
+    sol = charged_solute()
+    P, ref = _oracle(water_nacl, grid, sol, kind, order, 1e-10)
+    with solver(water_nacl, grid, 32) as S:
+        S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+        rep = S.solve(_sfe_kind(kind), pse_order=order, tol=1e-6)
+        g = S.get("g")
+        c = S.get("c")
+        sfe, _ = S.sfe(_sfe_kind(kind), order)
+    assert rep["converged"]
+    assert np.max(np.abs(g - ref["g"])) <= 1e-3
+    sref = orc.sfe(P, ref, {cl.KH: cl.SFE_KH, cl.PSE: cl.SFE_PSE}[kind], order)[0]
+    assert abs(sfe - sref) <= 0.05
+    assert np.isfinite(c).all()
+
+
+# ------------------------------------------------------------------ full size (sampled)
+@pytest.fixture(scope="module")
+def c2_ref():
+    path = os.path.join(GOLDEN, "solute50_128_reference.npz")
+    if not os.path.exists(path):
+        pytest.skip("full-size reference not generated")
+    return np.load(path)
+
+
+@pytest.mark.parametrize("precision,tag,order", [(32, "kh", 1), (64, "kh", 1), (32, "pse3", 3)])
+def test_full_size_solute50_128(water_nacl, c2_ref, precision, tag, order):
+    """50-atom solute, water + 0.1 M NaCl, 128^3 at 0.5 A: the launch configuration bench.py
+    times. FP64 is compared with the oracle at the same tolerance (1e-6), FP32 with the
+    oracle at 1e-10, on 1024 seeded grid points (all sites) and the SFE."""
+    key_ref = "%s_%g" % (tag, 1e-6 if precision == 64 else 1e-10)
+    if key_ref + "_g" not in c2_ref:
+        pytest.skip("reference for %s missing" % key_ref)
+    w = synth.WORKLOADS["solute50_128"]
+    sol = synth.workload_solute("solute50_128")
+    grid = synth.cubic_grid(w["n"], w["spacing"])
+    pts = c2_ref["points"]
+    closure = "kh" if tag == "kh" else "pse"
+    with solver(water_nacl, grid, precision, mdiis_nvec=w["mdiis_nvec"]) as S:
+        S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+        rep = S.solve(closure, pse_order=3, tol=1e-6)
+        g = S.get("g")
+        sfe, _ = S.sfe(closure, 3)
+    gs = g[:, pts[:, 0], pts[:, 1], pts[:, 2]]
+    dg = float(np.max(np.abs(gs - c2_ref[key_ref + "_g"])))
+    dsfe = abs(sfe - float(c2_ref[key_ref + "_sfe"]))
+    if precision == 64:
+        assert dg <= 1e-6 and dsfe <= 1e-4, (dg, dsfe)
+    else:
+        assert dg <= 1e-3 and dsfe <= 0.05, (dg, dsfe)
+    assert rep["converged"]
+
+
+# ------------------------------------------------------------------ edge cases
+def test_zero_potential_is_exact(water3):
+    grid = synth.cubic_grid(16, 0.5)
+    with solver(water3, grid, 64) as S:
+        S.set_solute(np.zeros((1, 3)), [0.0], [1.0], [0.0])
+        rep = S.solve("kh", tol=1e-12)
+        g, t, c = S.get("g"), S.get("t"), S.get("c")
+        sfe, _ = S.sfe("kh")
+    assert rep["converged"] and rep["iterations"] == 1
+    assert np.all(g == 1.0) and np.all(t == 0.0) and np.all(c == 0.0) and sfe == 0.0
+
+
+def test_not_converged_and_diverged(water3):
+    grid = synth.cubic_grid(16, 0.5)
+    with solver(water3, grid, 64, max_iter=3) as S:
+        with pytest.raises(capi.RismError) as e:
+            S.solve("kh")
+        assert e.value.status == capi.ESTATE
+        S.set_solute(np.zeros((1, 3)), [0.0], [3.73], [0.294])
+        rep = S.solve("kh", tol=1e-12, check=False)
+        assert rep["status"] == capi.ENOTCONV and rep["iterations"] == 3
+        assert np.isfinite(S.get("g")).all()
+        bad = np.zeros(S.field_shape)
+        bad[0, 3, 4, 5] = np.nan
+        S.set_guess(bad)
+        rep = S.solve("kh", check=False)
+        assert rep["status"] == capi.EDIVERGED
+
+
+def test_bitwise_reproducible(water_nacl):
+    grid = GRIDS[1]
+    sol = charged_solute()
+    out = []
+    for _ in range(2):
+        with solver(water_nacl, grid, 32) as S:
+            S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+            S.solve("kh", tol=1e-6)
+            out.append(S.get("g"))
+    assert np.array_equal(out[0], out[1])
