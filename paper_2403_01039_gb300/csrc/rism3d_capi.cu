@@ -154,7 +154,7 @@ static rism3d_status fail(rism3d_ctx *ctx, rism3d_status st, const char *fmt, ..
 namespace {
 
 struct Layout {
-    size_t ctrl, bu, phi, psi, spec, X, R, anchor, table, tw, partials, sfe, atoms, sites, staging, total;
+    size_t ctrl, bu, phi, w, psi, spec, X, R, anchor, table, tw, partials, sfe, atoms, sites, staging, total;
 };
 
 struct Geometry {
@@ -178,6 +178,7 @@ Layout make_layout(const Geometry &g) {
     L.ctrl = take(sizeof(Ctrl));
     L.bu = take((size_t)g.nv * g.G * g.s);
     L.phi = take((size_t)g.G * g.s);
+    L.w = take((size_t)g.nv * g.G * g.s);
     L.psi = take(specN * c);
     L.spec = take((size_t)g.nv * specN * c);
     L.X = take((size_t)g.M * g.nv * g.G * g.s);
@@ -274,6 +275,7 @@ void fill_fields(rism3d_ctx *ctx, const Geometry &g, const Layout &L, Fields<T> 
     f.specN = (long long)g.Nx * g.Ny * g.Kz;
     f.bu = reinterpret_cast<T *>(b + L.bu);
     f.phi = reinterpret_cast<T *>(b + L.phi);
+    f.w = reinterpret_cast<T *>(b + L.w);
     f.psi = reinterpret_cast<C *>(b + L.psi);
     f.psi_nyq = f.psi + f.specN;
     f.spec = reinterpret_cast<C *>(b + L.spec);
@@ -393,18 +395,18 @@ rism3d_status iteration(rism3d_ctx *ctx, bool with_mdiis) {
 
 // Algorithmic HBM bytes of the iterations that ran (from the device counters): per
 // site-point (P = n_v Nx Ny Nz of them, s bytes per real, z = (Kz + 1) / Kz for the half
-// spectrum) plane_fwd moves the history it combines (2 per stored pair + 1 for t, or 1 to
-// load t), beta*u (1), phi (1/n_v), the spectrum it writes (z) and the anchor (1 read, 1
-// write on refresh); pencil reads and writes the spectrum (2 z) plus Psi (z/n_v) until the
-// first anchor; plane_inv reads the spectrum (z), t and beta*u (2), the history residuals,
-// the anchor h_a, and writes R (1) and h_a on refresh.
+// spectrum) plane_fwd moves the history it combines (2 per stored pair + 1 for tau, or 1
+// to load tau), w (1), the spectrum it writes (z) and the anchor (1 read, 1 write on
+// refresh); pencil reads and writes the spectrum (2 z) plus Psi (z/n_v) until the first
+// anchor; plane_inv reads the spectrum (z), tau and w (2), the history residuals, the
+// anchor h_a, and writes R (1) and h_a on refresh.
 void account_iterations(rism3d_ctx *ctx, const Ctrl &c) {
     const double P = (double)ctx->nv * (double)ctx->G;
     const double s = ctx->fp32() ? 4.0 : 8.0;
     const double z = (double)(ctx->Kz + 1) / (double)ctx->Kz;
     const double it = (double)c.acc_iters;
     ctx->stats.iterations += c.acc_iters;
-    ctx->stats.bytes[0] += P * s * ((double)c.acc_fwd_units + it * (1.0 + 1.0 / ctx->nv + z) +
+    ctx->stats.bytes[0] += P * s * ((double)c.acc_fwd_units + it * (1.0 + z) +
                                     (double)c.acc_anchor + (double)c.acc_refresh);
     ctx->stats.bytes[1] += P * s * z * (2.0 * it + (double)c.acc_psi / ctx->nv);
     ctx->stats.bytes[2] += P * s * (it * (z + 3.0) + (double)c.acc_hist + (double)c.acc_anchor +
@@ -436,15 +438,17 @@ struct AuxTimer {
 
 template <typename T>
 rism3d_status timed_iteration(rism3d_ctx *ctx, const Fields<T> &f, cudaEvent_t *e) {
-    CUDA_TRY(ctx, cudaEventRecord(e[0], ctx->stream));
+    // external records: captured into the graph as event-record nodes that time each kernel
+    const unsigned x = cudaEventRecordExternal;
+    CUDA_TRY(ctx, cudaEventRecordWithFlags(e[0], ctx->stream, x));
     CUDA_TRY(ctx, launch_plane_fwd<T>(f, ctx->stream));
-    CUDA_TRY(ctx, cudaEventRecord(e[1], ctx->stream));
+    CUDA_TRY(ctx, cudaEventRecordWithFlags(e[1], ctx->stream, x));
     CUDA_TRY(ctx, launch_pencil<T>(f, ctx->stream));
-    CUDA_TRY(ctx, cudaEventRecord(e[2], ctx->stream));
+    CUDA_TRY(ctx, cudaEventRecordWithFlags(e[2], ctx->stream, x));
     CUDA_TRY(ctx, launch_plane_inv<T>(f, ctx->stream));
-    CUDA_TRY(ctx, cudaEventRecord(e[3], ctx->stream));
+    CUDA_TRY(ctx, cudaEventRecordWithFlags(e[3], ctx->stream, x));
     CUDA_TRY(ctx, launch_mdiis<T>(f, ctx->stream));
-    CUDA_TRY(ctx, cudaEventRecord(e[4], ctx->stream));
+    CUDA_TRY(ctx, cudaEventRecordWithFlags(e[4], ctx->stream, x));
     return RISM3D_OK;
 }
 
@@ -507,9 +511,9 @@ rism3d_status to_working(rism3d_ctx *ctx, const double *src, int on_device, int 
         dsrc = ctx->staging;
     }
     if (ctx->fp32())
-        CUDA_TRY(ctx, launch_from_double<float>(ctx->f32.X + (long long)slot * n, dsrc, n, ctx->stream));
+        CUDA_TRY(ctx, launch_guess_from_t<float>(ctx->f32, slot, dsrc, ctx->stream));
     else
-        CUDA_TRY(ctx, launch_from_double<double>(ctx->f64.X + (long long)slot * n, dsrc, n, ctx->stream));
+        CUDA_TRY(ctx, launch_guess_from_t<double>(ctx->f64, slot, dsrc, ctx->stream));
     return RISM3D_OK;
 }
 
@@ -700,7 +704,7 @@ rism3d_status rism3d_set_solute(rism3d_ctx *ctx, int n_atoms, const double *xyz,
         else
             CUDA_TRY(ctx, launch_potential<double>(ctx->f64, ctx->atoms, n_atoms, ctx->site_sig, ctx->site_eps,
                                                    ctx->site_q, ctx->beta, ctx->origin, ctx->spacing, ctx->stream));
-        tm.stop((P + ctx->G) * sb);
+        tm.stop((2.0 * P + ctx->G) * sb);
     }
     {
         AuxTimer tm(ctx, 5);
@@ -716,7 +720,7 @@ rism3d_status rism3d_set_solute(rism3d_ctx *ctx, int n_atoms, const double *xyz,
             CUDA_TRY(ctx, launch_init_guess<float>(ctx->f32, 0, ctx->stream));
         else
             CUDA_TRY(ctx, launch_init_guess<double>(ctx->f64, 0, ctx->stream));
-        tm.stop((P + ctx->G) * sb);
+        tm.stop(P * sb);
     }
     ctx->cur_slot = 0;
     ctx->has_solute = true;

@@ -76,11 +76,12 @@ struct Fields {
     int nv, Nx, Ny, Nz, Kz;         // Kz = Nz / 2
     long long G;                    // Nx * Ny * Nz
     long long specN;                // Nx * Ny * Kz complex values per site (kz < Kz)
-    T *bu;                          // [nv][G] beta * u
+    T *bu;                          // [nv][G] beta * u (outputs and SFE)
     T *phi;                         // [G] long-range field phi (f_g = beta q_g phi)
+    T *w;                           // [nv][G] f - beta*u; the iteration uses d = w + tau
     C *psi, *psi_nyq;               // beta Phi~ / dV on [Nx][Ny][Kz] and the kz = Kz plane [Nx][Ny]
     C *spec, *spec_nyq;             // [nv][Nx][Ny][Kz], [nv][Nx][Ny]
-    T *X, *R;                       // ring [M][nv][G]
+    T *X, *R;                       // ring [M][nv][G]: X holds tau = t - f, R the residual
     T *csr_a, *h_a;                 // anchor fields [nv][G]
     T *table;                       // [nk][nv + 1][nv]: X_ag / G and the charge row -Q_g / G
     int nk;
@@ -119,7 +120,7 @@ cudaError_t launch_longrange(const Fields<T> &f, const double *atoms, int n_atom
                              cudaStream_t s);
 template <typename T> cudaError_t launch_init_guess(const Fields<T> &f, int slot, cudaStream_t s);
 template <typename T>
-cudaError_t launch_from_double(T *dst, const double *src, long long n, cudaStream_t s);
+cudaError_t launch_guess_from_t(const Fields<T> &f, int slot, const double *src, cudaStream_t s);
 // field: 1 g, 2 c, 3 h, 4 t, 5 beta u, 6 phi, 7 R
 template <typename T>
 cudaError_t launch_get_field(const Fields<T> &f, int field, int slot, int kind, int order,

@@ -12,6 +12,11 @@
 //
 // Every field stays in HBM between launches; the solver state lives in a device struct
 // (Ctrl) so that one captured CUDA graph replays any number of iterations.
+//
+// The iterate is stored as tau = t - f (f = beta q phi of Eq. 29) and the potential as
+// w = f - beta*u, so that d = -beta*u + t = w + tau and c^sr = g - 1 - t + f = g - 1 - tau
+// (Eq. 31) without the large long-range parts of t and beta*u; since the MDIIS weights sum
+// to one, iterating on tau is the same iteration as on t.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -251,9 +256,7 @@ k_plane_fwd(Fields<T> f) {
         }
     }
     T *tcur = f.X + (long long)cur * ring + siteoff;
-    const T *bu = f.bu + siteoff;
-    const T *phi = f.phi + (long long)x * Ny * f.Nz;
-    const T bq = (T)f.bq[gam];
+    const T *wp = f.w + siteoff;
     const int anchor = ctl->anchor_valid, refresh = ctl->refresh;
     T *ca = f.csr_a + siteoff;
 
@@ -279,13 +282,12 @@ k_plane_fwd(Fields<T> f) {
         } else {
             t = *reinterpret_cast<const V2 *>(tcur + o);
         }
-        V2 u = *reinterpret_cast<const V2 *>(bu + o);
-        V2 p = *reinterpret_cast<const V2 *>(phi + o);
-        const T g0 = closure_g(-u.x + t.x, kind, order);
-        const T g1 = closure_g(-u.y + t.y, kind, order);
+        const V2 wv = *reinterpret_cast<const V2 *>(wp + o);
+        const T g0 = closure_g(wv.x + t.x, kind, order);
+        const T g1 = closure_g(wv.y + t.y, kind, order);
         V2 c;
-        c.x = g0 - (T)1 - t.x + bq * p.x;
-        c.y = g1 - (T)1 - t.y + bq * p.y;
+        c.x = g0 - (T)1 - t.x;
+        c.y = g1 - (T)1 - t.y;
         C dc = cmk(c.x, c.y);
         if (anchor) {                          // transform only c^sr - c^sr_a
             const V2 a = *reinterpret_cast<const V2 *>(ca + o);
@@ -513,7 +515,7 @@ k_plane_inv(Fields<T> f) {
     const long long ring = (long long)f.nv * f.G;
     const T *tcur = f.X + (long long)cur * ring + siteoff;
     T *rcur = f.R + (long long)cur * ring + siteoff;
-    const T *bu = f.bu + siteoff;
+    const T *wp = f.w + siteoff;
     const int anchor = ctl->anchor_valid, refresh = ctl->refresh;
     T *ha = f.h_a + siteoff;
     const T *Rh[kMaxHist];
@@ -527,20 +529,26 @@ k_plane_inv(Fields<T> f) {
         const int y = idx / Kz, m = idx - y * Kz;
         const long long o = (long long)y * f.Nz + 2 * m;
         const C hc = buf[y * pitch + m];
-        V2 h;
-        h.x = hc.x;
-        h.y = hc.y;
+        const V2 t = *reinterpret_cast<const V2 *>(tcur + o);
+        const V2 wv = *reinterpret_cast<const V2 *>(wp + o);
+        const T g0 = closure_g(wv.x + t.x, kind, order);
+        const T g1 = closure_g(wv.y + t.y, kind, order);
+        // R = h + 1 - g (Eq. 33) with h = h_a + dh; (h_a - g) first: near association peaks
+        // both are large and close, and the difference is then exact
+        V2 r, h;
         if (anchor) {
             const V2 a = *reinterpret_cast<const V2 *>(ha + o);
-            h.x += a.x;
-            h.y += a.y;
+            r.x = ((a.x - g0) + (T)1) + hc.x;
+            r.y = ((a.y - g1) + (T)1) + hc.y;
+            h.x = a.x + hc.x;
+            h.y = a.y + hc.y;
+        } else {
+            r.x = (hc.x - g0) + (T)1;
+            r.y = (hc.y - g1) + (T)1;
+            h.x = hc.x;
+            h.y = hc.y;
         }
         if (refresh) *reinterpret_cast<V2 *>(ha + o) = h;
-        const V2 t = *reinterpret_cast<const V2 *>(tcur + o);
-        const V2 u = *reinterpret_cast<const V2 *>(bu + o);
-        V2 r;
-        r.x = h.x + (T)1 - closure_g(-u.x + t.x, kind, order);
-        r.y = h.y + (T)1 - closure_g(-u.y + t.y, kind, order);
         *reinterpret_cast<V2 *>(rcur + o) = r;
         acc[0] += (double)r.x * (double)r.x + (double)r.y * (double)r.y;
 #pragma unroll
@@ -723,16 +731,20 @@ __global__ void k_mdiis(Ctrl *ctl, const double *partials, int nblocks) {
 }
 
 // ------------------------------------------------------------------ potential (Eq. 22, 29)
-template <typename T> struct PotAcc;
-
-// One thread per grid point and all sites; atoms staged through shared memory. LJ in the
-// working precision, the Coulomb sum sum_a q_a / r and phi accumulated in FP64.
+// One thread per grid point and all sites; atoms staged through shared memory. For the
+// FP32 form, far pairs are evaluated in FP32 (their Coulomb and phi terms accumulated in
+// FP64) and near pairs (r < 1.5 max sigma_ag, where the r^-12 term is large enough for FP32
+// coordinate rounding to show) entirely in FP64. Writes beta*u (capped at 1e4), phi and
+// w = beta q phi - beta*u.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_potential(Fields<T> f, const double *atoms, int n_atoms, const double *site_sig,
             const double *site_eps, const double *site_q, double beta, double ox, double oy,
             double oz, double dx, double dy, double dz) {
-    constexpr int TILE = 128;
+    constexpr int TILE = 64;
+    constexpr bool kMixed = sizeof(T) == 4;
+    __shared__ double ax[TILE], ay[TILE], az[TILE], aq[TILE], anear2[TILE];
+    __shared__ double dsig2[TILE][kMaxSites], deps4[TILE][kMaxSites];
     __shared__ T sx[TILE], sy[TILE], sz[TILE], sq[TILE];
     __shared__ T ssig2[TILE][kMaxSites], seps4[TILE][kMaxSites];
     const int nv = f.nv;
@@ -748,43 +760,75 @@ k_potential(Fields<T> f, const double *atoms, int n_atoms, const double *site_si
         iz = rem - iy * f.Nz;
     }
     // grid point relative to the origin
-    const T px = (T)(ix * dx), py = (T)(iy * dy), pz = (T)(iz * dz);
+    const double pxd = ix * dx, pyd = iy * dy, pzd = iz * dz;
+    const T px = (T)pxd, py = (T)pyd, pz = (T)pzd;
     T lj[kMaxSites];
+    double ljd[kMaxSites];
 #pragma unroll
-    for (int g = 0; g < kMaxSites; ++g) lj[g] = (T)0;
+    for (int g = 0; g < kMaxSites; ++g) {
+        lj[g] = (T)0;
+        ljd[g] = 0.0;
+    }
     double coul = 0.0, phi = 0.0;
     for (int a0 = 0; a0 < n_atoms; a0 += TILE) {
         const int na = min(TILE, n_atoms - a0);
         __syncthreads();
         for (int i = threadIdx.x; i < na; i += blockDim.x) {
             const double *at = atoms + (long long)(a0 + i) * kAtomStride;
-            sx[i] = (T)(at[0] - ox);
-            sy[i] = (T)(at[1] - oy);
-            sz[i] = (T)(at[2] - oz);
+            ax[i] = at[0] - ox;
+            ay[i] = at[1] - oy;
+            az[i] = at[2] - oz;
+            aq[i] = at[3];
+            sx[i] = (T)ax[i];
+            sy[i] = (T)ay[i];
+            sz[i] = (T)az[i];
             sq[i] = (T)at[3];
+            double smax = 0.0;
             for (int g = 0; g < nv; ++g) {
                 const double s = 0.5 * (at[4] + site_sig[g]);
-                ssig2[i][g] = (T)(s * s);
-                seps4[i][g] = (T)(4.0 * sqrt(at[5] * site_eps[g]));
+                smax = fmax(smax, s);
+                dsig2[i][g] = s * s;
+                deps4[i][g] = 4.0 * sqrt(at[5] * site_eps[g]);
+                ssig2[i][g] = (T)dsig2[i][g];
+                seps4[i][g] = (T)deps4[i][g];
             }
+            anear2[i] = kMixed ? 2.25 * smax * smax : -1.0;
         }
         __syncthreads();
         if (active) {
             for (int i = 0; i < na; ++i) {
                 const T ddx = px - sx[i], ddy = py - sy[i], ddz = pz - sz[i];
-                T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                r2 = r2 < (T)1e-8 ? (T)1e-8 : r2;
-                const T ir2 = (T)1 / r2;
-                const T r = sqrt(r2);
-                const T ir = (T)1 / r;
-                coul += (double)(sq[i] * ir);
-                phi += (double)(sq[i] * (T)(-expm1(-r)) * ir);
+                const T r2f = ddx * ddx + ddy * ddy + ddz * ddz;
+                if (kMixed && (double)r2f < anear2[i]) {
+                    const double ex = pxd - ax[i], ey = pyd - ay[i], ez = pzd - az[i];
+                    double r2 = ex * ex + ey * ey + ez * ez;
+                    r2 = r2 < 1e-8 ? 1e-8 : r2;
+                    const double r = sqrt(r2);
+                    const double ir = 1.0 / r, ir2 = 1.0 / r2;
+                    coul += aq[i] * ir;
+                    phi += aq[i] * (-expm1(-r)) * ir;
 #pragma unroll
-                for (int g = 0; g < kMaxSites; ++g) {
-                    if (g < nv) {
-                        const T s2 = ssig2[i][g] * ir2;
-                        const T s6 = s2 * s2 * s2;
-                        lj[g] += seps4[i][g] * (s6 * s6 - s6);
+                    for (int g = 0; g < kMaxSites; ++g) {
+                        if (g < nv) {
+                            const double s2 = dsig2[i][g] * ir2;
+                            const double s6 = s2 * s2 * s2;
+                            ljd[g] += deps4[i][g] * (s6 * s6 - s6);
+                        }
+                    }
+                } else {
+                    const T r2 = r2f < (T)1e-8 ? (T)1e-8 : r2f;
+                    const T ir2 = (T)1 / r2;
+                    const T r = sqrt(r2);
+                    const T ir = (T)1 / r;
+                    coul += (double)(sq[i] * ir);
+                    phi += (double)(sq[i] * (T)(-expm1(-r)) * ir);
+#pragma unroll
+                    for (int g = 0; g < kMaxSites; ++g) {
+                        if (g < nv) {
+                            const T s2 = ssig2[i][g] * ir2;
+                            const T s6 = s2 * s2 * s2;
+                            lj[g] += seps4[i][g] * (s6 * s6 - s6);
+                        }
                     }
                 }
             }
@@ -792,12 +836,14 @@ k_potential(Fields<T> f, const double *atoms, int n_atoms, const double *site_si
     }
     if (!active) return;
     const double C = 332.0637;
+    const double phiv = C * phi;
     for (int g = 0; g < nv; ++g) {
-        double v = beta * ((double)lj[g] + C * site_q[g] * coul);
+        double v = beta * ((double)lj[g] + ljd[g] + C * site_q[g] * coul);
         v = v > 1e4 ? 1e4 : v;
         f.bu[(long long)g * G + p] = (T)v;
+        f.w[(long long)g * G + p] = (T)(beta * site_q[g] * phiv - v);
     }
-    f.phi[p] = (T)(C * phi);
+    f.phi[p] = (T)phiv;
 }
 
 // ------------------------------------------------------------------ long range (Eq. 30)
@@ -851,23 +897,27 @@ k_longrange(Fields<T> f, const double *atoms, int n_atoms, double amp0) {
 }
 
 // ------------------------------------------------------------------ small helpers
+// Step 1: t = f, i.e. tau = 0.
 template <typename T>
 __global__ void k_init_guess(Fields<T> f, int slot) {
+    const long long n = (long long)f.nv * f.G;
+    const long long base = (long long)slot * n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        f.X[base + i] = (T)0;
+}
+
+// tau = t - beta q phi from a caller field t (FP64), into ring slot `slot`.
+template <typename T>
+__global__ void k_guess_from_t(Fields<T> f, int slot, const double *src) {
     const long long n = (long long)f.nv * f.G;
     const long long base = (long long)slot * n;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int g = (int)(i / f.G);
         const long long p = i - (long long)g * f.G;
-        f.X[base + i] = (T)(f.bq[g] * (double)f.phi[p]);
+        f.X[base + i] = (T)(src[i] - f.bq[g] * (double)f.phi[p]);
     }
-}
-
-template <typename T>
-__global__ void k_from_double(T *dst, const double *src, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        dst[i] = (T)src[i];
 }
 
 template <typename T>
@@ -884,14 +934,17 @@ __global__ void k_get_field(Fields<T> f, int field, int slot, int kind, int orde
         } else if (field == 7) {
             v = (double)f.R[(long long)slot * ring + i];
         } else {
-            const T t = f.X[(long long)slot * ring + i];
+            const int g = (int)(i / f.G);
+            const long long p = i - (long long)g * f.G;
+            const T tau = f.X[(long long)slot * ring + i];
+            const double fq = f.bq[g] * (double)f.phi[p];
             if (field == 4) {
-                v = (double)t;
+                v = (double)tau + fq;
             } else {
-                const T g = closure_g(-f.bu[i] + t, kind, order);
-                if (field == 1) v = (double)g;
-                else if (field == 3) v = (double)(g - (T)1);
-                else v = (double)(g - (T)1 - t);
+                const T gv = closure_g(f.w[i] + tau, kind, order);
+                if (field == 1) v = (double)gv;
+                else if (field == 3) v = (double)(gv - (T)1);
+                else v = (double)(gv - (T)1 - tau) - fq;      // c = h - t
             }
         }
         dst[i] = v;
@@ -906,17 +959,18 @@ k_sfe(Fields<T> f, int slot, int kind, int order, int sfe_kind, int sfe_order, d
     const int g = blockIdx.y;
     const long long ring = (long long)f.nv * f.G;
     const T *tt = f.X + (long long)slot * ring + (long long)g * f.G;
-    const T *bu = f.bu + (long long)g * f.G;
+    const T *wp = f.w + (long long)g * f.G;
+    const double bq = f.bq[g];
     double acc = 0.0;
     double fact = 1.0;
     for (int i = 2; i <= sfe_order + 1; ++i) fact *= i;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < f.G;
          p += (long long)gridDim.x * blockDim.x) {
-        const T t = tt[p];
-        const T d = -bu[p] + t;
+        const T tau = tt[p];
+        const T d = wp[p] + tau;
         const T gv = closure_g(d, kind, order);
         const double h = (double)(gv - (T)1);
-        const double c = (double)(gv - (T)1 - t);
+        const double c = (double)(gv - (T)1 - tau) - bq * (double)f.phi[p];   // c = h - t
         double v = -c - 0.5 * h * c;
         if (sfe_kind == 2) v += 0.5 * h * h;                     // HNC, Eq. 17
         else if (sfe_kind == 1) v += h < 0.0 ? 0.5 * h * h : 0.0;  // KH, Eq. 18
@@ -994,8 +1048,8 @@ template <typename T> cudaError_t launch_init_guess(const Fields<T> &f, int slot
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_from_double(T *dst, const double *src, long long n, cudaStream_t s) {
-    k_from_double<T><<<152 * 8, 256, 0, s>>>(dst, src, n);
+cudaError_t launch_guess_from_t(const Fields<T> &f, int slot, const double *src, cudaStream_t s) {
+    k_guess_from_t<T><<<152 * 8, 256, 0, s>>>(f, slot, src);
     return cudaGetLastError();
 }
 template <typename T>
@@ -1027,7 +1081,7 @@ cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sf
     template cudaError_t launch_longrange<T>(const Fields<T> &, const double *, int, double,    \
                                              cudaStream_t);                                     \
     template cudaError_t launch_init_guess<T>(const Fields<T> &, int, cudaStream_t);            \
-    template cudaError_t launch_from_double<T>(T *, const double *, long long, cudaStream_t);   \
+    template cudaError_t launch_guess_from_t<T>(const Fields<T> &, int, const double *, cudaStream_t); \
     template cudaError_t launch_get_field<T>(const Fields<T> &, int, int, int, int, double *,   \
                                              cudaStream_t);                                     \
     template cudaError_t launch_sfe<T>(const Fields<T> &, int, int, int, int, int, double *,    \
