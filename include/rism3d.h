@@ -190,6 +190,23 @@ rism3d_status rism3d_get_stats(const rism3d_ctx *ctx, rism3d_stats *out);
 /* Zero the counters. */
 rism3d_status rism3d_reset_stats(rism3d_ctx *ctx);
 
+/* Solvation free energy (same integrands as rism3d_get_sfe) from caller fields, without
+ * allocating device memory. The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate - for example code running while a CUDA stream is being
+ * captured into a graph, or a host framework that owns every device allocation - and needs
+ * no context. h, c and (for RISM3D_SFE_PSE only, else may be NULL) d = -beta u + t are
+ * device arrays [n_sites][n_points] of FP64; rho is host [n_sites]; per_site (host
+ * [n_sites]) may be NULL. Runs on cuda_stream (NULL = default stream) and returns after it
+ * has finished. Its scratch is a static device array of 8 x 152 + 8 doubles that every GPU
+ * that loads the library keeps until the process exits: n_sites above 8 is rejected with
+ * RISM3D_EINVAL. The first call on each device looks up that array's device address, so
+ * make it before any stream capture. Every call shares the array (each call rewrites all it
+ * reads, so nothing needs clearing); calls that overlap on the GPU race on it. */
+rism3d_status rism3d_sfe_noalloc(int n_sites, long long n_points, const double *h, const double *c,
+                                 const double *d, const double *rho, double temperature, double dV,
+                                 int kind, int pse_order, double *total, double *per_site,
+                                 void *cuda_stream);
+
 /* Message of the last failure on ctx (or of the last failed create when ctx is NULL). */
 const char *rism3d_last_error(const rism3d_ctx *ctx);
 

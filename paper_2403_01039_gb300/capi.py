@@ -89,6 +89,8 @@ def load():
         "rism3d_destroy": (None, [c_void_p]),
     }
     sig.update({
+        "rism3d_sfe_noalloc": (c_int, [c_int, ctypes.c_longlong, c_void_p, c_void_p, c_void_p, _dp,
+                                       c_double, c_double, c_int, c_int, P(c_double), _dp, c_void_p]),
         "rism1d_options_default": (None, [P(Rism1dOptions)]),
         "rism1d_xrism": (c_int, [P(Rism1dSolvent), P(Rism1dOptions), _dp, _dp, P(c_int), _dp]),
         "rism1d_last_error": (ctypes.c_char_p, []),
@@ -157,6 +159,29 @@ def default_options():
 def _check(lib, ctx, st):
     if st != OK:
         raise RismError(st, lib.rism3d_last_error(ctx).decode())
+
+
+def sfe_noalloc(h, c, rho, temperature, dV, kind="kh", pse_order=3, d=None, stream=None):
+    """rism3d_sfe_noalloc on CUDA float64 tensors h, c (and d for PSE) of shape
+    [n_sites, ...]: the SFE with the library's static scratch, no device allocation.
+    Returns (total, per_site)."""
+    lib = load()
+    n_sites = h.shape[0]
+    n_points = h.numel() // n_sites
+    for x in (h, c) + ((d,) if d is not None else ()):
+        if x.dtype.itemsize != 8 or not x.is_cuda or not x.is_contiguous() or x.numel() != h.numel():
+            raise ValueError("h, c, d must be contiguous float64 CUDA tensors of one shape")
+    rho_a, prho = _arr(rho)
+    tot = ctypes.c_double()
+    per = np.zeros(n_sites)
+    st = lib.rism3d_sfe_noalloc(n_sites, n_points, ctypes.c_void_p(h.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                ctypes.c_void_p(d.data_ptr() if d is not None else 0), prho,
+                                float(temperature), float(dV), SFE_KINDS[kind], int(pse_order),
+                                ctypes.byref(tot), per.ctypes.data_as(_dp),
+                                ctypes.c_void_p(stream.cuda_stream if stream is not None else 0))
+    if st != OK:
+        raise RismError(st, lib.rism3d_last_error(None).decode())
+    return tot.value, per
 
 
 def xrism(sites, n_r=2048, dr=0.05, closure="kh", tol=1e-10, charge_steps=10):

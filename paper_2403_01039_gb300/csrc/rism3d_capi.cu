@@ -129,6 +129,10 @@ struct rism3d_ctx {
     bool fp32() const { return precision == 32; }
 };
 
+namespace rism {
+void set_global_error(const char *msg) { g_create_error = msg; }
+}  // namespace rism
+
 static rism3d_status fail(rism3d_ctx *ctx, rism3d_status st, const char *fmt, ...) {
     char buf[512];
     va_list ap;

@@ -129,6 +129,9 @@ template <typename T>
 cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sfe_kind,
                        int sfe_order, double *partials, int blocks_per_site, cudaStream_t s);
 
+// Message returned by rism3d_last_error(NULL) (thread-local).
+void set_global_error(const char *msg);
+
 constexpr int kSfeBlocksPerSite = 152;
 constexpr size_t kAtomStride = 9;
 
