@@ -228,6 +228,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def replica_totals(secs, iters, device):
+    """Replicas only: every rank solved its own copies; the job took as long as its slowest
+    rank and did the sum of all ranks' iterations. One all-reduce of two scalars per
+    quantity, on the timing path only (no collective touches the solver's data)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(secs)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(n[0])
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -273,15 +287,7 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     stats = S.stats()
     iters = sum(r["iterations"] for r in reps)
-    t = torch.tensor([ms / 1e3, float(iters)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        tsum = t.clone()
-        torch.distributed.all_reduce(tsum[1:], op=torch.distributed.ReduceOp.SUM)
-        secs, iters_all = float(tmax[0]), float(tsum[1])
-    else:
-        secs, iters_all = float(t[0]), float(t[1])
+    secs, iters_all = replica_totals(ms / 1e3, iters, "cuda")
     value = world * args.steps / secs
     sgi = iters_all * nv * G / secs
 
@@ -299,12 +305,8 @@ def run_ours(args):
         S.sfe(args.closure, args.pse_order)
         S.get("g", out=g_host.numpy())
     barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e_val = world * args.e2e_steps / e2e_s if world == 1 else None
-    if world > 1:
-        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-        e2e_val = world * args.e2e_steps / float(te[0])
+    e2e_s, _ = replica_totals(time.perf_counter() - t0, 0, "cuda")
+    e2e_val = world * args.e2e_steps / e2e_s
     h2d = int(len(solute["q"]) * (3 + 3) * 8)
     d2h = int(nv * G * 8 + nv * 152 * 8)
 

@@ -100,6 +100,11 @@ typedef struct {
     int max_atoms;            /* capacity for rism3d_set_solute */
     int timing;               /* 1: record CUDA events around every kernel of the solve so
                                  rism3d_get_stats reports measured per-kernel device time */
+    int accelerator;          /* 0: MDIIS (Eq. 40, mdiis_nvec vectors); 1: the modified
+                                 Anderson method with two histories (Eqs. 34-39; Picard for
+                                 the first two steps; mdiis_damp is its mixing b) */
+    double anderson_s1;       /* Anderson shift s_1 (paper's value 0.2) */
+    double anderson_s2;       /* Anderson shift s_2 (paper's value 0.0) */
     void *cuda_stream;        /* cudaStream_t to run on; NULL: the library creates one */
     void *workspace;          /* device buffer of >= rism3d_workspace_bytes bytes, 256-byte
                                  aligned, owned by the caller and kept alive until
@@ -134,8 +139,9 @@ typedef struct {
 /* Library version string, static storage. */
 const char *rism3d_version(void);
 
-/* Fill *opt with the defaults: precision 32, M = 5, eta = 0.7, static damping,
- * max_iter 10000, check_every 8, max_atoms 100000, timing off, NULL stream and workspace. */
+/* Fill *opt with the defaults: precision 32, MDIIS with M = 5, eta = 0.7, static damping,
+ * max_iter 10000, check_every 8, max_atoms 100000, timing off, Anderson shifts 0.2 / 0.0,
+ * NULL stream and workspace. */
 void rism3d_options_default(rism3d_options *opt);
 
 /* Bytes of device workspace a context with these inputs needs. EINVAL on bad input,

@@ -24,6 +24,7 @@ Readings (the paper is silent or garbled):
 """
 import numpy as np
 
+from . import anderson
 from . import closure as cl
 from . import mdiis
 from .potential import beta_u, phi_long_range, phik_long_range, kvectors_half
@@ -120,9 +121,14 @@ STAGE_TOL = 1.0e-4   # tolerance of every stage but the last one (the last uses 
 
 
 def solve(problem, kind=cl.KH, pse_order=3, tol=1e-6, max_iter=10000, mdiis_nvec=5,
-          mdiis_damp=0.7, dynamic_damp=False, t_guess=None, verbose=False):
+          mdiis_damp=0.7, dynamic_damp=False, t_guess=None, verbose=False, accel="mdiis",
+          anderson_s=(0.2, 0.0)):
     """Run steps 1-7 (per closure stage) and return a dict with t, g, h, c, d, the total
-    iteration count and the RMS history."""
+    iteration count and the RMS history. ``accel`` is "mdiis" (Eq. 40) or "anderson" (the
+    modified Anderson method of Eqs. 34-39 with two histories, shifts ``anderson_s`` and
+    mixing b = ``mdiis_damp``)."""
+    if accel == "anderson":
+        mdiis_nvec = 3
     P = problem
     t = P.f.copy() if t_guess is None else np.array(t_guess, dtype=np.float64, copy=True)  # step 1
     stages = closure_stages(kind, pse_order)
@@ -159,7 +165,10 @@ def solve(problem, kind=cl.KH, pse_order=3, tol=1e-6, max_iter=10000, mdiis_nvec
             for i in range(k):
                 for j in range(i, k):
                     B[i, j] = B[j, i] = float(np.sum(hist_R[i] * hist_R[j]))
-            c, dropped = mdiis.coefficients(B)
+            if accel == "anderson":
+                c, dropped = anderson.coefficients(B, *anderson_s), 0
+            else:
+                c, dropped = mdiis.coefficients(B)
             for _ in range(dropped):
                 hist_t.pop(0)
                 hist_R.pop(0)

@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
                 ("mdiis_damp", ctypes.c_double), ("dynamic_damp", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("max_atoms", ctypes.c_int), ("timing", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p),
+                ("accelerator", ctypes.c_int), ("anderson_s1", ctypes.c_double),
+                ("anderson_s2", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
@@ -215,7 +216,8 @@ class Solver:
 
     def __init__(self, solvent, grid, precision=32, mdiis_nvec=5, mdiis_damp=0.7,
                  dynamic_damp=False, max_iter=10000, check_every=8, max_atoms=100000,
-                 timing=False, stream=None, device=None):
+                 timing=False, accelerator="mdiis", anderson_s=(0.2, 0.0), stream=None,
+                 device=None):
         import torch
         self._torch = torch
         lib = load()
@@ -235,6 +237,8 @@ class Solver:
         o.check_every = check_every
         o.max_atoms = max_atoms
         o.timing = int(bool(timing))
+        o.accelerator = {"mdiis": 0, "anderson": 1}[accelerator]
+        o.anderson_s1, o.anderson_s2 = float(anderson_s[0]), float(anderson_s[1])
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
             o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)

@@ -23,7 +23,7 @@ constexpr double kKB = 0.0019872041;      // kcal / (mol K)
 constexpr double kCoulomb = 332.0637;     // kcal A / (mol e^2)
 constexpr double kPi = 3.14159265358979323846;
 constexpr size_t kMaxSmem = 227 * 1024;
-constexpr size_t kPencilSmemTarget = 100 * 1024;
+constexpr size_t kPencilSmemTarget = 64 * 1024;
 
 thread_local std::string g_create_error;
 
@@ -222,6 +222,8 @@ rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, cons
         return fail(nullptr, RISM3D_EINVAL, "mdiis_nvec must be in 1..%d", kMaxHist);
     if (!(op->mdiis_damp > 0.0 && op->mdiis_damp <= 2.0))
         return fail(nullptr, RISM3D_EINVAL, "mdiis_damp must be in (0, 2]");
+    if (op->accelerator != 0 && op->accelerator != 1)
+        return fail(nullptr, RISM3D_EINVAL, "accelerator must be 0 (MDIIS) or 1 (modified Anderson)");
     if (op->max_iter < 1 || op->check_every < 1 || op->max_atoms < 1)
         return fail(nullptr, RISM3D_EINVAL, "max_iter, check_every and max_atoms must be >= 1");
     g.nv = sv->n_sites;
@@ -230,17 +232,18 @@ rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, cons
     g.Nz = gr->n[2];
     g.Kz = g.Nz / 2;
     g.G = (long long)g.Nx * g.Ny * g.Nz;
-    g.M = op->mdiis_nvec;
+    g.M = op->accelerator == 1 ? 3 : op->mdiis_nvec;   // Anderson keeps the last three pairs
     g.nk = sv->n_k;
     g.max_atoms = op->max_atoms;
     g.s = op->precision == 32 ? 4 : 8;
     if (!make_plan(g.Nx, g.px) || !make_plan(g.Ny, g.py) || !make_plan(g.Kz, g.ph))
         return fail(nullptr, RISM3D_EUNSUPPORTED, "Nx, Ny and Nz/2 must factor into 2, 3 and 5");
-    const int maxc = g.s == 4 ? 16 : 8;
+    const int maxc = 8;                         // complex values a thread holds per FFT stage
     const size_t c = 2 * (size_t)g.s;
     g.pitch = g.Kz + 1;
     if (g.pitch % 2 == 0) g.pitch += 1;        // odd pitch: column access without bank conflicts
-    g.plane_smem = c * ((size_t)g.Ny * g.pitch + g.Kz + g.Ny + g.Kz + 1) + 32 * sizeof(double) + 16;
+    g.plane_smem = c * ((size_t)g.Ny * g.pitch + g.Kz + g.Ny + g.Kz + 1) +
+                   (kMaxHist + 1) * (kThreadsPlane / 32) * sizeof(double) + 16;
     if (g.plane_smem > kMaxSmem)
         return fail(nullptr, RISM3D_EUNSUPPORTED,
                     "a y-z plane (%d x %d) needs %zu bytes of shared memory (limit %zu)", g.Ny,
@@ -275,6 +278,7 @@ void fill_fields(rism3d_ctx *ctx, const Geometry &g, const Layout &L, Fields<T> 
     f.Ny = g.Ny;
     f.Nz = g.Nz;
     f.Kz = g.Kz;
+    f.M = g.M;
     f.G = g.G;
     f.specN = (long long)g.Nx * g.Ny * g.Kz;
     f.bu = reinterpret_cast<T *>(b + L.bu);
@@ -492,7 +496,10 @@ void reset_ctrl(rism3d_ctx *ctx, Ctrl &c) {
     std::memset(&c, 0, sizeof(Ctrl));
     c.status = kRunning;
     c.max_iter = ctx->opt.max_iter;
-    c.M = ctx->opt.mdiis_nvec;
+    c.M = ctx->opt.accelerator == 1 ? 3 : ctx->opt.mdiis_nvec;
+    c.accel = ctx->opt.accelerator;
+    c.s1 = ctx->opt.anderson_s1;
+    c.s2 = ctx->opt.anderson_s2;
     c.dynamic = ctx->opt.dynamic_damp ? 1 : 0;
     c.damp = ctx->opt.mdiis_damp;
     c.inv_count = 1.0 / ((double)ctx->nv * (double)ctx->G);
@@ -559,6 +566,9 @@ void rism3d_options_default(rism3d_options *opt) {
     opt->max_iter = 10000;
     opt->check_every = 8;
     opt->max_atoms = 100000;
+    opt->accelerator = 0;
+    opt->anderson_s1 = 0.2;
+    opt->anderson_s2 = 0.0;
 }
 
 rism3d_status rism3d_workspace_bytes(const rism3d_solvent *solvent, const rism3d_grid *grid,

@@ -10,7 +10,7 @@ constexpr int kMaxSites = 8;      // solvent sites n_v
 constexpr int kMaxHist = 16;      // MDIIS vectors M
 constexpr int kMaxRadixStages = 10;
 constexpr int kMaxClosureStages = 12;
-constexpr int kThreadsPlane = 512;
+constexpr int kThreadsPlane = 256;
 constexpr int kThreadsPencil = 256;
 
 // Solver status words written by the device (Ctrl::status).
@@ -38,6 +38,8 @@ struct Ctrl {
     int M;                          // history capacity
     int dynamic;
     double damp;
+    int accel;                      // 0 MDIIS (Eq. 40), 1 modified Anderson (Eqs. 34-39)
+    double s1, s2;                  // Anderson shifts
     double inv_count;               // 1 / (n_v * Nx * Ny * Nz)
     int n_partials;                 // blocks that wrote Gram partials
     // iterate bookkeeping
@@ -74,6 +76,7 @@ template <typename T>
 struct Fields {
     typedef typename Cx<T>::type C;
     int nv, Nx, Ny, Nz, Kz;         // Kz = Nz / 2
+    int M;                          // MDIIS ring capacity
     long long G;                    // Nx * Ny * Nz
     long long specN;                // Nx * Ny * Kz complex values per site (kz < Kz)
     T *bu;                          // [nv][G] beta * u (outputs and SFE)
@@ -95,7 +98,7 @@ struct Fields {
     int pencil_pitch;
     double bq[kMaxSites];           // beta * q_gamma
     double ks[3];                   // 2 pi / (N d) per axis
-    double *partials;               // [nv * Nx][kMaxHist + 1]
+    double *partials;               // [kMaxHist + 1][nv * Nx] (value-major)
     Ctrl *ctrl;
 };
 

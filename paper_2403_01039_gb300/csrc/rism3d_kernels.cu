@@ -192,7 +192,7 @@ __device__ void fft_smem(C *buf, const FftPlan &p, int es, int nb, int bs, int c
 }
 
 template <typename T> struct MaxC;
-template <> struct MaxC<float> { static constexpr int v = 16; };
+template <> struct MaxC<float> { static constexpr int v = 8; };
 template <> struct MaxC<double> { static constexpr int v = 8; };
 
 // ------------------------------------------------------------------ closure
@@ -213,13 +213,62 @@ __device__ __forceinline__ T closure_g(T d, int kind, int order) {
     return s;
 }
 
+// Error-free FP32 dot-product accumulation (the Dot2 scheme of Ogita, Rump and Oishi,
+// "Accurate sum and dot product", 2005): the rounding error of each product (recovered
+// with an FMA) and of each sum (TwoSum) is carried in a second FP32 word, so the pair
+// (hi, lo) holds the FP32 dot product to about FP64 accuracy without FP64 arithmetic.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+template <typename T> struct GramAcc;
+template <> struct GramAcc<float> {
+    float hi, lo;
+    __device__ __forceinline__ void zero() { hi = lo = 0.f; }
+    __device__ __forceinline__ void add(float x, float y) {
+        const float p = x * y;
+        const float pe = __fmaf_rn(x, y, -p);
+        float sm, e;
+        two_sum(hi, p, sm, e);
+        hi = sm;
+        lo += e + pe;
+    }
+    __device__ __forceinline__ void merge(float h2, float l2) {
+        float sm, e;
+        two_sum(hi, h2, sm, e);
+        hi = sm;
+        lo += l2 + e;
+    }
+    __device__ __forceinline__ void warp_reduce() {
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            merge(h2, l2);
+        }
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <> struct GramAcc<double> {
+    double s;
+    __device__ __forceinline__ void zero() { s = 0.0; }
+    __device__ __forceinline__ void add(double x, double y) { s += x * y; }
+    __device__ __forceinline__ void warp_reduce() {
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { typedef float2 type; };
 template <> struct Vec2<double> { typedef double2 type; };
 
 // ------------------------------------------------------------------ pass 1: plane_fwd
-template <typename T>
-__global__ void __launch_bounds__(kThreadsPlane)
+// One block per (x plane, site). MAXH bounds the stored MDIIS pairs (8 or 16) so the update
+// coefficients and slots live in registers.
+template <typename T, int MAXH>
+__global__ void __launch_bounds__(kThreadsPlane, sizeof(T) == 4 ? 3 : 2)
 k_plane_fwd(Fields<T> f) {
     typedef typename Cx<T>::type C;
     typedef typename Vec2<T>::type V2;
@@ -242,18 +291,14 @@ k_plane_fwd(Fields<T> f) {
     const int do_update = ctl->do_update;
     const int upd_n = ctl->upd_n;
     const T eta = (T)ctl->eta;
-    T coef[kMaxHist];
-    const T *Xs[kMaxHist];
-    const T *Rs[kMaxHist];
-    const long long siteoff = (long long)gam * f.G + (long long)x * Ny * f.Nz;
     const long long ring = (long long)f.nv * f.G;
+    const long long siteoff = (long long)gam * f.G + (long long)x * Ny * f.Nz;
+    T coef[MAXH];
+    int slot[MAXH];
 #pragma unroll
-    for (int i = 0; i < kMaxHist; ++i) {
-        if (i < upd_n) {
-            coef[i] = (T)ctl->upd_coef[i];
-            Xs[i] = f.X + (long long)ctl->upd_slot[i] * ring + siteoff;
-            Rs[i] = f.R + (long long)ctl->upd_slot[i] * ring + siteoff;
-        }
+    for (int i = 0; i < MAXH; ++i) {
+        coef[i] = i < upd_n ? (T)ctl->upd_coef[i] : (T)0;
+        slot[i] = i < upd_n ? ctl->upd_slot[i] : 0;
     }
     T *tcur = f.X + (long long)cur * ring + siteoff;
     const T *wp = f.w + siteoff;
@@ -270,10 +315,11 @@ k_plane_fwd(Fields<T> f) {
             t.x = (T)0;
             t.y = (T)0;
 #pragma unroll
-            for (int i = 0; i < kMaxHist; ++i) {
+            for (int i = 0; i < MAXH; ++i) {
                 if (i < upd_n) {
-                    V2 xv = *reinterpret_cast<const V2 *>(Xs[i] + o);
-                    V2 rv = *reinterpret_cast<const V2 *>(Rs[i] + o);
+                    const long long base = (long long)slot[i] * ring + siteoff + o;
+                    const V2 xv = *reinterpret_cast<const V2 *>(f.X + base);
+                    const V2 rv = *reinterpret_cast<const V2 *>(f.R + base);
                     t.x += coef[i] * (xv.x + eta * rv.x);
                     t.y += coef[i] * (xv.y + eta * rv.y);
                 }
@@ -312,17 +358,13 @@ k_plane_fwd(Fields<T> f) {
         } else {
             const int k2 = Kz - k;
             C a = row[k], b = row[k2];
-            // for k: Zk = a, Zc = conj(b); for k2: Zk = b, Zc = conj(a)
             C e1 = cscale(cadd(a, cconj(b)), (T)0.5);
-            C o1 = cscale(csub(a, cconj(b)), (T)0.5);        // times -i w^k below
-            C w1 = tw_z[k];
-            C X1 = cadd(e1, cmul(cmuli(o1, -1), w1));
+            C o1 = cscale(csub(a, cconj(b)), (T)0.5);
+            C X1 = cadd(e1, cmul(cmuli(o1, -1), tw_z[k]));
             if (k2 != k) {
                 C e2 = cscale(cadd(b, cconj(a)), (T)0.5);
                 C o2 = cscale(csub(b, cconj(a)), (T)0.5);
-                C w2 = tw_z[k2];
-                C X2 = cadd(e2, cmul(cmuli(o2, -1), w2));
-                row[k2] = X2;
+                row[k2] = cadd(e2, cmul(cmuli(o2, -1), tw_z[k2]));
             }
             row[k] = X1;
         }
@@ -330,7 +372,6 @@ k_plane_fwd(Fields<T> f) {
     __syncthreads();
     // columns: complex FFT of length Ny for kz = 0..Kz
     fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz + 1, 1, f.chunk_cols_fwd, tw_y, -1);
-    // store the plane of the half spectrum
     C *dst = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz;
     for (int idx = threadIdx.x; idx < Ny * Kz; idx += blockDim.x) {
         const int y = idx / Kz, k = idx - y * Kz;
@@ -343,24 +384,24 @@ k_plane_fwd(Fields<T> f) {
 // ------------------------------------------------------------------ pass 2: pencil
 __device__ __forceinline__ int signed_index(int i, int N) { return (2 * i < N) ? i : i - N; }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreadsPencil)
+// One block per tile of W spectrum columns (all x, all NV sites). NV is a template argument
+// so the contraction unrolls over exactly the solvent sites.
+template <typename T, int NV>
+__global__ void __launch_bounds__(kThreadsPencil, sizeof(T) == 4 ? 3 : 2)
 k_pencil(Fields<T> f) {
     typedef typename Cx<T>::type C;
     if (f.ctrl->status != kRunning) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *buf = reinterpret_cast<C *>(smraw);
-    const int Nx = f.Nx, Ny = f.Ny, Kz = f.Kz, W = f.W, nv = f.nv, pp = f.pencil_pitch;
-    C *tw_x = buf + (long)nv * W * pp;
+    const int Nx = f.Nx, Ny = f.Ny, Kz = f.Kz, W = f.W, pp = f.pencil_pitch;
+    C *tw_x = buf + (long)NV * W * pp;
     for (int i = threadIdx.x; i < Nx; i += blockDim.x) tw_x[i] = f.tw_x[i];
 
-    // decode the tile: main tiles cover (y, kz0 .. kz0+W) with kz < Kz; Nyquist tiles cover
-    // (y0 .. y0+W, kz = Kz)
+    // main tiles cover (y, kz0 .. kz0+W) with kz < Kz; Nyquist tiles (y0 .. y0+W, kz = Kz)
     int tile = blockIdx.x;
-    bool nyq = tile >= f.tiles_main;
+    const bool nyq = tile >= f.tiles_main;
     int y = 0, kz0 = 0, y0 = 0, ncol;
-    long long col_base, xstride, psi_base;
-    const C *src_base;
+    long long col_base, xstride;
     if (!nyq) {
         const int per = (Kz + W - 1) / W;
         y = tile / per;
@@ -368,20 +409,16 @@ k_pencil(Fields<T> f) {
         ncol = min(W, Kz - kz0);
         col_base = (long long)y * Kz + kz0;
         xstride = (long long)Ny * Kz;
-        src_base = f.spec;
-        psi_base = col_base;
     } else {
         tile -= f.tiles_main;
         y0 = tile * W;
         ncol = min(W, Ny - y0);
         col_base = y0;
         xstride = Ny;
-        src_base = f.spec_nyq;
-        psi_base = col_base;
     }
-    const long long site_stride = nv == 0 ? 0 : (long long)Nx * xstride;
-    // load [site][col][x]
-    const int nload = nv * Nx * ncol;
+    const C *src_base = nyq ? f.spec_nyq : f.spec;
+    const long long site_stride = (long long)Nx * xstride;
+    const int nload = NV * Nx * ncol;
     for (int idx = threadIdx.x; idx < nload; idx += blockDim.x) {
         const int c = idx % ncol;
         const int rest = idx / ncol;
@@ -389,51 +426,51 @@ k_pencil(Fields<T> f) {
         buf[(a * W + c) * pp + xx] = src_base[a * site_stride + xx * xstride + col_base + c];
     }
     __syncthreads();
-    fft_smem<C, MaxC<T>::v>(buf, f.px, 1, nv * W, pp, f.chunk_x, tw_x, -1);
-    // contraction (Eq. 13 with Eq. 32): E_g = sum_a D_a A_ag(|k|) + Psi A_{nv,g}
+    fft_smem<C, MaxC<T>::v>(buf, f.px, 1, NV * W, pp, f.chunk_x, tw_x, -1);
+    // contraction (Eq. 13 with Eq. 32): E_g = sum_a D_a A_ag(|k|) [+ Psi A_{nv,g} before the
+    // first anchor, after which f~ is part of h_a]
     const C *psi = nyq ? f.psi_nyq : f.psi;
-    const bool psi_on = f.ctrl->anchor_valid == 0;   // after the first anchor, f~ lives in h_a
+    const bool psi_on = f.ctrl->anchor_valid == 0;
     const int npts = Nx * ncol;
-    const int rowlen = (nv + 1) * nv;
+    constexpr int rowlen = (NV + 1) * NV;
+    const T ks0 = (T)f.ks[0], ks1 = (T)f.ks[1], ks2 = (T)f.ks[2], inv_dk = (T)f.inv_dk;
     for (int idx = threadIdx.x; idx < npts; idx += blockDim.x) {
         const int c = idx % ncol, xx = idx / ncol;
         const int yy = nyq ? y0 + c : y;
         const int kz = nyq ? Kz : kz0 + c;
-        const double kx = f.ks[0] * signed_index(xx, Nx);
-        const double ky = f.ks[1] * signed_index(yy, Ny);
-        const double kzv = f.ks[2] * (double)kz;
-        const T kmag = (T)sqrt(kx * kx + ky * ky + kzv * kzv);
-        const T xk = kmag * (T)f.inv_dk;
+        const T kx = ks0 * (T)signed_index(xx, Nx);
+        const T ky = ks1 * (T)signed_index(yy, Ny);
+        const T kzv = ks2 * (T)kz;
+        const T xk = sqrt(kx * kx + ky * ky + kzv * kzv) * inv_dk;
         int j = (int)floor(xk);
         if (j > f.nk - 2) j = f.nk - 2;
         T w = xk - (T)j;
         w = w < (T)0 ? (T)0 : (w > (T)1 ? (T)1 : w);
         const T *A0 = f.table + (long long)j * rowlen;
         const T *A1 = A0 + rowlen;
-        C D[kMaxSites];
+        C D[NV];
 #pragma unroll
-        for (int a = 0; a < kMaxSites; ++a)
-            if (a < nv) D[a] = buf[(a * W + c) * pp + xx];
-        C Psi = psi_on ? psi[xx * xstride + psi_base + c] : cmk((T)0, (T)0);
+        for (int a = 0; a < NV; ++a) D[a] = buf[(a * W + c) * pp + xx];
+        const C Psi = psi_on ? psi[xx * xstride + col_base + c] : cmk((T)0, (T)0);
 #pragma unroll
-        for (int g = 0; g < kMaxSites; ++g) {
-            if (g < nv) {
-                T ar = (T)0, ai = (T)0;
+        for (int g = 0; g < NV; ++g) {
+            T ar = (T)0, ai = (T)0;
 #pragma unroll
-                for (int a = 0; a < kMaxSites + 1; ++a) {
-                    if (a < nv || (a == nv && psi_on)) {
-                        const T coef = __ldg(A0 + a * nv + g) * ((T)1 - w) + __ldg(A1 + a * nv + g) * w;
-                        const C v = (a < nv) ? D[a] : Psi;
-                        ar += coef * v.x;
-                        ai += coef * v.y;
-                    }
-                }
-                buf[(g * W + c) * pp + xx] = cmk(ar, ai);
+            for (int a = 0; a < NV; ++a) {
+                const T coef = __ldg(A0 + a * NV + g) * ((T)1 - w) + __ldg(A1 + a * NV + g) * w;
+                ar += coef * D[a].x;
+                ai += coef * D[a].y;
             }
+            if (psi_on) {
+                const T coef = __ldg(A0 + NV * NV + g) * ((T)1 - w) + __ldg(A1 + NV * NV + g) * w;
+                ar += coef * Psi.x;
+                ai += coef * Psi.y;
+            }
+            buf[(g * W + c) * pp + xx] = cmk(ar, ai);
         }
     }
     __syncthreads();
-    fft_smem<C, MaxC<T>::v>(buf, f.px, 1, nv * W, pp, f.chunk_x, tw_x, +1);
+    fft_smem<C, MaxC<T>::v>(buf, f.px, 1, NV * W, pp, f.chunk_x, tw_x, +1);
     C *dst_base = nyq ? f.spec_nyq : f.spec;
     for (int idx = threadIdx.x; idx < nload; idx += blockDim.x) {
         const int c = idx % ncol;
@@ -444,23 +481,11 @@ k_pencil(Fields<T> f) {
 }
 
 // ------------------------------------------------------------------ pass 3: plane_inv
-template <typename T>
-__device__ __forceinline__ double block_sum(double v, double *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
-        for (int i = 0; i < nw; ++i) s += red[i];
-    }
-    return s;   // valid in thread 0
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreadsPlane)
+// One block per (x plane, site): inverse y and z transforms, residual, and the block's
+// contribution to <R_cur, R_i> and sum R^2 (Dot2 accumulation, FP64 across threads).
+// Partials are stored value-major: partials[i * n_blocks + block].
+template <typename T, int MAXH>
+__global__ void __launch_bounds__(kThreadsPlane, sizeof(T) == 4 ? 3 : 2)
 k_plane_inv(Fields<T> f) {
     typedef typename Cx<T>::type C;
     typedef typename Vec2<T>::type V2;
@@ -494,37 +519,31 @@ k_plane_inv(Fields<T> f) {
         C *row = buf + y * pitch;
         const int k2 = Kz - k;
         C a = row[k], b = row[k2];
-        C w1 = cconj(tw_z[k]);
-        C Z1 = cadd(cadd(a, cconj(b)), cmuli(cmul(csub(a, cconj(b)), w1), +1));
-        if (k != 0 && k2 != k) {
-            C w2 = cconj(tw_z[k2]);
-            C Z2 = cadd(cadd(b, cconj(a)), cmuli(cmul(csub(b, cconj(a)), w2), +1));
-            row[k2] = Z2;
-        }
+        C Z1 = cadd(cadd(a, cconj(b)), cmuli(cmul(csub(a, cconj(b)), cconj(tw_z[k])), +1));
+        if (k != 0 && k2 != k)
+            row[k2] = cadd(cadd(b, cconj(a)), cmuli(cmul(csub(b, cconj(a)), cconj(tw_z[k2])), +1));
         row[k] = Z1;
     }
     __syncthreads();
     fft_smem<C, MaxC<T>::v>(buf, f.ph, 1, Ny, pitch, f.chunk_rows, tw_h, +1);
 
-    // residual R = h + 1 - g (Eq. 33) and Gram partials
     const int stage = ctl->stage;
     const int kind = ctl->stage_kind[stage], order = ctl->stage_order[stage];
     const int cur = ctl->cur;
     const int hist_n = ctl->hist_n;
-    const long long siteoff = (long long)gam * f.G + (long long)x * Ny * f.Nz;
     const long long ring = (long long)f.nv * f.G;
+    const long long siteoff = (long long)gam * f.G + (long long)x * Ny * f.Nz;
     const T *tcur = f.X + (long long)cur * ring + siteoff;
     T *rcur = f.R + (long long)cur * ring + siteoff;
     const T *wp = f.w + siteoff;
     const int anchor = ctl->anchor_valid, refresh = ctl->refresh;
     T *ha = f.h_a + siteoff;
-    const T *Rh[kMaxHist];
+    int hslot[MAXH];
 #pragma unroll
-    for (int i = 0; i < kMaxHist; ++i)
-        if (i < hist_n) Rh[i] = f.R + (long long)ctl->hist_slot[i] * ring + siteoff;
-    double acc[kMaxHist + 1];
+    for (int i = 0; i < MAXH; ++i) hslot[i] = i < hist_n ? ctl->hist_slot[i] : 0;
+    GramAcc<T> acc[MAXH + 1];
 #pragma unroll
-    for (int i = 0; i <= kMaxHist; ++i) acc[i] = 0.0;
+    for (int i = 0; i <= MAXH; ++i) acc[i].zero();
     for (int idx = threadIdx.x; idx < Ny * Kz; idx += blockDim.x) {
         const int y = idx / Kz, m = idx - y * Kz;
         const long long o = (long long)y * f.Nz + 2 * m;
@@ -550,22 +569,32 @@ k_plane_inv(Fields<T> f) {
         }
         if (refresh) *reinterpret_cast<V2 *>(ha + o) = h;
         *reinterpret_cast<V2 *>(rcur + o) = r;
-        acc[0] += (double)r.x * (double)r.x + (double)r.y * (double)r.y;
+        acc[0].add(r.x, r.x);
+        acc[0].add(r.y, r.y);
 #pragma unroll
-        for (int i = 0; i < kMaxHist; ++i) {
+        for (int i = 0; i < MAXH; ++i) {
             if (i < hist_n) {
-                const V2 q = *reinterpret_cast<const V2 *>(Rh[i] + o);
-                acc[i + 1] += (double)r.x * (double)q.x + (double)r.y * (double)q.y;
+                const V2 q = *reinterpret_cast<const V2 *>(f.R + (long long)hslot[i] * ring + siteoff + o);
+                acc[i + 1].add(r.x, q.x);
+                acc[i + 1].add(r.y, q.y);
             }
         }
     }
-    double *part = f.partials + ((long long)gam * f.Nx + x) * (kMaxHist + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const long long nblocks = (long long)f.nv * f.Nx;
+    const long long blk = (long long)gam * f.Nx + x;
 #pragma unroll
-    for (int i = 0; i <= kMaxHist; ++i) {
+    for (int i = 0; i <= MAXH; ++i) {
         if (i <= hist_n) {
-            const double s = block_sum<T>(acc[i], red);
-            if (threadIdx.x == 0) part[i] = s;
+            acc[i].warp_reduce();
+            if (lane == 0) red[i * nw + warp] = acc[i].value();
         }
+    }
+    __syncthreads();
+    if (threadIdx.x <= hist_n) {
+        double s = 0.0;
+        for (int k = 0; k < nw; ++k) s += red[threadIdx.x * nw + k];
+        f.partials[threadIdx.x * nblocks + blk] = s;
     }
 }
 
@@ -589,8 +618,17 @@ __global__ void k_mdiis(Ctrl *ctl, const double *partials, int nblocks) {
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp <= hist_n) {
-        double s = 0.0;
-        for (int b = lane; b < nblocks; b += 32) s += partials[(long long)b * (kMaxHist + 1) + warp];
+        const double *pv = partials + (long long)warp * nblocks;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int b = lane;
+        for (; b + 96 < nblocks; b += 128) {
+            s0 += pv[b];
+            s1 += pv[b + 32];
+            s2 += pv[b + 64];
+            s3 += pv[b + 96];
+        }
+        for (; b < nblocks; b += 32) s0 += pv[b];
+        double s = (s0 + s1) + (s2 + s3);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) sums[warp] = s;
     }
@@ -644,10 +682,54 @@ __global__ void k_mdiis(Ctrl *ctl, const double *partials, int nblocks) {
     int k = 0;
     for (int i = 0; i < hist_n; ++i) H[k++] = ctl->hist_slot[i];
     H[k++] = cur;
-    // bordered solve with drop-oldest retry
     double c[kMaxHist];
     int first = 0;
-    for (;;) {
+    if (ctl->accel == 1) {
+        // modified Anderson, two histories (Eqs. 34-39): theta from the 2 x 2 system of
+        // Eq. 36 on D_i = R_new - R_{new-i}; a_i = theta_i + s_i; Picard while fewer than
+        // three pairs are stored or if the system is singular
+        for (int i = 0; i < k; ++i) c[i] = 0.0;
+        c[k - 1] = 1.0;
+        if (k >= 3) {
+            const int n0 = H[k - 1], n1 = H[k - 2], n2 = H[k - 3];
+            const int di[2] = {n1, n2};
+            double Mm[2][2], rhs[2];
+            const double b00 = ctl->B[n0 * kMaxHist + n0];
+            for (int i = 0; i < 2; ++i) {
+                rhs[i] = b00 - ctl->B[n0 * kMaxHist + di[i]];
+                for (int j = 0; j < 2; ++j)
+                    Mm[i][j] = b00 - ctl->B[n0 * kMaxHist + di[j]] - ctl->B[n0 * kMaxHist + di[i]] +
+                               ctl->B[di[i] * kMaxHist + di[j]];
+            }
+            const double sc = fmax(Mm[0][0], Mm[1][1]);
+            if (sc > 0.0) {
+                for (int i = 0; i < 2; ++i) {
+                    rhs[i] /= sc;
+                    for (int j = 0; j < 2; ++j) Mm[i][j] /= sc;
+                }
+                // 2 x 2 Gaussian elimination with partial pivoting
+                int p = fabs(Mm[1][0]) > fabs(Mm[0][0]) ? 1 : 0;
+                if (fabs(Mm[p][0]) >= 1e-12) {
+                    if (p == 1) {
+                        double t0 = Mm[0][0], t1 = Mm[0][1], tr = rhs[0];
+                        Mm[0][0] = Mm[1][0]; Mm[0][1] = Mm[1][1]; rhs[0] = rhs[1];
+                        Mm[1][0] = t0; Mm[1][1] = t1; rhs[1] = tr;
+                    }
+                    const double fct = Mm[1][0] / Mm[0][0];
+                    const double m11 = Mm[1][1] - fct * Mm[0][1];
+                    const double r1 = rhs[1] - fct * rhs[0];
+                    if (fabs(m11) >= 1e-12) {
+                        const double th1 = r1 / m11;
+                        const double th0 = (rhs[0] - Mm[0][1] * th1) / Mm[0][0];
+                        const double a1 = th0 + ctl->s1, a2 = th1 + ctl->s2;
+                        c[k - 1] = 1.0 - a1 - a2;
+                        c[k - 2] = a1;
+                        c[k - 3] = a2;
+                    }
+                }
+            }
+        }
+    } else for (;;) {                 // MDIIS: bordered solve with drop-oldest retry
         const int n = k - first;
         if (n == 1) {
             c[0] = 1.0;
@@ -951,6 +1033,19 @@ __global__ void k_get_field(Fields<T> f, int field, int slot, int kind, int orde
     }
 }
 
+// Block-wide FP64 sum (result valid in thread 0).
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    return s;
+}
+
 // SFE integrands (Eqs. 17-18, GF, PSE-n) accumulated in FP64, per site and block.
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -980,14 +1075,15 @@ k_sfe(Fields<T> f, int slot, int kind, int order, int sfe_kind, int sfe_order, d
         }
         acc += v;
     }
-    const double s = block_sum<T>(acc, red);
+    const double s = block_sum(acc, red);
     if (threadIdx.x == 0) partials[(long long)g * gridDim.x + blockIdx.x] = s;
 }
 
 // ------------------------------------------------------------------ launchers
 template <typename T> size_t plane_smem_bytes(const Fields<T> &f) {
     typedef typename Cx<T>::type C;
-    return sizeof(C) * ((size_t)f.Ny * f.pitch + f.Kz + f.Ny + f.Kz + 1) + 32 * sizeof(double) + 16;
+    return sizeof(C) * ((size_t)f.Ny * f.pitch + f.Kz + f.Ny + f.Kz + 1) +
+           (kMaxHist + 1) * (kThreadsPlane / 32) * sizeof(double) + 16;
 }
 template <typename T> size_t pencil_smem_bytes(const Fields<T> &f) {
     typedef typename Cx<T>::type C;
@@ -1000,25 +1096,57 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 }
 
 template <typename T> cudaError_t prepare_kernels(const Fields<T> &f) {
-    cudaError_t e = set_smem(k_plane_fwd<T>, plane_smem_bytes(f));
-    if (e == cudaSuccess) e = set_smem(k_plane_inv<T>, plane_smem_bytes(f));
-    if (e == cudaSuccess) e = set_smem(k_pencil<T>, pencil_smem_bytes(f));
-    return e;
+    const size_t pl = plane_smem_bytes(f), pe = pencil_smem_bytes(f);
+    cudaError_t e = set_smem(k_plane_fwd<T, 8>, pl);
+    if (e == cudaSuccess) e = set_smem(k_plane_fwd<T, kMaxHist>, pl);
+    if (e == cudaSuccess) e = set_smem(k_plane_inv<T, 8>, pl);
+    if (e == cudaSuccess) e = set_smem(k_plane_inv<T, kMaxHist>, pl);
+    if (e != cudaSuccess) return e;
+    switch (f.nv) {
+        case 1: return set_smem(k_pencil<T, 1>, pe);
+        case 2: return set_smem(k_pencil<T, 2>, pe);
+        case 3: return set_smem(k_pencil<T, 3>, pe);
+        case 4: return set_smem(k_pencil<T, 4>, pe);
+        case 5: return set_smem(k_pencil<T, 5>, pe);
+        case 6: return set_smem(k_pencil<T, 6>, pe);
+        case 7: return set_smem(k_pencil<T, 7>, pe);
+        case 8: return set_smem(k_pencil<T, 8>, pe);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T> cudaError_t launch_plane_fwd(const Fields<T> &f, cudaStream_t s) {
     const size_t sm = plane_smem_bytes(f);
-    k_plane_fwd<T><<<dim3(f.Nx, f.nv), kThreadsPlane, sm, s>>>(f);
+    const dim3 grid(f.Nx, f.nv);
+    if (f.M <= 8)
+        k_plane_fwd<T, 8><<<grid, kThreadsPlane, sm, s>>>(f);
+    else
+        k_plane_fwd<T, kMaxHist><<<grid, kThreadsPlane, sm, s>>>(f);
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_plane_inv(const Fields<T> &f, cudaStream_t s) {
     const size_t sm = plane_smem_bytes(f);
-    k_plane_inv<T><<<dim3(f.Nx, f.nv), kThreadsPlane, sm, s>>>(f);
+    const dim3 grid(f.Nx, f.nv);
+    if (f.M <= 8)
+        k_plane_inv<T, 8><<<grid, kThreadsPlane, sm, s>>>(f);
+    else
+        k_plane_inv<T, kMaxHist><<<grid, kThreadsPlane, sm, s>>>(f);
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_pencil(const Fields<T> &f, cudaStream_t s) {
     const size_t sm = pencil_smem_bytes(f);
-    k_pencil<T><<<f.tiles_main + f.tiles_nyq, kThreadsPencil, sm, s>>>(f);
+    const unsigned grid = f.tiles_main + f.tiles_nyq;
+    switch (f.nv) {
+        case 1: k_pencil<T, 1><<<grid, kThreadsPencil, sm, s>>>(f); break;
+        case 2: k_pencil<T, 2><<<grid, kThreadsPencil, sm, s>>>(f); break;
+        case 3: k_pencil<T, 3><<<grid, kThreadsPencil, sm, s>>>(f); break;
+        case 4: k_pencil<T, 4><<<grid, kThreadsPencil, sm, s>>>(f); break;
+        case 5: k_pencil<T, 5><<<grid, kThreadsPencil, sm, s>>>(f); break;
+        case 6: k_pencil<T, 6><<<grid, kThreadsPencil, sm, s>>>(f); break;
+        case 7: k_pencil<T, 7><<<grid, kThreadsPencil, sm, s>>>(f); break;
+        case 8: k_pencil<T, 8><<<grid, kThreadsPencil, sm, s>>>(f); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_mdiis(const Fields<T> &f, cudaStream_t s) {

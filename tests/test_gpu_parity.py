@@ -157,10 +157,15 @@ def test_solve_fp64_charged(water_nacl, kind, order):
 
 @pytest.mark.parametrize("kind,order", [(cl.KH, 1), (cl.PSE, 3)])
 def test_solve_fp32_charged(water_nacl, kind, order):
-    """FP32 form against the oracle converged to 1e-10."""
+    """FP32 form against the oracle converged to 1e-10. The g bar is 1e-3, or 1.5 times the
+    oracle's own truncation at tol 1e-6 where that is larger: near PSE-3 association peaks
+    (g ~ 200) FP64 stopped at RMS 1e-6 already differs from its 1e-10 solution by 8e-3."""
     grid = GRIDS[2]
     sol = charged_solute()
-    P, ref = _oracle(water_nacl, grid, sol, kind, order, 1e-10)
+    P = orc.Problem(water_nacl, grid, sol)
+    ref = orc.solve(P, kind, order, tol=1e-10, mdiis_nvec=5)
+    loose = orc.solve(P, kind, order, tol=1e-6, mdiis_nvec=5)
+    trunc = float(np.max(np.abs(loose["g"] - ref["g"])))
     with solver(water_nacl, grid, 32) as S:
         S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
         rep = S.solve(_sfe_kind(kind), pse_order=order, tol=1e-6)
@@ -168,7 +173,7 @@ def test_solve_fp32_charged(water_nacl, kind, order):
         c = S.get("c")
         sfe, _ = S.sfe(_sfe_kind(kind), order)
     assert rep["converged"]
-    assert np.max(np.abs(g - ref["g"])) <= 1e-3
+    assert np.max(np.abs(g - ref["g"])) <= max(1e-3, 1.5 * trunc)
     sref = orc.sfe(P, ref, {cl.KH: cl.SFE_KH, cl.PSE: cl.SFE_PSE}[kind], order)[0]
     assert abs(sfe - sref) <= 0.05
     assert np.isfinite(c).all()
@@ -207,7 +212,10 @@ def test_full_size_solute50_128(water_nacl, c2_ref, precision, tag, order):
     if precision == 64:
         assert dg <= 1e-6 and dsfe <= 1e-4, (dg, dsfe)
     else:
-        assert dg <= 1e-3 and dsfe <= 0.05, (dg, dsfe)
+        # 1e-3, or 1.5x the oracle's own truncation at tol 1e-6 (see test_solve_fp32_charged)
+        loose = "%s_%g_g" % (tag, 1e-6)
+        trunc = float(np.max(np.abs(c2_ref[loose] - c2_ref[key_ref + "_g"]))) if loose in c2_ref else 0.0
+        assert dg <= max(1e-3, 1.5 * trunc) and dsfe <= 0.05, (dg, dsfe, trunc)
     assert rep["converged"]
 
 
@@ -250,3 +258,23 @@ def test_bitwise_reproducible(water_nacl):
             S.solve("kh", tol=1e-6)
             out.append(S.get("g"))
     assert np.array_equal(out[0], out[1])
+
+
+# ------------------------------------------------------------------ modified Anderson
+@pytest.mark.parametrize("gi", [0, 1])
+def test_solve_fp64_modified_anderson(water_nacl, gi):
+    """The paper's own GPU accelerator (Eqs. 34-39; s1 = 0.2, s2 = 0, b = 0.6) against the
+    oracle running the same accelerator: same iterate sequence, FP64 bars."""
+    grid = GRIDS[gi]
+    sol = charged_solute()
+    P = orc.Problem(water_nacl, grid, sol)
+    ref = orc.solve(P, cl.KH, 1, tol=1e-6, accel="anderson", mdiis_damp=0.6)
+    assert ref["converged"]
+    with solver(water_nacl, grid, 64, accelerator="anderson", mdiis_damp=0.6) as S:
+        S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+        rep = S.solve("kh", tol=1e-6)
+        g = S.get("g")
+        sfe, _ = S.sfe("kh")
+    assert rep["converged"] and abs(rep["iterations"] - ref["iterations"]) <= 1
+    assert np.max(np.abs(g - ref["g"])) <= 1e-6
+    assert abs(sfe - orc.sfe(P, ref, cl.SFE_KH)[0]) <= 1e-4
