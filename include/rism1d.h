@@ -66,6 +66,15 @@ void rism1d_options_default(rism1d_options *opt);
 rism1d_status rism1d_xrism(const rism1d_solvent *solvent, const rism1d_options *opt, double *chi,
                            double *dk, int *iterations, double *rms);
 
+/* As rism1d_xrism, and also (each may be NULL): c_r ([n_sites][n_sites][n_r - 1], the full
+ * direct correlation c = c_s - beta u_L at r_i = i dr, i = 1..n_r-1), the bulk pressure of
+ * Eq. 20, P = sum_G rho_G (n_G + 1) k_B T / 2 - 2 pi k_B T sum_ab rho_a rho_b int c_ab r^2 dr
+ * (kcal/mol/A^3; G runs over species, n_G their site counts), and k_B T chi_T = X_00(0) / rho_0
+ * (A^3; the structure factor of the first site, the molecular centre for water). */
+rism1d_status rism1d_xrism_ex(const rism1d_solvent *solvent, const rism1d_options *opt, double *chi,
+                              double *dk, double *c_r, double *pressure, double *kT_chi_T,
+                              int *iterations, double *rms);
+
 const char *rism1d_last_error(void);
 
 #ifdef __cplusplus

@@ -105,6 +105,9 @@ typedef struct {
                                  the first two steps; mdiis_damp is its mixing b) */
     double anderson_s1;       /* Anderson shift s_1 (paper's value 0.2) */
     double anderson_s2;       /* Anderson shift s_2 (paper's value 0.0) */
+    int slab_rows;            /* 0: whole y-z planes per block when they fit in shared memory,
+                                 else row chunks plus a y-pencil pass (automatic); > 0 forces
+                                 chunks of this many rows */
     void *cuda_stream;        /* cudaStream_t to run on; NULL: the library creates one */
     void *workspace;          /* device buffer of >= rism3d_workspace_bytes bytes, 256-byte
                                  aligned, owned by the caller and kept alive until
@@ -123,8 +126,9 @@ typedef struct {
  * rism3d_reset_stats. Kernel index: 0 plane_fwd (MDIIS update + closure + forward z/y FFT),
  * 1 pencil (x FFT + Eq. 13 contraction + inverse x FFT), 2 plane_inv (inverse y/z FFT +
  * residual + Gram partials), 3 mdiis (Gram reduction + bordered solve), 4 potential
- * (Eqs. 22, 29), 5 long_range (Eq. 30), 6 sfe, 7 other (guess, conversions, field output). */
-#define RISM3D_N_KERNELS 8
+ * (Eqs. 22, 29), 5 long_range (Eq. 30), 6 sfe, 7 other (guess, conversions, field output),
+ * 8 and 9 the forward and inverse y-pencil passes (planes split into row chunks only). */
+#define RISM3D_N_KERNELS 10
 typedef struct {
     long long launches[RISM3D_N_KERNELS];   /* kernels launched (including ones that found the
                                                solve finished and returned at once) */
@@ -189,6 +193,21 @@ rism3d_status rism3d_get(rism3d_ctx *ctx, int field, double *dst, size_t count, 
  * FP64. per_site ([n_sites], host) may be NULL. */
 rism3d_status rism3d_get_sfe(rism3d_ctx *ctx, int kind, int pse_order, double *total,
                              double *per_site);
+
+/* Partial molar volume of Eq. 19, V = k_B T chi_T (1 - sum_g rho_g int c_g(r) dr), in A^3 per
+ * molecule, from the current iterate; kT_chi_T (A^3) is the solvent's k_B T times its
+ * isothermal compressibility (rism1d_xrism_ex reports it). c_integral ([n_sites], host) may
+ * be NULL; it receives int c_g(r) dr as grid sums. The pressure correction of Eq. 21 is
+ * -P * V with the bulk pressure P of Eq. 20 (rism1d_xrism_ex). */
+rism3d_status rism3d_get_pmv(rism3d_ctx *ctx, double kT_chi_T, double *pmv, double *c_integral);
+
+/* Derivative of the SFE with respect to every solute atom position (the second "Eq. 21",
+ * Hybrid implementation section): grad[a][k] = sum_g rho_g dV sum_grid g_g(r) du_g(r)/dR_a,k
+ * in kcal/mol/A, with du/dR the analytic derivative of Eq. 22's pair terms (Lorentz-Berthelot
+ * mixing, r^2 floored at 1e-8 A^2). grad is host [n_atoms][3]. For a neutral solute this is the
+ * exact derivative of the KH/HNC SFE on the grid; for a charged one it omits the dependence of
+ * the long-range split (Eqs. 29-30) on the atom positions. */
+rism3d_status rism3d_get_sfe_gradient(rism3d_ctx *ctx, double *grad);
 
 /* Copy the counters; timing fields are zero unless the context was created with timing = 1. */
 rism3d_status rism3d_get_stats(const rism3d_ctx *ctx, rism3d_stats *out);

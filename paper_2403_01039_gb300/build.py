@@ -17,6 +17,8 @@ LIB = os.path.join(OUT_DIR, "librism3d.so")
 SOURCES = ["rism3d_kernels.cu", "rism3d_capi.cu", "rism3d_noalloc.cu", "rism1d.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+if os.environ.get("RISM_MINBLOCKS_F32"):
+    FLAGS.append("-DRISM_MINBLOCKS_F32=%d" % int(os.environ["RISM_MINBLOCKS_F32"]))
 
 
 def _nvcc():

@@ -40,12 +40,14 @@ class Options(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("max_atoms", ctypes.c_int), ("timing", ctypes.c_int),
                 ("accelerator", ctypes.c_int), ("anderson_s1", ctypes.c_double),
-                ("anderson_s2", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
+                ("anderson_s2", ctypes.c_double), ("slab_rows", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
-N_KERNELS = 8
-KERNEL_NAMES = ["plane_fwd", "pencil", "plane_inv", "mdiis", "potential", "long_range", "sfe", "other"]
+N_KERNELS = 10
+KERNEL_NAMES = ["plane_fwd", "pencil", "plane_inv", "mdiis", "potential", "long_range", "sfe", "other",
+                "ypencil_fwd", "ypencil_inv"]
 
 
 class Stats(ctypes.Structure):
@@ -84,6 +86,8 @@ def load():
         "rism3d_residual": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),
         "rism3d_get": (c_int, [c_void_p, c_int, c_void_p, c_size_t, c_int]),
         "rism3d_get_sfe": (c_int, [c_void_p, c_int, c_int, P(c_double), _dp]),
+        "rism3d_get_pmv": (c_int, [c_void_p, c_double, P(c_double), _dp]),
+        "rism3d_get_sfe_gradient": (c_int, [c_void_p, _dp]),
         "rism3d_get_stats": (c_int, [c_void_p, P(Stats)]),
         "rism3d_reset_stats": (c_int, [c_void_p]),
         "rism3d_last_error": (ctypes.c_char_p, [c_void_p]),
@@ -94,6 +98,8 @@ def load():
                                        c_double, c_double, c_int, c_int, P(c_double), _dp, c_void_p]),
         "rism1d_options_default": (None, [P(Rism1dOptions)]),
         "rism1d_xrism": (c_int, [P(Rism1dSolvent), P(Rism1dOptions), _dp, _dp, P(c_int), _dp]),
+        "rism1d_xrism_ex": (c_int, [P(Rism1dSolvent), P(Rism1dOptions), _dp, _dp, _dp, _dp, _dp,
+                                    P(c_int), _dp]),
         "rism1d_last_error": (ctypes.c_char_p, []),
     })
     for name, (res, args) in sig.items():
@@ -185,9 +191,11 @@ def sfe_noalloc(h, c, rho, temperature, dV, kind="kh", pse_order=3, d=None, stre
     return tot.value, per
 
 
-def xrism(sites, n_r=2048, dr=0.05, closure="kh", tol=1e-10, charge_steps=10):
+def xrism(sites, n_r=2048, dr=0.05, closure="kh", tol=1e-10, charge_steps=10, thermo=False):
     """Solvent susceptibility X_ag(k_j), k_j = j dk, of a pure solvent (Eq. 4) from the
-    library's host 1D-RISM solver. Returns (chi [n][n][n_r], dk, iterations, rms)."""
+    library's host 1D-RISM solver. Returns (chi [n][n][n_r], dk, iterations, rms); with
+    thermo=True also a dict with the full direct correlation c [n][n][n_r - 1] at r_i = i dr,
+    the bulk pressure of Eq. 20 (kcal/mol/A^3) and k_B T chi_T (A^3)."""
     lib = load()
     keep = {k: _arr(sites[k]) for k in ("q", "sigma", "eps", "rho")}
     species = np.ascontiguousarray(sites["species"], dtype=np.int32)
@@ -201,13 +209,18 @@ def xrism(sites, n_r=2048, dr=0.05, closure="kh", tol=1e-10, charge_steps=10):
     o.n_r, o.dr, o.tol, o.charge_steps = int(n_r), float(dr), float(tol), int(charge_steps)
     o.closure = {"kh": 1, "hnc": 2}[closure]
     chi = np.zeros((n, n, n_r))
-    dk = ctypes.c_double()
+    c_r = np.zeros((n, n, n_r - 1))
+    dk, pres, ktchi = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     its = ctypes.c_int()
     rms = ctypes.c_double()
-    st = lib.rism1d_xrism(ctypes.byref(sv), ctypes.byref(o), chi.ctypes.data_as(_dp), ctypes.byref(dk),
-                          ctypes.byref(its), ctypes.byref(rms))
+    st = lib.rism1d_xrism_ex(ctypes.byref(sv), ctypes.byref(o), chi.ctypes.data_as(_dp), ctypes.byref(dk),
+                             c_r.ctypes.data_as(_dp) if thermo else None,
+                             ctypes.byref(pres) if thermo else None,
+                             ctypes.byref(ktchi) if thermo else None, ctypes.byref(its), ctypes.byref(rms))
     if st != 0:
         raise RuntimeError("rism1d_xrism failed (%d): %s" % (st, lib.rism1d_last_error().decode()))
+    if thermo:
+        return chi, dk.value, its.value, rms.value, dict(c=c_r, pressure=pres.value, kT_chi_T=ktchi.value)
     return chi, dk.value, its.value, rms.value
 
 
@@ -216,8 +229,8 @@ class Solver:
 
     def __init__(self, solvent, grid, precision=32, mdiis_nvec=5, mdiis_damp=0.7,
                  dynamic_damp=False, max_iter=10000, check_every=8, max_atoms=100000,
-                 timing=False, accelerator="mdiis", anderson_s=(0.2, 0.0), stream=None,
-                 device=None):
+                 timing=False, accelerator="mdiis", anderson_s=(0.2, 0.0), slab_rows=0,
+                 stream=None, device=None):
         import torch
         self._torch = torch
         lib = load()
@@ -239,6 +252,7 @@ class Solver:
         o.timing = int(bool(timing))
         o.accelerator = {"mdiis": 0, "anderson": 1}[accelerator]
         o.anderson_s1, o.anderson_s2 = float(anderson_s[0]), float(anderson_s[1])
+        o.slab_rows = int(slab_rows)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
             o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
@@ -287,6 +301,7 @@ class Solver:
         s, ps = _arr(sigma)
         e, pe = _arr(eps)
         _check(self.lib, self.ctx, self.lib.rism3d_set_solute(self.ctx, len(q), pxyz, pq, ps, pe))
+        self.n_atoms = len(q)
 
     def set_guess(self, t):
         p, dev, keep = self._field_arg(t)
@@ -342,6 +357,21 @@ class Solver:
         _check(self.lib, self.ctx, self.lib.rism3d_get_sfe(self.ctx, SFE_KINDS[kind], int(pse_order),
                                                            ctypes.byref(tot), per.ctypes.data_as(_dp)))
         return tot.value, per
+
+    def pmv(self, kT_chi_T):
+        """Partial molar volume (Eq. 19, A^3) and the per-site c integrals of the current
+        iterate, given the solvent's k_B T chi_T (A^3)."""
+        v = ctypes.c_double()
+        ci = np.zeros(self.n_sites)
+        _check(self.lib, self.ctx, self.lib.rism3d_get_pmv(self.ctx, float(kT_chi_T), ctypes.byref(v),
+                                                           ci.ctypes.data_as(_dp)))
+        return v.value, ci
+
+    def sfe_gradient(self):
+        """dSFE/dR of every solute atom (kcal/mol/A), [n_atoms, 3]."""
+        g = np.zeros((getattr(self, "n_atoms", 0), 3))
+        _check(self.lib, self.ctx, self.lib.rism3d_get_sfe_gradient(self.ctx, g.ctypes.data_as(_dp)))
+        return g
 
     def stats(self):
         st = Stats()

@@ -145,6 +145,12 @@ void rism1d_options_default(rism1d_options *o) {
 
 rism1d_status rism1d_xrism(const rism1d_solvent *sv, const rism1d_options *op, double *chi, double *dk_out,
                            int *iterations, double *rms_out) {
+    return rism1d_xrism_ex(sv, op, chi, dk_out, nullptr, nullptr, nullptr, iterations, rms_out);
+}
+
+rism1d_status rism1d_xrism_ex(const rism1d_solvent *sv, const rism1d_options *op, double *chi, double *dk_out,
+                              double *c_r, double *pressure, double *kT_chi_T, int *iterations,
+                              double *rms_out) {
     if (!sv || !op || !chi || !dk_out) return fail(RISM1D_EINVAL, "null argument");
     const int n = sv->n_sites, N = op->n_r;
     if (n < 1 || n > 16) return fail(RISM1D_EINVAL, "n_sites must be in 1..16");
@@ -323,6 +329,41 @@ rism1d_status rism1d_xrism(const rism1d_solvent *sv, const rism1d_options *op, d
             row[0] = w0 + sv->rho[a] * h0;
             for (int j = 0; j < P; ++j) row[j + 1] = W[at(a, b) + j] + sv->rho[a] * H[at(a, b) + j];
         }
+    // full direct correlation c = c_s - beta u_L (Coulomb tail of Eq. 29's form) at full charge
+    if (c_r || pressure) {
+        std::vector<double> cfull(F);
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+                const double qq = sv->q[a] * sv->q[b];
+                for (int i = 0; i < P; ++i) {
+                    const double x = at(a, b) + i;
+                    (void)x;
+                    cfull[at(a, b) + i] = cs[at(a, b) + i] - beta * kCoulomb * qq * (-std::expm1(-r[i])) / r[i];
+                }
+            }
+        if (c_r) std::copy(cfull.begin(), cfull.end(), c_r);
+        if (pressure) {
+            const double kT = 1.0 / beta;
+            double ideal = 0.0;
+            std::vector<int> seen;
+            for (int a = 0; a < n; ++a) {
+                if (std::find(seen.begin(), seen.end(), sv->species[a]) != seen.end()) continue;
+                seen.push_back(sv->species[a]);
+                int nsites = 0;
+                for (int b = 0; b < n; ++b) nsites += sv->species[b] == sv->species[a];
+                ideal += sv->rho[a] * (nsites + 1) * kT / 2.0;
+            }
+            double ex = 0.0;
+            for (int a = 0; a < n; ++a)
+                for (int b = 0; b < n; ++b) {
+                    double integ = 0.0;
+                    for (int i = 0; i < P; ++i) integ += r[i] * r[i] * cfull[at(a, b) + i];
+                    ex += sv->rho[a] * sv->rho[b] * integ * dr;
+                }
+            *pressure = ideal - 2.0 * kPi * kT * ex;
+        }
+    }
+    if (kT_chi_T) *kT_chi_T = chi[0] / sv->rho[0];
     *dk_out = dk;
     if (iterations) *iterations = total;
     if (rms_out) *rms_out = rms;

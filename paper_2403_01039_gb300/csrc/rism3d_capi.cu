@@ -4,6 +4,7 @@
 // (unit conversion, table scaling, twiddle factors) and schedules launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -24,6 +25,8 @@ constexpr double kCoulomb = 332.0637;     // kcal A / (mol e^2)
 constexpr double kPi = 3.14159265358979323846;
 constexpr size_t kMaxSmem = 227 * 1024;
 constexpr size_t kPencilSmemTarget = 64 * 1024;
+constexpr size_t kSlabSmemTarget = 72 * 1024;   // row-chunk size when a plane does not fit
+constexpr int kEventsPerIter = 7;                 // up to six kernels per iteration
 
 thread_local std::string g_create_error;
 
@@ -80,6 +83,18 @@ bool make_plan(int L, FftPlan &p) {
     return true;
 }
 
+// Sequences one warp can transform together while each lane holds at most maxc values in
+// every stage (0 when a single sequence does not fit: the block-wide path is used).
+int warp_seqs(const FftPlan &p, int maxc) {
+    int cap = 1 << 30;
+    for (int s = 0; s < p.nst; ++s) {
+        const int R = p.radix[s];
+        const int c = 32 * (maxc / R) * R;          // values one warp holds in this stage
+        cap = c < cap ? c : cap;
+    }
+    return cap / p.L;
+}
+
 // Largest batch chunk for which every stage keeps at most MAXC / R butterflies per thread.
 int fft_chunk(const FftPlan &p, int nthreads, int maxc) {
     int chunk = 1 << 30;
@@ -112,6 +127,8 @@ struct rism3d_ctx {
     // device pointers inside the workspace
     Ctrl *ctrl = nullptr;
     double *atoms = nullptr, *site_sig = nullptr, *site_eps = nullptr, *site_q = nullptr;
+    double *site_rho_dV = nullptr;
+    int n_atoms = 0;
     double *sfe_part = nullptr, *staging = nullptr;
     Fields<float> f32{};
     Fields<double> f64{};
@@ -158,7 +175,8 @@ static rism3d_status fail(rism3d_ctx *ctx, rism3d_status st, const char *fmt, ..
 namespace {
 
 struct Layout {
-    size_t ctrl, bu, phi, w, psi, spec, X, R, anchor, table, tw, partials, sfe, atoms, sites, staging, total;
+    size_t ctrl, bu, phi, w, psi, spec, X, R, anchor, phase, table, tw, partials, sfe, atoms, sites, staging,
+        total;
 };
 
 struct Geometry {
@@ -166,7 +184,8 @@ struct Geometry {
     long long G;
     FftPlan px, py, ph;
     int pitch, W, pencil_pitch, chunk_rows, chunk_cols, chunk_x;
-    size_t plane_smem, pencil_smem;
+    int slab_rows, nyc, Wy, ypitch, chunk_y;
+    size_t plane_smem, pencil_smem, ypencil_smem;
 };
 
 Layout make_layout(const Geometry &g) {
@@ -188,12 +207,13 @@ Layout make_layout(const Geometry &g) {
     L.X = take((size_t)g.M * g.nv * g.G * g.s);
     L.R = take((size_t)g.M * g.nv * g.G * g.s);
     L.anchor = take((size_t)2 * g.nv * g.G * g.s);
+    L.phase = take((size_t)kPhaseChunk * (g.Nx + g.Ny + g.Kz + 1) * c);
     L.table = take((size_t)g.nk * (g.nv + 1) * g.nv * g.s);
     L.tw = take((size_t)(g.Nx + g.Ny + g.Kz + g.Kz + 1) * c);
-    L.partials = take((size_t)g.nv * g.Nx * (kMaxHist + 1) * sizeof(double));
+    L.partials = take((size_t)g.nv * g.Nx * g.nyc * (kMaxHist + 1) * sizeof(double));
     L.sfe = take((size_t)g.nv * kSfeBlocksPerSite * sizeof(double));
     L.atoms = take((size_t)g.max_atoms * kAtomStride * sizeof(double));
-    L.sites = take((size_t)3 * kMaxSites * sizeof(double));
+    L.sites = take((size_t)4 * kMaxSites * sizeof(double));
     L.staging = take((size_t)g.nv * g.G * sizeof(double));
     L.total = o;
     return L;
@@ -222,6 +242,7 @@ rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, cons
         return fail(nullptr, RISM3D_EINVAL, "mdiis_nvec must be in 1..%d", kMaxHist);
     if (!(op->mdiis_damp > 0.0 && op->mdiis_damp <= 2.0))
         return fail(nullptr, RISM3D_EINVAL, "mdiis_damp must be in (0, 2]");
+    if (op->slab_rows < 0) return fail(nullptr, RISM3D_EINVAL, "slab_rows must be >= 0");
     if (op->accelerator != 0 && op->accelerator != 1)
         return fail(nullptr, RISM3D_EINVAL, "accelerator must be 0 (MDIIS) or 1 (modified Anderson)");
     if (op->max_iter < 1 || op->check_every < 1 || op->max_atoms < 1)
@@ -242,12 +263,35 @@ rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, cons
     const size_t c = 2 * (size_t)g.s;
     g.pitch = g.Kz + 1;
     if (g.pitch % 2 == 0) g.pitch += 1;        // odd pitch: column access without bank conflicts
-    g.plane_smem = c * ((size_t)g.Ny * g.pitch + g.Kz + g.Ny + g.Kz + 1) +
-                   (kMaxHist + 1) * (kThreadsPlane / 32) * sizeof(double) + 16;
+    auto plane_bytes = [&](int rows) {
+        return c * ((size_t)rows * g.pitch + g.Kz + g.Ny + g.Kz + 1) +
+               (kMaxHist + 1) * (kThreadsPlane / 32) * sizeof(double) + 16;
+    };
+    // whole y-z planes when they fit in shared memory, else row chunks + a y-pencil pass
+    g.slab_rows = g.Ny;
+    if (op->slab_rows > 0) {
+        g.slab_rows = op->slab_rows < g.Ny ? op->slab_rows : g.Ny;
+    } else if (plane_bytes(g.Ny) > kMaxSmem) {
+        int r = 1;
+        while (2 * r <= g.Ny && plane_bytes(2 * r) <= kSlabSmemTarget) r *= 2;
+        g.slab_rows = r;
+    }
+    g.nyc = (g.Ny + g.slab_rows - 1) / g.slab_rows;
+    g.plane_smem = plane_bytes(g.slab_rows);
     if (g.plane_smem > kMaxSmem)
         return fail(nullptr, RISM3D_EUNSUPPORTED,
-                    "a y-z plane (%d x %d) needs %zu bytes of shared memory (limit %zu)", g.Ny,
+                    "a row chunk of %d rows x %d needs %zu bytes of shared memory (limit %zu)", g.slab_rows,
                     g.Kz + 1, g.plane_smem, kMaxSmem);
+    g.ypitch = g.Ny + 1;
+    g.Wy = 1;
+    for (int w = 16; w >= 1; w /= 2)
+        if (c * ((size_t)g.nv * w * g.ypitch + g.Ny) <= kPencilSmemTarget || w == 1) {
+            g.Wy = w;
+            break;
+        }
+    g.ypencil_smem = c * ((size_t)g.nv * g.Wy * g.ypitch + g.Ny);
+    if (g.nyc > 1 && g.ypencil_smem > kMaxSmem)
+        return fail(nullptr, RISM3D_EUNSUPPORTED, "y pencils of %d points do not fit in shared memory", g.Ny);
     g.pencil_pitch = g.Nx + 1;
     g.W = 1;
     for (int w = 16; w >= 1; w /= 2) {
@@ -261,10 +305,14 @@ rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, cons
     if (g.pencil_smem > kMaxSmem)
         return fail(nullptr, RISM3D_EUNSUPPORTED, "x pencils of %d points do not fit in shared memory",
                     g.Nx);
+    g.px.seq_per_warp = warp_seqs(g.px, maxc);
+    g.py.seq_per_warp = warp_seqs(g.py, maxc);
+    g.ph.seq_per_warp = warp_seqs(g.ph, maxc);
     g.chunk_rows = fft_chunk(g.ph, kThreadsPlane, maxc);
     g.chunk_cols = fft_chunk(g.py, kThreadsPlane, maxc);
     g.chunk_x = fft_chunk(g.px, kThreadsPencil, maxc);
-    if (g.chunk_rows < 1 || g.chunk_cols < 1 || g.chunk_x < 1)
+    g.chunk_y = fft_chunk(g.py, kThreadsPencil, maxc);
+    if (g.chunk_rows < 1 || g.chunk_cols < 1 || g.chunk_x < 1 || g.chunk_y < 1)
         return fail(nullptr, RISM3D_EUNSUPPORTED, "transform length too long for one block");
     return RISM3D_OK;
 }
@@ -292,6 +340,7 @@ void fill_fields(rism3d_ctx *ctx, const Geometry &g, const Layout &L, Fields<T> 
     f.R = reinterpret_cast<T *>(b + L.R);
     f.csr_a = reinterpret_cast<T *>(b + L.anchor);
     f.h_a = f.csr_a + (long long)g.nv * g.G;
+    f.phase = reinterpret_cast<C *>(b + L.phase);
     f.table = reinterpret_cast<T *>(b + L.table);
     f.nk = g.nk;
     C *tw = reinterpret_cast<C *>(b + L.tw);
@@ -306,6 +355,13 @@ void fill_fields(rism3d_ctx *ctx, const Geometry &g, const Layout &L, Fields<T> 
     f.chunk_cols_fwd = g.chunk_cols;
     f.chunk_x = g.chunk_x;
     f.pitch = g.pitch;
+    f.slab_rows = g.slab_rows;
+    f.nyc = g.nyc;
+    f.Wy = g.Wy;
+    f.ypitch = g.ypitch;
+    f.ytiles_main = g.Nx * ((g.Kz + g.Wy - 1) / g.Wy);
+    f.ytiles_nyq = (g.Nx + g.Wy - 1) / g.Wy;
+    f.chunk_y = g.chunk_y;
     f.W = g.W;
     f.pencil_pitch = g.pencil_pitch;
     f.tiles_main = g.Ny * ((g.Kz + g.W - 1) / g.W);
@@ -387,12 +443,42 @@ void closure_stages(int kind, int order, double tol, Ctrl &c) {
     for (int i = 0; i < n; ++i) c.stage_tol[i] = (i == n - 1) ? tol : stage_tol;
 }
 
+// The kernels of one iteration in order, with their stats slots: plane_fwd (0),
+// [y pencils forward (8)], pencil (1), [y pencils inverse (9)], plane_inv (2), mdiis (3).
+template <typename T>
+rism3d_status launch_step(rism3d_ctx *ctx, const Fields<T> &f, int slot) {
+    switch (slot) {
+        case 0: CUDA_TRY(ctx, launch_plane_fwd<T>(f, ctx->stream)); break;
+        case 8: CUDA_TRY(ctx, launch_ypencil<T>(f, -1, ctx->stream)); break;
+        case 1: CUDA_TRY(ctx, launch_pencil<T>(f, ctx->stream)); break;
+        case 9: CUDA_TRY(ctx, launch_ypencil<T>(f, +1, ctx->stream)); break;
+        case 2: CUDA_TRY(ctx, launch_plane_inv<T>(f, ctx->stream)); break;
+        case 3: CUDA_TRY(ctx, launch_mdiis<T>(f, ctx->stream)); break;
+        default: break;
+    }
+    return RISM3D_OK;
+}
+
+int iteration_slots(const rism3d_ctx *ctx, bool with_mdiis, int *slots) {
+    const bool split = (ctx->fp32() ? ctx->f32.nyc : ctx->f64.nyc) > 1;
+    int n = 0;
+    slots[n++] = 0;
+    if (split) slots[n++] = 8;
+    slots[n++] = 1;
+    if (split) slots[n++] = 9;
+    slots[n++] = 2;
+    if (with_mdiis) slots[n++] = 3;
+    return n;
+}
+
 template <typename T>
 rism3d_status run_iteration_kernels(rism3d_ctx *ctx, const Fields<T> &f, bool with_mdiis) {
-    CUDA_TRY(ctx, launch_plane_fwd<T>(f, ctx->stream));
-    CUDA_TRY(ctx, launch_pencil<T>(f, ctx->stream));
-    CUDA_TRY(ctx, launch_plane_inv<T>(f, ctx->stream));
-    if (with_mdiis) CUDA_TRY(ctx, launch_mdiis<T>(f, ctx->stream));
+    int slots[8];
+    const int n = iteration_slots(ctx, with_mdiis, slots);
+    for (int i = 0; i < n; ++i) {
+        rism3d_status st = launch_step<T>(ctx, f, slots[i]);
+        if (st != RISM3D_OK) return st;
+    }
     return RISM3D_OK;
 }
 
@@ -419,7 +505,12 @@ void account_iterations(rism3d_ctx *ctx, const Ctrl &c) {
     ctx->stats.bytes[1] += P * s * z * (2.0 * it + (double)c.acc_psi / ctx->nv);
     ctx->stats.bytes[2] += P * s * (it * (z + 3.0) + (double)c.acc_hist + (double)c.acc_anchor +
                                     (double)c.acc_refresh);
-    ctx->stats.bytes[3] += 8.0 * ctx->nv * ctx->Nx * (it + (double)c.acc_hist);
+    const int nyc = ctx->fp32() ? ctx->f32.nyc : ctx->f64.nyc;
+    ctx->stats.bytes[3] += 8.0 * ctx->nv * ctx->Nx * nyc * (it + (double)c.acc_hist);
+    if (nyc > 1) {                    // y pencils read and write the spectrum
+        ctx->stats.bytes[8] += P * s * z * 2.0 * it;
+        ctx->stats.bytes[9] += P * s * z * 2.0 * it;
+    }
 }
 
 // Event pair around a direct (non-graph) launch of kernel k, when timing is on.
@@ -448,15 +539,14 @@ template <typename T>
 rism3d_status timed_iteration(rism3d_ctx *ctx, const Fields<T> &f, cudaEvent_t *e) {
     // external records: captured into the graph as event-record nodes that time each kernel
     const unsigned x = cudaEventRecordExternal;
+    int slots[8];
+    const int n = iteration_slots(ctx, true, slots);
     CUDA_TRY(ctx, cudaEventRecordWithFlags(e[0], ctx->stream, x));
-    CUDA_TRY(ctx, launch_plane_fwd<T>(f, ctx->stream));
-    CUDA_TRY(ctx, cudaEventRecordWithFlags(e[1], ctx->stream, x));
-    CUDA_TRY(ctx, launch_pencil<T>(f, ctx->stream));
-    CUDA_TRY(ctx, cudaEventRecordWithFlags(e[2], ctx->stream, x));
-    CUDA_TRY(ctx, launch_plane_inv<T>(f, ctx->stream));
-    CUDA_TRY(ctx, cudaEventRecordWithFlags(e[3], ctx->stream, x));
-    CUDA_TRY(ctx, launch_mdiis<T>(f, ctx->stream));
-    CUDA_TRY(ctx, cudaEventRecordWithFlags(e[4], ctx->stream, x));
+    for (int i = 0; i < n; ++i) {
+        rism3d_status st = launch_step<T>(ctx, f, slots[i]);
+        if (st != RISM3D_OK) return st;
+        CUDA_TRY(ctx, cudaEventRecordWithFlags(e[i + 1], ctx->stream, x));
+    }
     return RISM3D_OK;
 }
 
@@ -465,15 +555,15 @@ rism3d_status build_graph(rism3d_ctx *ctx) {
     cudaGraph_t g = nullptr;
     const int K = ctx->opt.check_every;
     if (ctx->opt.timing && ctx->ev.empty()) {
-        ctx->ev.assign((size_t)K * 5, nullptr);
+        ctx->ev.assign((size_t)K * kEventsPerIter, nullptr);
         for (auto &e : ctx->ev) CUDA_TRY(ctx, cudaEventCreate(&e));
     }
     CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     rism3d_status st = RISM3D_OK;
     for (int i = 0; i < K && st == RISM3D_OK; ++i) {
         if (ctx->opt.timing)
-            st = ctx->fp32() ? timed_iteration<float>(ctx, ctx->f32, &ctx->ev[(size_t)i * 5])
-                             : timed_iteration<double>(ctx, ctx->f64, &ctx->ev[(size_t)i * 5]);
+            st = ctx->fp32() ? timed_iteration<float>(ctx, ctx->f32, &ctx->ev[(size_t)i * kEventsPerIter])
+                             : timed_iteration<double>(ctx, ctx->f64, &ctx->ev[(size_t)i * kEventsPerIter]);
         else
             st = iteration(ctx, true);
     }
@@ -656,13 +746,15 @@ rism3d_status rism3d_create(const rism3d_solvent *sv, const rism3d_grid *gr, con
     ctx->site_sig = reinterpret_cast<double *>(b + L.sites);
     ctx->site_eps = ctx->site_sig + kMaxSites;
     ctx->site_q = ctx->site_eps + kMaxSites;
+    ctx->site_rho_dV = ctx->site_q + kMaxSites;
     ctx->sfe_part = reinterpret_cast<double *>(b + L.sfe);
     ctx->staging = reinterpret_cast<double *>(b + L.staging);
-    double sites[3 * kMaxSites] = {0};
+    double sites[4 * kMaxSites] = {0};
     for (int i = 0; i < g.nv; ++i) {
         sites[i] = ctx->sig[i];
         sites[kMaxSites + i] = ctx->eps[i];
         sites[2 * kMaxSites + i] = ctx->q[i];
+        sites[3 * kMaxSites + i] = ctx->rho[i] * ctx->dV;
     }
     if (cudaMemcpy(ctx->site_sig, sites, sizeof(sites), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(fail(ctx, RISM3D_ECUDA, "upload of solvent sites failed"));
@@ -737,6 +829,7 @@ rism3d_status rism3d_set_solute(rism3d_ctx *ctx, int n_atoms, const double *xyz,
         tm.stop(P * sb);
     }
     ctx->cur_slot = 0;
+    ctx->n_atoms = n_atoms;
     ctx->has_solute = true;
     ctx->last_kind = kKH;
     ctx->last_order = 1;
@@ -777,14 +870,17 @@ rism3d_status rism3d_solve(rism3d_ctx *ctx, int closure, int pse_order, double t
         CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         const int ran = c.iter - iter_before;
         iter_before = c.iter;
-        for (int k = 0; k < 4; ++k) ctx->stats.launches[k] += K;
+        int slots[8];
+        const int nk = iteration_slots(ctx, true, slots);
+        for (int k = 0; k < nk; ++k) ctx->stats.launches[slots[k]] += K;
         if (ctx->opt.timing) {
             for (int i = 0; i < ran && i < K; ++i)
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < nk; ++k) {
                     float ms = 0.f;
-                    CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev[(size_t)i * 5 + k], ctx->ev[(size_t)i * 5 + k + 1]));
-                    ctx->stats.ms[k] += ms;
-                    ctx->stats.timed[k] += 1;
+                    const size_t e0 = (size_t)i * kEventsPerIter + k;
+                    CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev[e0], ctx->ev[e0 + 1]));
+                    ctx->stats.ms[slots[k]] += ms;
+                    ctx->stats.timed[slots[k]] += 1;
                 }
         }
         if (c.status != kRunning) break;
@@ -828,7 +924,11 @@ rism3d_status rism3d_residual(rism3d_ctx *ctx, int closure, int pse_order, const
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, ctx->stream));
     st = iteration(ctx, false);
     if (st != RISM3D_OK) return st;
-    for (int kk = 0; kk < 3; ++kk) ctx->stats.launches[kk] += 1;
+    {
+        int slots[8];
+        const int nk = iteration_slots(ctx, false, slots);
+        for (int kk = 0; kk < nk; ++kk) ctx->stats.launches[slots[kk]] += 1;
+    }
     const int k = c.stage_kind[0], o = c.stage_order[0];
     st = field_out(ctx, RISM3D_R, 0, k, o, R, (size_t)ctx->nv * ctx->G, on_device);
     // leave the device idle
@@ -878,6 +978,71 @@ rism3d_status rism3d_get_sfe(rism3d_ctx *ctx, int kind, int pse_order, double *t
         tot += v;
     }
     *total = tot;
+    return RISM3D_OK;
+}
+
+rism3d_status rism3d_get_pmv(rism3d_ctx *ctx, double kT_chi_T, double *pmv, double *c_integral) {
+    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+    if (!pmv || !(kT_chi_T > 0.0)) return fail(ctx, RISM3D_EINVAL, "need pmv and kT_chi_T > 0");
+    if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "get_pmv before set_solute");
+    DeviceGuard dg(ctx->device);
+    {
+        AuxTimer tm(ctx, 6);
+        if (ctx->fp32())
+            CUDA_TRY(ctx, launch_sfe<float>(ctx->f32, ctx->cur_slot, ctx->last_kind, ctx->last_order, 5, 1,
+                                            ctx->sfe_part, kSfeBlocksPerSite, ctx->stream));
+        else
+            CUDA_TRY(ctx, launch_sfe<double>(ctx->f64, ctx->cur_slot, ctx->last_kind, ctx->last_order, 5, 1,
+                                             ctx->sfe_part, kSfeBlocksPerSite, ctx->stream));
+        tm.stop(2.0 * ctx->nv * ctx->G * (ctx->fp32() ? 4.0 : 8.0));
+    }
+    std::vector<double> part((size_t)ctx->nv * kSfeBlocksPerSite);
+    CUDA_TRY(ctx, cudaMemcpyAsync(part.data(), ctx->sfe_part, part.size() * sizeof(double),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    double rc = 0.0;
+    for (int g = 0; g < ctx->nv; ++g) {
+        double sum = 0.0;
+        for (int b = 0; b < kSfeBlocksPerSite; ++b) sum += part[(size_t)g * kSfeBlocksPerSite + b];
+        const double ci = ctx->dV * sum;
+        if (c_integral) c_integral[g] = ci;
+        rc += ctx->rho[g] * ci;
+    }
+    *pmv = kT_chi_T * (1.0 - rc);
+    return RISM3D_OK;
+}
+
+rism3d_status rism3d_get_sfe_gradient(rism3d_ctx *ctx, double *grad) {
+    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+    if (!grad) return fail(ctx, RISM3D_EINVAL, "null grad");
+    if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "get_sfe_gradient before set_solute");
+    DeviceGuard dg(ctx->device);
+    // partial sums and results in the FP64 staging field, atoms taken in chunks that fit
+    const long long cap = (long long)ctx->nv * ctx->G;
+    const long long per_atom = 3LL * kGradBlocks + 3;
+    int chunk = (int)std::min<long long>(ctx->n_atoms, cap / per_atom);
+    if (chunk < 1) return fail(ctx, RISM3D_EUNSUPPORTED, "grid too small for the gradient scratch");
+    for (int a0 = 0; a0 < ctx->n_atoms; a0 += chunk) {
+        const int na = std::min(chunk, ctx->n_atoms - a0);
+        double *part = ctx->staging;
+        double *out = ctx->staging + (long long)na * 3 * kGradBlocks;
+        const double *atoms = ctx->atoms + (long long)a0 * kAtomStride;
+        AuxTimer tm(ctx, 7);
+        if (ctx->fp32())
+            CUDA_TRY(ctx, launch_sfe_gradient<float>(ctx->f32, ctx->cur_slot, ctx->last_kind, ctx->last_order,
+                                                     ctx->site_rho_dV, atoms, na, ctx->site_sig, ctx->site_eps,
+                                                     ctx->site_q, ctx->origin, ctx->spacing, part, out,
+                                                     ctx->stream));
+        else
+            CUDA_TRY(ctx, launch_sfe_gradient<double>(ctx->f64, ctx->cur_slot, ctx->last_kind, ctx->last_order,
+                                                      ctx->site_rho_dV, atoms, na, ctx->site_sig, ctx->site_eps,
+                                                      ctx->site_q, ctx->origin, ctx->spacing, part, out,
+                                                      ctx->stream));
+        tm.stop((double)ctx->nv * ctx->G * (ctx->fp32() ? 4.0 : 8.0));
+        CUDA_TRY(ctx, cudaMemcpyAsync(grad + (size_t)a0 * 3, out, (size_t)na * 3 * sizeof(double),
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    }
     return RISM3D_OK;
 }
 

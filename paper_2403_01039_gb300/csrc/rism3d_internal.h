@@ -22,6 +22,7 @@ struct FftPlan {
     int L;
     int nst;
     int radix[kMaxRadixStages];
+    int seq_per_warp;               // > 0: warp-cooperative transform of this many sequences
 };
 
 // Device-resident solver state. The iteration kernels read it on every launch, so one
@@ -86,6 +87,7 @@ struct Fields {
     C *spec, *spec_nyq;             // [nv][Nx][Ny][Kz], [nv][Nx][Ny]
     T *X, *R;                       // ring [M][nv][G]: X holds tau = t - f, R the residual
     T *csr_a, *h_a;                 // anchor fields [nv][G]
+    C *phase;                       // per-atom axis phase tables [kPhaseChunk][Nx + Ny + Kz + 1]
     T *table;                       // [nk][nv + 1][nv]: X_ag / G and the charge row -Q_g / G
     int nk;
     double inv_dk;
@@ -93,12 +95,14 @@ struct Fields {
     FftPlan px, py, ph;
     int chunk_rows, chunk_cols_fwd, chunk_x;   // batch chunk sizes of the in-place FFTs
     int pitch;                      // complex row pitch of a plane in shared memory
+    int slab_rows, nyc;             // rows per plane block and row chunks per plane (1: whole)
+    int Wy, ypitch, ytiles_main, ytiles_nyq, chunk_y;   // y-pencil pass (split planes only)
     int W;                          // columns per pencil tile
     int tiles_main, tiles_nyq;
     int pencil_pitch;
     double bq[kMaxSites];           // beta * q_gamma
     double ks[3];                   // 2 pi / (N d) per axis
-    double *partials;               // [kMaxHist + 1][nv * Nx] (value-major)
+    double *partials;               // [kMaxHist + 1][nv * Nx * nyc] (value-major)
     Ctrl *ctrl;
 };
 
@@ -111,6 +115,7 @@ template <typename T> size_t pencil_smem_bytes(const Fields<T> &f);
 template <typename T> cudaError_t launch_plane_fwd(const Fields<T> &f, cudaStream_t s);
 template <typename T> cudaError_t launch_pencil(const Fields<T> &f, cudaStream_t s);
 template <typename T> cudaError_t launch_plane_inv(const Fields<T> &f, cudaStream_t s);
+template <typename T> cudaError_t launch_ypencil(const Fields<T> &f, int sign, cudaStream_t s);
 template <typename T> cudaError_t launch_mdiis(const Fields<T> &f, cudaStream_t s);
 // atoms: [n][8] doubles: x, y, z (absolute), q, sigma, eps, ux, uy, uz with u = (R - r0) / L
 template <typename T>
@@ -135,7 +140,17 @@ cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sf
 // Message returned by rism3d_last_error(NULL) (thread-local).
 void set_global_error(const char *msg);
 
+// d(SFE)/dR of every atom (second Eq. 21); rho_dV[g] = rho_g dV (device); partials needs
+// n_atoms * 3 * kGradBlocks doubles; out receives [n_atoms][3] (device).
+template <typename T>
+cudaError_t launch_sfe_gradient(const Fields<T> &f, int slot, int kind, int order, const double *rho_dV,
+                                const double *atoms, int n_atoms, const double *site_sig,
+                                const double *site_eps, const double *site_q, const double *origin,
+                                const double *spacing, double *partials, double *out, cudaStream_t s);
+
 constexpr int kSfeBlocksPerSite = 152;
+constexpr int kGradBlocks = 304;
+constexpr int kPhaseChunk = 256;  // atoms per long-range pass (phase-table capacity)
 constexpr size_t kAtomStride = 9;
 
 }  // namespace rism

@@ -23,6 +23,13 @@
 
 #include "rism3d_internal.h"
 
+// Resident blocks per SM the FP32 plane and pencil kernels are compiled for (register budget
+// 65536 / (256 x this)); 3 (80 registers, a few hundred bytes of spills) measured faster
+// than 2 (no spills): these kernels are latency-bound and need the resident warps.
+#ifndef RISM_MINBLOCKS_F32
+#define RISM_MINBLOCKS_F32 3
+#endif
+
 namespace rism {
 
 // ------------------------------------------------------------------ complex helpers
@@ -121,30 +128,59 @@ template <> struct Dft<5> {
 };
 
 // ------------------------------------------------------------------ batched in-place FFT
-// Self-sorting (Stockham) mixed-radix transform of nb sequences of length L held in
-// shared memory (element stride es, sequence stride bs). All threads of the block take
-// part; each stage loads every butterfly input into registers, synchronises, then writes,
-// so the transform runs in place. MAXI bounds the butterflies a thread holds per stage;
-// the host picks the batch chunk so that this bound holds.
-template <typename C, int R, int MAXI>
-__device__ __forceinline__ void fft_stage(C *buf, int L, int es, int nb, int bs, int Ns,
-                                          const C *tw, int sign) {
-    const int LR = L / R;
-    const int items = nb * LR;
-    const int step = L / (Ns * R);
+// Self-sorting (Stockham) mixed-radix transform of nb sequences of length L held in shared
+// memory (element stride es, sequence stride bs). A stage loads every butterfly input into
+// registers, synchronises, then writes, so the transform runs in place. For power-of-two
+// lengths the index arithmetic uses shifts and masks.
+struct StageIdx {
+    int LR, Ns, step;
+    bool pow2;
+    int lgLR, lgNs;
+    __device__ __forceinline__ void split(int it, int &b, int &j, int &k, int &jq) const {
+        if (pow2) {
+            b = it >> lgLR;
+            j = it & (LR - 1);
+            k = j & (Ns - 1);
+            jq = j >> lgNs;
+        } else {
+            b = it / LR;
+            j = it - b * LR;
+            jq = j / Ns;
+            k = j - jq * Ns;
+        }
+    }
+};
+
+__device__ __forceinline__ StageIdx make_stage(int L, int R, int Ns) {
+    StageIdx s;
+    s.LR = L / R;
+    s.Ns = Ns;
+    s.step = L / (Ns * R);
+    s.pow2 = ((L & (L - 1)) == 0) && ((R & (R - 1)) == 0);
+    s.lgLR = __ffs(s.LR) - 1;
+    s.lgNs = __ffs(Ns) - 1;
+    return s;
+}
+
+// One stage over `items` butterflies of nb sequences, shared by `nthr` threads with index
+// `tid`; `bar` is the barrier of that group (block or warp).
+template <typename C, int R, int MAXI, bool WARP>
+__device__ __forceinline__ void fft_stage(C *buf, const StageIdx &si, int es, int nb, int bs,
+                                          const C *tw, int sign, int tid, int nthr) {
+    const int items = nb * si.LR;
     C v[MAXI][R];
 #pragma unroll
     for (int m = 0; m < MAXI; ++m) {
-        const int it = threadIdx.x + m * blockDim.x;
+        const int it = tid + m * nthr;
         if (it < items) {
-            const int b = it / LR, j = it - b * LR;
+            int b, j, k, jq;
+            si.split(it, b, j, k, jq);
             const C *src = buf + (long)b * bs;
-            const int k = j % Ns;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                C a = src[(j + r * LR) * es];
+                C a = src[(j + r * si.LR) * es];
                 if (r > 0) {
-                    C w = tw[k * r * step];
+                    C w = tw[k * r * si.step];
                     if (sign > 0) w.y = -w.y;
                     a = cmul(a, w);
                 }
@@ -152,43 +188,59 @@ __device__ __forceinline__ void fft_stage(C *buf, int L, int es, int nb, int bs,
             }
         }
     }
-    __syncthreads();
+    if (WARP) __syncwarp(); else __syncthreads();
 #pragma unroll
     for (int m = 0; m < MAXI; ++m) {
-        const int it = threadIdx.x + m * blockDim.x;
+        const int it = tid + m * nthr;
         if (it < items) {
-            const int b = it / LR, j = it - b * LR;
-            const int k = j % Ns;
+            int b, j, k, jq;
+            si.split(it, b, j, k, jq);
             Dft<R>::run(v[m], sign);
-            const int d0 = (j / Ns) * Ns * R + k;
+            const int d0 = jq * si.Ns * R + k;
             C *dst = buf + (long)b * bs;
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[(d0 + r * Ns) * es] = v[m][r];
+            for (int r = 0; r < R; ++r) dst[(d0 + r * si.Ns) * es] = v[m][r];
         }
     }
-    __syncthreads();
+    if (WARP) __syncwarp(); else __syncthreads();
 }
 
+template <typename C, int MAXC, bool WARP>
+__device__ __forceinline__ void fft_stages_inl(C *base, const FftPlan &p, int es, int nbc, int bs,
+                                           const C *tw, int sign, int tid, int nthr) {
+    int Ns = 1;
+    for (int st = 0; st < p.nst; ++st) {
+        const int R = p.radix[st];
+        const StageIdx si = make_stage(p.L, R, Ns);
+        switch (R) {
+            case 8: fft_stage<C, 8, MAXC / 8, WARP>(base, si, es, nbc, bs, tw, sign, tid, nthr); break;
+            case 4: fft_stage<C, 4, MAXC / 4, WARP>(base, si, es, nbc, bs, tw, sign, tid, nthr); break;
+            case 2: fft_stage<C, 2, MAXC / 2, WARP>(base, si, es, nbc, bs, tw, sign, tid, nthr); break;
+            case 3: fft_stage<C, 3, MAXC / 3, WARP>(base, si, es, nbc, bs, tw, sign, tid, nthr); break;
+            case 5: fft_stage<C, 5, MAXC / 5, WARP>(base, si, es, nbc, bs, tw, sign, tid, nthr); break;
+            default: break;
+        }
+        Ns *= R;
+    }
+}
+
+// Transform the nb sequences. When the plan allows (seq_per_warp > 0), each warp takes its
+// own groups of seq_per_warp sequences and separates stages with warp barriers only;
+// otherwise the whole block takes chunks of `chunk` sequences with block barriers.
 template <typename C, int MAXC>
 __device__ void fft_smem(C *buf, const FftPlan &p, int es, int nb, int bs, int chunk, const C *tw,
                          int sign) {
-    for (int b0 = 0; b0 < nb; b0 += chunk) {
-        const int nbc = min(chunk, nb - b0);
-        C *base = buf + (long)b0 * bs;
-        int Ns = 1;
-        for (int st = 0; st < p.nst; ++st) {
-            const int R = p.radix[st];
-            switch (R) {
-                case 8: fft_stage<C, 8, MAXC / 8>(base, p.L, es, nbc, bs, Ns, tw, sign); break;
-                case 4: fft_stage<C, 4, MAXC / 4>(base, p.L, es, nbc, bs, Ns, tw, sign); break;
-                case 2: fft_stage<C, 2, MAXC / 2>(base, p.L, es, nbc, bs, Ns, tw, sign); break;
-                case 3: fft_stage<C, 3, MAXC / 3>(base, p.L, es, nbc, bs, Ns, tw, sign); break;
-                case 5: fft_stage<C, 5, MAXC / 5>(base, p.L, es, nbc, bs, Ns, tw, sign); break;
-                default: break;
-            }
-            Ns *= R;
-        }
+    if (p.seq_per_warp > 0) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const int S = p.seq_per_warp;
+        for (int g0 = warp * S; g0 < nb; g0 += nw * S)
+            fft_stages_inl<C, MAXC, true>(buf + (long)g0 * bs, p, es, min(S, nb - g0), bs, tw, sign, lane, 32);
+        __syncthreads();
+        return;
     }
+    for (int b0 = 0; b0 < nb; b0 += chunk)
+        fft_stages_inl<C, MAXC, false>(buf + (long)b0 * bs, p, es, min(chunk, nb - b0), bs, tw, sign,
+                                       threadIdx.x, blockDim.x);
 }
 
 template <typename T> struct MaxC;
@@ -260,15 +312,41 @@ template <> struct GramAcc<double> {
     __device__ __forceinline__ double value() const { return s; }
 };
 
+// Sum of many terms in the working precision carried to about FP64 accuracy: FP32 keeps the
+// TwoSum error of every addition in a second word; FP64 adds directly.
+template <typename T> struct SumAcc;
+template <> struct SumAcc<float> {
+    float hi, lo;
+    __device__ __forceinline__ void zero() { hi = lo = 0.f; }
+    __device__ __forceinline__ void add(float x) {
+        float sm, e;
+        two_sum(hi, x, sm, e);
+        hi = sm;
+        lo += e;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <> struct SumAcc<double> {
+    double s;
+    __device__ __forceinline__ void zero() { s = 0.0; }
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { typedef float2 type; };
 template <> struct Vec2<double> { typedef double2 type; };
 
+// Read-only-path load of two consecutive reals. Used for fields that no other thread writes
+// during the pass (each element is read, and possibly rewritten, by one thread only).
+__device__ __forceinline__ float2 ld2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+__device__ __forceinline__ double2 ld2(const double *p) { return __ldg(reinterpret_cast<const double2 *>(p)); }
+
 // ------------------------------------------------------------------ pass 1: plane_fwd
-// One block per (x plane, site). MAXH bounds the stored MDIIS pairs (8 or 16) so the update
-// coefficients and slots live in registers.
+// One block per (x plane or row chunk of one, site). MAXH bounds the stored MDIIS pairs the
+// update combines (5, 8 or 16), so the loop over them unrolls.
 template <typename T, int MAXH>
-__global__ void __launch_bounds__(kThreadsPlane, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kThreadsPlane, sizeof(T) == 4 ? RISM_MINBLOCKS_F32 : 2)
 k_plane_fwd(Fields<T> f) {
     typedef typename Cx<T>::type C;
     typedef typename Vec2<T>::type V2;
@@ -277,14 +355,17 @@ k_plane_fwd(Fields<T> f) {
     extern __shared__ __align__(16) unsigned char smraw[];
     C *buf = reinterpret_cast<C *>(smraw);
     const int Ny = f.Ny, Kz = f.Kz, pitch = f.pitch;
-    C *tw_h = buf + (long)Ny * pitch;
+    C *tw_h = buf + (long)f.slab_rows * pitch;    // after the block's rows
     C *tw_y = tw_h + Kz;
     C *tw_z = tw_y + Ny;
     for (int i = threadIdx.x; i < Kz; i += blockDim.x) tw_h[i] = f.tw_h[i];
     for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw_y[i] = f.tw_y[i];
     for (int i = threadIdx.x; i <= Kz; i += blockDim.x) tw_z[i] = f.tw_z[i];
 
-    const int x = blockIdx.x, gam = blockIdx.y;
+    // block = (x plane, row chunk yc, site): rows y0 .. y0 + nyb of plane x
+    const int nyc = f.nyc;
+    const int x = blockIdx.x / nyc, yc = blockIdx.x - (blockIdx.x / nyc) * nyc, gam = blockIdx.y;
+    const int y0 = yc * f.slab_rows, nyb = min(f.slab_rows, Ny - y0);
     const int stage = ctl->stage;
     const int kind = ctl->stage_kind[stage], order = ctl->stage_order[stage];
     const int cur = ctl->cur;
@@ -293,62 +374,82 @@ k_plane_fwd(Fields<T> f) {
     const T eta = (T)ctl->eta;
     const long long ring = (long long)f.nv * f.G;
     const long long siteoff = (long long)gam * f.G + (long long)x * Ny * f.Nz;
-    T coef[MAXH];
-    int slot[MAXH];
-#pragma unroll
-    for (int i = 0; i < MAXH; ++i) {
+    __shared__ T coef[MAXH];
+    __shared__ long long slot_off[MAXH];
+    if (threadIdx.x < MAXH) {
+        const int i = threadIdx.x;
         coef[i] = i < upd_n ? (T)ctl->upd_coef[i] : (T)0;
-        slot[i] = i < upd_n ? ctl->upd_slot[i] : 0;
+        slot_off[i] = i < upd_n ? (long long)ctl->upd_slot[i] * ring + siteoff : 0;
     }
+    __syncthreads();
     T *tcur = f.X + (long long)cur * ring + siteoff;
     const T *wp = f.w + siteoff;
     const int anchor = ctl->anchor_valid, refresh = ctl->refresh;
     T *ca = f.csr_a + siteoff;
 
-    // update (Eq. 40) + closure + c^sr (Eq. 31), packed two reals per complex along z
-    const int npairs = Ny * Kz;
-    for (int idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
-        const int y = idx / Kz, m = idx - y * Kz;
-        const long long o = (long long)y * f.Nz + 2 * m;
-        V2 t;
+    // update (Eq. 40) + closure + c^sr (Eq. 31), packed two reals per complex along z; two
+    // elements per thread and iteration with every load issued before any store
+    const int npairs = nyb * Kz;
+    const int step = 2 * blockDim.x;
+    for (int i0 = threadIdx.x; i0 < npairs; i0 += step) {
+        const int i1 = i0 + blockDim.x;
+        const bool has1 = i1 < npairs;
+        const int yA = i0 / Kz, mA = i0 - yA * Kz;
+        const int yB = has1 ? i1 / Kz : yA, mB = has1 ? i1 - yB * Kz : mA;
+        const long long oA = (long long)(y0 + yA) * f.Nz + 2 * mA;
+        const long long oB = (long long)(y0 + yB) * f.Nz + 2 * mB;
+        V2 tA, tB;
         if (do_update) {
-            t.x = (T)0;
-            t.y = (T)0;
+            tA.x = tA.y = tB.x = tB.y = (T)0;
 #pragma unroll
             for (int i = 0; i < MAXH; ++i) {
                 if (i < upd_n) {
-                    const long long base = (long long)slot[i] * ring + siteoff + o;
-                    const V2 xv = *reinterpret_cast<const V2 *>(f.X + base);
-                    const V2 rv = *reinterpret_cast<const V2 *>(f.R + base);
-                    t.x += coef[i] * (xv.x + eta * rv.x);
-                    t.y += coef[i] * (xv.y + eta * rv.y);
+                    const T *xb = f.X + slot_off[i], *rb = f.R + slot_off[i];
+                    const V2 xa = ld2(xb + oA), ra = ld2(rb + oA);
+                    const V2 xv = ld2(xb + oB), rv = ld2(rb + oB);
+                    tA.x += coef[i] * (xa.x + eta * ra.x);
+                    tA.y += coef[i] * (xa.y + eta * ra.y);
+                    tB.x += coef[i] * (xv.x + eta * rv.x);
+                    tB.y += coef[i] * (xv.y + eta * rv.y);
                 }
             }
-            *reinterpret_cast<V2 *>(tcur + o) = t;
         } else {
-            t = *reinterpret_cast<const V2 *>(tcur + o);
+            tA = ld2(tcur + oA);
+            tB = ld2(tcur + oB);
         }
-        const V2 wv = *reinterpret_cast<const V2 *>(wp + o);
-        const T g0 = closure_g(wv.x + t.x, kind, order);
-        const T g1 = closure_g(wv.y + t.y, kind, order);
-        V2 c;
-        c.x = g0 - (T)1 - t.x;
-        c.y = g1 - (T)1 - t.y;
-        C dc = cmk(c.x, c.y);
+        const V2 wA = ld2(wp + oA), wB = ld2(wp + oB);
+        V2 aA, aB;
+        if (anchor) {
+            aA = ld2(ca + oA);
+            aB = ld2(ca + oB);
+        }
+        V2 cA, cB;
+        cA.x = closure_g(wA.x + tA.x, kind, order) - (T)1 - tA.x;
+        cA.y = closure_g(wA.y + tA.y, kind, order) - (T)1 - tA.y;
+        cB.x = closure_g(wB.x + tB.x, kind, order) - (T)1 - tB.x;
+        cB.y = closure_g(wB.y + tB.y, kind, order) - (T)1 - tB.y;
+        C dA = cmk(cA.x, cA.y), dB = cmk(cB.x, cB.y);
         if (anchor) {                          // transform only c^sr - c^sr_a
-            const V2 a = *reinterpret_cast<const V2 *>(ca + o);
-            dc.x -= a.x;
-            dc.y -= a.y;
+            dA.x -= aA.x;
+            dA.y -= aA.y;
+            dB.x -= aB.x;
+            dB.y -= aB.y;
         }
-        if (refresh) *reinterpret_cast<V2 *>(ca + o) = c;
-        buf[y * pitch + m] = dc;
+        if (do_update) *reinterpret_cast<V2 *>(tcur + oA) = tA;
+        if (refresh) *reinterpret_cast<V2 *>(ca + oA) = cA;
+        buf[yA * pitch + mA] = dA;
+        if (has1) {
+            if (do_update) *reinterpret_cast<V2 *>(tcur + oB) = tB;
+            if (refresh) *reinterpret_cast<V2 *>(ca + oB) = cB;
+            buf[yB * pitch + mB] = dB;
+        }
     }
     __syncthreads();
     // rows: complex FFT of length Kz
-    fft_smem<C, MaxC<T>::v>(buf, f.ph, 1, Ny, pitch, f.chunk_rows, tw_h, -1);
+    fft_smem<C, MaxC<T>::v>(buf, f.ph, 1, nyb, pitch, f.chunk_rows, tw_h, -1);
     // real-to-complex post-processing: X[k] = E[k] + w^k O[k], k = 0..Kz
     const int half = Kz / 2;
-    for (int idx = threadIdx.x; idx < Ny * (half + 1); idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < nyb * (half + 1); idx += blockDim.x) {
         const int y = idx / (half + 1), k = idx - y * (half + 1);
         C *row = buf + y * pitch;
         if (k == 0) {
@@ -370,15 +471,16 @@ k_plane_fwd(Fields<T> f) {
         }
     }
     __syncthreads();
-    // columns: complex FFT of length Ny for kz = 0..Kz
-    fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz + 1, 1, f.chunk_cols_fwd, tw_y, -1);
-    C *dst = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz;
-    for (int idx = threadIdx.x; idx < Ny * Kz; idx += blockDim.x) {
+    // columns: complex FFT of length Ny for kz = 0..Kz (whole planes only; a split plane
+    // leaves the y transform to the y-pencil pass)
+    if (nyc == 1) fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz + 1, 1, f.chunk_cols_fwd, tw_y, -1);
+    C *dst = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz + (long long)y0 * Kz;
+    for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
         const int y = idx / Kz, k = idx - y * Kz;
         dst[idx] = buf[y * pitch + k];
     }
-    C *dn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny;
-    for (int y = threadIdx.x; y < Ny; y += blockDim.x) dn[y] = buf[y * pitch + Kz];
+    C *dn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny + y0;
+    for (int y = threadIdx.x; y < nyb; y += blockDim.x) dn[y] = buf[y * pitch + Kz];
 }
 
 // ------------------------------------------------------------------ pass 2: pencil
@@ -387,7 +489,7 @@ __device__ __forceinline__ int signed_index(int i, int N) { return (2 * i < N) ?
 // One block per tile of W spectrum columns (all x, all NV sites). NV is a template argument
 // so the contraction unrolls over exactly the solvent sites.
 template <typename T, int NV>
-__global__ void __launch_bounds__(kThreadsPencil, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kThreadsPencil, sizeof(T) == 4 ? RISM_MINBLOCKS_F32 : 2)
 k_pencil(Fields<T> f) {
     typedef typename Cx<T>::type C;
     if (f.ctrl->status != kRunning) return;
@@ -480,12 +582,68 @@ k_pencil(Fields<T> f) {
     }
 }
 
+// ------------------------------------------------------------------ y pencils (split planes)
+// When a y-z plane does not fit in shared memory the plane passes work on row chunks and
+// this pass does the y transform: a tile holds W spectrum columns of one x plane for all y
+// and all sites (main tiles: kz0 .. kz0+W; Nyquist tiles: the kz = Kz values of W planes).
+template <typename T>
+__global__ void __launch_bounds__(kThreadsPencil)
+k_ypencil(Fields<T> f, int sign) {
+    typedef typename Cx<T>::type C;
+    if (f.ctrl->status != kRunning) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *buf = reinterpret_cast<C *>(smraw);
+    const int Nx = f.Nx, Ny = f.Ny, Kz = f.Kz, W = f.Wy, pp = f.ypitch, nv = f.nv;
+    C *tw_y = buf + (long)nv * W * pp;
+    for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw_y[i] = f.tw_y[i];
+    int tile = blockIdx.x;
+    const bool nyq = tile >= f.ytiles_main;
+    long long col_base, col_stride, ystride, site_stride;
+    int ncol;
+    const C *base;
+    if (!nyq) {
+        const int per = (Kz + W - 1) / W;
+        const int x = tile / per, kz0 = (tile - x * per) * W;
+        ncol = min(W, Kz - kz0);
+        col_base = (long long)x * Ny * Kz + kz0;
+        col_stride = 1;
+        ystride = Kz;
+        site_stride = (long long)Nx * Ny * Kz;
+        base = f.spec;
+    } else {
+        tile -= f.ytiles_main;
+        const int x0 = tile * W;
+        ncol = min(W, Nx - x0);
+        col_base = (long long)x0 * Ny;
+        col_stride = Ny;
+        ystride = 1;
+        site_stride = (long long)Nx * Ny;
+        base = f.spec_nyq;
+    }
+    C *gbase = const_cast<C *>(base);
+    const int nload = nv * Ny * ncol;
+    for (int idx = threadIdx.x; idx < nload; idx += blockDim.x) {
+        const int c = idx % ncol;
+        const int rest = idx / ncol;
+        const int y = rest % Ny, a = rest / Ny;
+        buf[(a * W + c) * pp + y] = gbase[a * site_stride + col_base + c * col_stride + y * ystride];
+    }
+    __syncthreads();
+    fft_smem<C, MaxC<T>::v>(buf, f.py, 1, nv * W, pp, f.chunk_y, tw_y, sign);
+    for (int idx = threadIdx.x; idx < nload; idx += blockDim.x) {
+        const int c = idx % ncol;
+        const int rest = idx / ncol;
+        const int y = rest % Ny, a = rest / Ny;
+        gbase[a * site_stride + col_base + c * col_stride + y * ystride] = buf[(a * W + c) * pp + y];
+    }
+}
+
 // ------------------------------------------------------------------ pass 3: plane_inv
 // One block per (x plane, site): inverse y and z transforms, residual, and the block's
 // contribution to <R_cur, R_i> and sum R^2 (Dot2 accumulation, FP64 across threads).
 // Partials are stored value-major: partials[i * n_blocks + block].
 template <typename T, int MAXH>
-__global__ void __launch_bounds__(kThreadsPlane, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kThreadsPlane, sizeof(T) == 4 ? RISM_MINBLOCKS_F32 : 2)
 k_plane_inv(Fields<T> f) {
     typedef typename Cx<T>::type C;
     typedef typename Vec2<T>::type V2;
@@ -494,27 +652,29 @@ k_plane_inv(Fields<T> f) {
     extern __shared__ __align__(16) unsigned char smraw[];
     C *buf = reinterpret_cast<C *>(smraw);
     const int Ny = f.Ny, Kz = f.Kz, pitch = f.pitch;
-    C *tw_h = buf + (long)Ny * pitch;
+    C *tw_h = buf + (long)f.slab_rows * pitch;    // after the block's rows
     C *tw_y = tw_h + Kz;
     C *tw_z = tw_y + Ny;
     double *red = reinterpret_cast<double *>(tw_z + (Kz + 1));
     for (int i = threadIdx.x; i < Kz; i += blockDim.x) tw_h[i] = f.tw_h[i];
     for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw_y[i] = f.tw_y[i];
     for (int i = threadIdx.x; i <= Kz; i += blockDim.x) tw_z[i] = f.tw_z[i];
-    const int x = blockIdx.x, gam = blockIdx.y;
+    const int nyc = f.nyc;
+    const int x = blockIdx.x / nyc, yc = blockIdx.x - (blockIdx.x / nyc) * nyc, gam = blockIdx.y;
+    const int y0 = yc * f.slab_rows, nyb = min(f.slab_rows, Ny - y0);
 
-    const C *src = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz;
-    for (int idx = threadIdx.x; idx < Ny * Kz; idx += blockDim.x) {
+    const C *src = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz + (long long)y0 * Kz;
+    for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
         const int y = idx / Kz, k = idx - y * Kz;
         buf[y * pitch + k] = src[idx];
     }
-    const C *sn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny;
-    for (int y = threadIdx.x; y < Ny; y += blockDim.x) buf[y * pitch + Kz] = sn[y];
+    const C *sn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny + y0;
+    for (int y = threadIdx.x; y < nyb; y += blockDim.x) buf[y * pitch + Kz] = sn[y];
     __syncthreads();
-    fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz + 1, 1, f.chunk_cols_fwd, tw_y, +1);
+    if (nyc == 1) fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz + 1, 1, f.chunk_cols_fwd, tw_y, +1);
     // complex-to-real pre-processing: Z[k] = (X[k] + conj X[Kz-k]) + i w^-k (X[k] - conj X[Kz-k])
     const int half = Kz / 2;
-    for (int idx = threadIdx.x; idx < Ny * (half + 1); idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < nyb * (half + 1); idx += blockDim.x) {
         const int y = idx / (half + 1), k = idx - y * (half + 1);
         C *row = buf + y * pitch;
         const int k2 = Kz - k;
@@ -525,7 +685,7 @@ k_plane_inv(Fields<T> f) {
         row[k] = Z1;
     }
     __syncthreads();
-    fft_smem<C, MaxC<T>::v>(buf, f.ph, 1, Ny, pitch, f.chunk_rows, tw_h, +1);
+    fft_smem<C, MaxC<T>::v>(buf, f.ph, 1, nyb, pitch, f.chunk_rows, tw_h, +1);
 
     const int stage = ctl->stage;
     const int kind = ctl->stage_kind[stage], order = ctl->stage_order[stage];
@@ -538,51 +698,87 @@ k_plane_inv(Fields<T> f) {
     const T *wp = f.w + siteoff;
     const int anchor = ctl->anchor_valid, refresh = ctl->refresh;
     T *ha = f.h_a + siteoff;
-    int hslot[MAXH];
-#pragma unroll
-    for (int i = 0; i < MAXH; ++i) hslot[i] = i < hist_n ? ctl->hist_slot[i] : 0;
+    __shared__ long long hoff[MAXH];
+    if (threadIdx.x < MAXH) hoff[threadIdx.x] = threadIdx.x < hist_n ? (long long)ctl->hist_slot[threadIdx.x] * ring + siteoff : 0;
+    __syncthreads();
     GramAcc<T> acc[MAXH + 1];
 #pragma unroll
     for (int i = 0; i <= MAXH; ++i) acc[i].zero();
-    for (int idx = threadIdx.x; idx < Ny * Kz; idx += blockDim.x) {
-        const int y = idx / Kz, m = idx - y * Kz;
-        const long long o = (long long)y * f.Nz + 2 * m;
-        const C hc = buf[y * pitch + m];
-        const V2 t = *reinterpret_cast<const V2 *>(tcur + o);
-        const V2 wv = *reinterpret_cast<const V2 *>(wp + o);
-        const T g0 = closure_g(wv.x + t.x, kind, order);
-        const T g1 = closure_g(wv.y + t.y, kind, order);
+    const int nel = nyb * Kz;
+    const int step = 2 * blockDim.x;
+    for (int i0 = threadIdx.x; i0 < nel; i0 += step) {
+        const int i1 = i0 + blockDim.x;
+        const bool has1 = i1 < nel;
+        const int yA = i0 / Kz, mA = i0 - yA * Kz;
+        const int yB = has1 ? i1 / Kz : yA, mB = has1 ? i1 - yB * Kz : mA;
+        const long long oA = (long long)(y0 + yA) * f.Nz + 2 * mA;
+        const long long oB = (long long)(y0 + yB) * f.Nz + 2 * mB;
+        // loads of both elements first: t, w, anchor, history residuals
+        const V2 tA = ld2(tcur + oA), tB = ld2(tcur + oB);
+        const V2 wA = ld2(wp + oA), wB = ld2(wp + oB);
+        V2 aA, aB;
+        if (anchor) {
+            aA = ld2(ha + oA);
+            aB = ld2(ha + oB);
+        }
+        V2 qA[MAXH], qB[MAXH];
+#pragma unroll
+        for (int i = 0; i < MAXH; ++i)
+            if (i < hist_n) {
+                qA[i] = ld2(f.R + hoff[i] + oA);
+                qB[i] = ld2(f.R + hoff[i] + oB);
+            }
+        const C hcA = buf[yA * pitch + mA], hcB = buf[yB * pitch + mB];
+        const T gA0 = closure_g(wA.x + tA.x, kind, order), gA1 = closure_g(wA.y + tA.y, kind, order);
+        const T gB0 = closure_g(wB.x + tB.x, kind, order), gB1 = closure_g(wB.y + tB.y, kind, order);
         // R = h + 1 - g (Eq. 33) with h = h_a + dh; (h_a - g) first: near association peaks
         // both are large and close, and the difference is then exact
-        V2 r, h;
+        V2 rA, rB, hA, hB;
         if (anchor) {
-            const V2 a = *reinterpret_cast<const V2 *>(ha + o);
-            r.x = ((a.x - g0) + (T)1) + hc.x;
-            r.y = ((a.y - g1) + (T)1) + hc.y;
-            h.x = a.x + hc.x;
-            h.y = a.y + hc.y;
+            rA.x = ((aA.x - gA0) + (T)1) + hcA.x;
+            rA.y = ((aA.y - gA1) + (T)1) + hcA.y;
+            rB.x = ((aB.x - gB0) + (T)1) + hcB.x;
+            rB.y = ((aB.y - gB1) + (T)1) + hcB.y;
+            hA.x = aA.x + hcA.x;
+            hA.y = aA.y + hcA.y;
+            hB.x = aB.x + hcB.x;
+            hB.y = aB.y + hcB.y;
         } else {
-            r.x = (hc.x - g0) + (T)1;
-            r.y = (hc.y - g1) + (T)1;
-            h.x = hc.x;
-            h.y = hc.y;
+            rA.x = (hcA.x - gA0) + (T)1;
+            rA.y = (hcA.y - gA1) + (T)1;
+            rB.x = (hcB.x - gB0) + (T)1;
+            rB.y = (hcB.y - gB1) + (T)1;
+            hA.x = hcA.x;
+            hA.y = hcA.y;
+            hB.x = hcB.x;
+            hB.y = hcB.y;
         }
-        if (refresh) *reinterpret_cast<V2 *>(ha + o) = h;
-        *reinterpret_cast<V2 *>(rcur + o) = r;
-        acc[0].add(r.x, r.x);
-        acc[0].add(r.y, r.y);
+        acc[0].add(rA.x, rA.x);
+        acc[0].add(rA.y, rA.y);
 #pragma unroll
-        for (int i = 0; i < MAXH; ++i) {
+        for (int i = 0; i < MAXH; ++i)
             if (i < hist_n) {
-                const V2 q = *reinterpret_cast<const V2 *>(f.R + (long long)hslot[i] * ring + siteoff + o);
-                acc[i + 1].add(r.x, q.x);
-                acc[i + 1].add(r.y, q.y);
+                acc[i + 1].add(rA.x, qA[i].x);
+                acc[i + 1].add(rA.y, qA[i].y);
             }
+        if (refresh) *reinterpret_cast<V2 *>(ha + oA) = hA;
+        *reinterpret_cast<V2 *>(rcur + oA) = rA;
+        if (has1) {
+            acc[0].add(rB.x, rB.x);
+            acc[0].add(rB.y, rB.y);
+#pragma unroll
+            for (int i = 0; i < MAXH; ++i)
+                if (i < hist_n) {
+                    acc[i + 1].add(rB.x, qB[i].x);
+                    acc[i + 1].add(rB.y, qB[i].y);
+                }
+            if (refresh) *reinterpret_cast<V2 *>(ha + oB) = hB;
+            *reinterpret_cast<V2 *>(rcur + oB) = rB;
         }
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const long long nblocks = (long long)f.nv * f.Nx;
-    const long long blk = (long long)gam * f.Nx + x;
+    const long long nblocks = (long long)f.nv * f.Nx * nyc;
+    const long long blk = ((long long)gam * f.Nx + x) * nyc + yc;
 #pragma unroll
     for (int i = 0; i <= MAXH; ++i) {
         if (i <= hist_n) {
@@ -599,43 +795,34 @@ k_plane_inv(Fields<T> f) {
 }
 
 // ------------------------------------------------------------------ MDIIS (one block)
-// Reduce the Gram partials in a fixed order (bit-reproducible), update B, then one thread
-// solves the bordered system [B 1; 1^T 0][c; l] = [0; 1] by Gaussian elimination with
-// partial pivoting (B scaled by its largest diagonal entry; pivots below 1e-12 drop the
-// oldest vector and retry), and prepares the next update (Eq. 40).
-__global__ void k_mdiis(Ctrl *ctl, const double *partials, int nblocks) {
-    __shared__ double sums[kMaxHist + 1];
-    if (ctl->status != kRunning) return;
-    const int hist_n = ctl->hist_n;
-    __syncthreads();
-    if (threadIdx.x == 0) {           // what this iteration's kernels moved (byte model)
-        ctl->acc_iters += 1;
-        ctl->acc_fwd_units += ctl->do_update ? 2 * ctl->upd_n + 1 : 1;
-        ctl->acc_hist += hist_n;
-        ctl->acc_anchor += ctl->anchor_valid;
-        ctl->acc_refresh += ctl->refresh;
-        ctl->acc_psi += ctl->anchor_valid == 0;
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp <= hist_n) {
-        const double *pv = partials + (long long)warp * nblocks;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int b = lane;
-        for (; b + 96 < nblocks; b += 128) {
-            s0 += pv[b];
-            s1 += pv[b + 32];
-            s2 += pv[b + 64];
-            s3 += pv[b + 96];
-        }
-        for (; b < nblocks; b += 32) s0 += pv[b];
-        double s = (s0 + s1) + (s2 + s3);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) sums[warp] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
+// Reduce the Gram partials in a fixed order (bit-reproducible), update the Gram matrix,
+// solve for the accelerator's coefficients (Eq. 40 as the bordered DIIS system, or the
+// modified Anderson rule of Eqs. 34-39) and prepare the next update. The control block is
+// staged in shared memory: the bookkeeping is a short serial chain, and on this GPU a chain
+// of FP64 operations on global memory costs tens of microseconds.
 
-    const int M = ctl->M;
+// Scratch of the MDIIS kernel in shared memory.
+struct MdiisScratch {
+    double A[kMaxHist + 1][kMaxHist + 2];    // bordered system, augmented with its rhs
+    double fcol[kMaxHist + 1];
+    double inv_diag[kMaxHist + 1];
+    double c[kMaxHist];
+    int H[kMaxHist];
+    int k, first, mode;
+};
+
+// Bookkeeping before the coefficient solve (thread 0): byte counters, RMS, convergence and
+// closure stages, the Gram row of the new residual, and the candidate history H (oldest
+// first). mode: 0 = nothing more to do, 1 = MDIIS bordered solve, 2 = modified Anderson.
+__device__ void mdiis_pre(Ctrl *ctl, const double *sums, MdiisScratch &sc) {
+    const int hist_n = ctl->hist_n;
+    sc.mode = 0;
+    ctl->acc_iters += 1;
+    ctl->acc_fwd_units += ctl->do_update ? 2 * ctl->upd_n + 1 : 1;
+    ctl->acc_hist += hist_n;
+    ctl->acc_anchor += ctl->anchor_valid;
+    ctl->acc_refresh += ctl->refresh;
+    ctl->acc_psi += ctl->anchor_valid == 0;
     const int cur = ctl->cur;
     const double rr = sums[0];
     const double rms = sqrt(rr * ctl->inv_count);
@@ -671,145 +858,219 @@ __global__ void k_mdiis(Ctrl *ctl, const double *partials, int nblocks) {
         ctl->status = kMaxIter;
         return;
     }
-    // Gram row of the new residual
     for (int i = 0; i < hist_n; ++i) {
         const int s = ctl->hist_slot[i];
         ctl->B[cur * kMaxHist + s] = sums[i + 1];
         ctl->B[s * kMaxHist + cur] = sums[i + 1];
     }
     ctl->B[cur * kMaxHist + cur] = rr;
-    int H[kMaxHist];
     int k = 0;
-    for (int i = 0; i < hist_n; ++i) H[k++] = ctl->hist_slot[i];
-    H[k++] = cur;
-    double c[kMaxHist];
-    int first = 0;
-    if (ctl->accel == 1) {
-        // modified Anderson, two histories (Eqs. 34-39): theta from the 2 x 2 system of
-        // Eq. 36 on D_i = R_new - R_{new-i}; a_i = theta_i + s_i; Picard while fewer than
-        // three pairs are stored or if the system is singular
-        for (int i = 0; i < k; ++i) c[i] = 0.0;
-        c[k - 1] = 1.0;
-        if (k >= 3) {
-            const int n0 = H[k - 1], n1 = H[k - 2], n2 = H[k - 3];
-            const int di[2] = {n1, n2};
-            double Mm[2][2], rhs[2];
-            const double b00 = ctl->B[n0 * kMaxHist + n0];
-            for (int i = 0; i < 2; ++i) {
-                rhs[i] = b00 - ctl->B[n0 * kMaxHist + di[i]];
-                for (int j = 0; j < 2; ++j)
-                    Mm[i][j] = b00 - ctl->B[n0 * kMaxHist + di[j]] - ctl->B[n0 * kMaxHist + di[i]] +
-                               ctl->B[di[i] * kMaxHist + di[j]];
-            }
-            const double sc = fmax(Mm[0][0], Mm[1][1]);
-            if (sc > 0.0) {
-                for (int i = 0; i < 2; ++i) {
-                    rhs[i] /= sc;
-                    for (int j = 0; j < 2; ++j) Mm[i][j] /= sc;
-                }
-                // 2 x 2 Gaussian elimination with partial pivoting
-                int p = fabs(Mm[1][0]) > fabs(Mm[0][0]) ? 1 : 0;
-                if (fabs(Mm[p][0]) >= 1e-12) {
-                    if (p == 1) {
-                        double t0 = Mm[0][0], t1 = Mm[0][1], tr = rhs[0];
-                        Mm[0][0] = Mm[1][0]; Mm[0][1] = Mm[1][1]; rhs[0] = rhs[1];
-                        Mm[1][0] = t0; Mm[1][1] = t1; rhs[1] = tr;
-                    }
-                    const double fct = Mm[1][0] / Mm[0][0];
-                    const double m11 = Mm[1][1] - fct * Mm[0][1];
-                    const double r1 = rhs[1] - fct * rhs[0];
-                    if (fabs(m11) >= 1e-12) {
-                        const double th1 = r1 / m11;
-                        const double th0 = (rhs[0] - Mm[0][1] * th1) / Mm[0][0];
-                        const double a1 = th0 + ctl->s1, a2 = th1 + ctl->s2;
-                        c[k - 1] = 1.0 - a1 - a2;
-                        c[k - 2] = a1;
-                        c[k - 3] = a2;
-                    }
-                }
-            }
-        }
-    } else for (;;) {                 // MDIIS: bordered solve with drop-oldest retry
-        const int n = k - first;
+    for (int i = 0; i < hist_n; ++i) sc.H[k++] = ctl->hist_slot[i];
+    sc.H[k++] = cur;
+    sc.k = k;
+    sc.first = 0;
+    sc.mode = ctl->accel == 1 ? 2 : 1;
+}
+
+// Modified Anderson coefficients (Eqs. 34-39, two histories): theta from the 2 x 2 system
+// of Eq. 36 on D_i = R_new - R_{new-i}, a_i = theta_i + s_i; Picard while fewer than three
+// pairs are stored or if the system is singular.
+__device__ void anderson_coef(const Ctrl *ctl, MdiisScratch &sc) {
+    const int k = sc.k;
+    for (int i = 0; i < k; ++i) sc.c[i] = 0.0;
+    sc.c[k - 1] = 1.0;
+    if (k < 3) return;
+    const int n0 = sc.H[k - 1], n1 = sc.H[k - 2], n2 = sc.H[k - 3];
+    const int di[2] = {n1, n2};
+    double Mm[2][2], rhs[2];
+    const double b00 = ctl->B[n0 * kMaxHist + n0];
+    for (int i = 0; i < 2; ++i) {
+        rhs[i] = b00 - ctl->B[n0 * kMaxHist + di[i]];
+        for (int j = 0; j < 2; ++j)
+            Mm[i][j] = b00 - ctl->B[n0 * kMaxHist + di[j]] - ctl->B[n0 * kMaxHist + di[i]] +
+                       ctl->B[di[i] * kMaxHist + di[j]];
+    }
+    const double sc0 = fmax(Mm[0][0], Mm[1][1]);
+    if (!(sc0 > 0.0)) return;
+    const double is = 1.0 / sc0;
+    for (int i = 0; i < 2; ++i) {
+        rhs[i] *= is;
+        for (int j = 0; j < 2; ++j) Mm[i][j] *= is;
+    }
+    const int p = fabs(Mm[1][0]) > fabs(Mm[0][0]) ? 1 : 0;
+    if (fabs(Mm[p][0]) < 1e-12) return;
+    if (p == 1) {
+        const double t0 = Mm[0][0], t1 = Mm[0][1], tr = rhs[0];
+        Mm[0][0] = Mm[1][0];
+        Mm[0][1] = Mm[1][1];
+        rhs[0] = rhs[1];
+        Mm[1][0] = t0;
+        Mm[1][1] = t1;
+        rhs[1] = tr;
+    }
+    const double fct = Mm[1][0] / Mm[0][0];
+    const double m11 = Mm[1][1] - fct * Mm[0][1];
+    const double r1 = rhs[1] - fct * rhs[0];
+    if (fabs(m11) < 1e-12) return;
+    const double th1 = r1 / m11;
+    const double th0 = (rhs[0] - Mm[0][1] * th1) / Mm[0][0];
+    const double a1 = th0 + ctl->s1, a2 = th1 + ctl->s2;
+    sc.c[k - 1] = 1.0 - a1 - a2;
+    sc.c[k - 2] = a1;
+    sc.c[k - 3] = a2;
+}
+
+// MDIIS coefficients by one warp: lane j owns column j of [B / max diag, 1; 1^T, 0 | rhs];
+// Gaussian elimination with partial pivoting (pivot search by shuffles, one reciprocal per
+// pivot); a pivot below 1e-12 drops the oldest vector and retries.
+__device__ void mdiis_coef_warp(const Ctrl *ctl, MdiisScratch &sc, int lane) {
+    for (;;) {
+        const int n = sc.k - sc.first;
         if (n == 1) {
-            c[0] = 1.0;
-            break;
+            if (lane == 0) sc.c[0] = 1.0;
+            __syncwarp();
+            return;
         }
-        double A[kMaxHist + 1][kMaxHist + 2];
-        double scale = 0.0;
-        for (int i = 0; i < n; ++i) scale = fmax(scale, ctl->B[H[first + i] * kMaxHist + H[first + i]]);
-        const double inv = scale > 0.0 ? 1.0 / scale : 1.0;
-        for (int i = 0; i < n; ++i) {
-            for (int j = 0; j < n; ++j) A[i][j] = ctl->B[H[first + i] * kMaxHist + H[first + j]] * inv;
-            A[i][n] = 1.0;
-            A[i][n + 1] = 0.0;
-        }
-        for (int j = 0; j < n; ++j) A[n][j] = 1.0;
-        A[n][n] = 0.0;
-        A[n][n + 1] = 1.0;
         const int dim = n + 1;
+        const int *H = sc.H + sc.first;
+        double scale = 0.0;
+        for (int i = 0; i < n; ++i) scale = fmax(scale, ctl->B[H[i] * kMaxHist + H[i]]);
+        const double inv = scale > 0.0 ? 1.0 / scale : 1.0;
+        if (lane <= dim)                       // lane j fills column j (j = dim: the rhs)
+            for (int i = 0; i < dim; ++i) {
+                double v;
+                if (lane == dim) v = (i == n) ? 1.0 : 0.0;
+                else if (i == n) v = (lane == n) ? 0.0 : 1.0;
+                else if (lane == n) v = 1.0;
+                else v = ctl->B[H[i] * kMaxHist + H[lane]] * inv;
+                sc.A[i][lane] = v;
+            }
+        __syncwarp();
         bool ok = true;
-        for (int col = 0; col < dim && ok; ++col) {
-            int p = col;
-            double best = fabs(A[col][col]);
-            for (int r = col + 1; r < dim; ++r)
-                if (fabs(A[r][col]) > best) {
-                    best = fabs(A[r][col]);
-                    p = r;
+        for (int col = 0; col < dim; ++col) {
+            double v = (lane >= col && lane < dim) ? fabs(sc.A[lane][col]) : -1.0;
+            int p = lane;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+                const int p2 = __shfl_xor_sync(0xffffffffu, p, o);
+                if (v2 > v || (v2 == v && p2 < p)) {
+                    v = v2;
+                    p = p2;
                 }
-            if (best < 1e-12) {
+            }
+            if (v < 1e-12) {
                 ok = false;
                 break;
             }
-            if (p != col)
-                for (int j = col; j <= dim; ++j) {
-                    const double tmp = A[col][j];
-                    A[col][j] = A[p][j];
-                    A[p][j] = tmp;
-                }
-            for (int r = col + 1; r < dim; ++r) {
-                const double fct = A[r][col] / A[col][col];
-                for (int j = col; j <= dim; ++j) A[r][j] -= fct * A[col][j];
+            if (p != col && lane <= dim) {
+                const double t = sc.A[col][lane];
+                sc.A[col][lane] = sc.A[p][lane];
+                sc.A[p][lane] = t;
             }
+            __syncwarp();
+            const double id = 1.0 / sc.A[col][col];
+            if (lane == 0) sc.inv_diag[col] = id;
+            if (lane > col && lane < dim) sc.fcol[lane] = sc.A[lane][col] * id;
+            __syncwarp();
+            if (lane > col && lane <= dim)
+                for (int r = col + 1; r < dim; ++r) sc.A[r][lane] -= sc.fcol[r] * sc.A[col][lane];
+            __syncwarp();
         }
         if (ok) {
-            double xsol[kMaxHist + 1];
-            for (int r = dim - 1; r >= 0; --r) {
-                double s = A[r][dim];
-                for (int j = r + 1; j < dim; ++j) s -= A[r][j] * xsol[j];
-                xsol[r] = s / A[r][r];
+            if (lane == 0) {
+                double xs[kMaxHist + 1];
+                for (int r = dim - 1; r >= 0; --r) {
+                    double s = sc.A[r][dim];
+                    for (int j = r + 1; j < dim; ++j) s -= sc.A[r][j] * xs[j];
+                    xs[r] = s * sc.inv_diag[r];
+                }
+                for (int i = 0; i < n; ++i) sc.c[i] = xs[i];
             }
-            for (int i = 0; i < n; ++i) c[i] = xsol[i];
-            break;
+            __syncwarp();
+            return;
         }
-        ++first;
+        if (lane == 0) sc.first += 1;
+        __syncwarp();
     }
-    const int n = k - first;
+}
+
+// After the solve (thread 0): damping, the update list and the ring slot of the next
+// iterate (a free slot while the history is short, else the oldest, which leaves it).
+__device__ void mdiis_post(Ctrl *ctl, MdiisScratch &sc) {
+    const int M = ctl->M;
+    const int n = sc.k - sc.first;
+    const int *H = sc.H + sc.first;
     double eta = ctl->damp;
-    if (ctl->dynamic) eta = fmin(fmax(-0.2 * log10(rms), 0.1), 1.0);
+    if (ctl->dynamic) eta = fmin(fmax(-0.2 * log10(ctl->rms), 0.1), 1.0);
     ctl->eta = eta;
     ctl->upd_n = n;
     for (int i = 0; i < n; ++i) {
-        ctl->upd_slot[i] = H[first + i];
-        ctl->upd_coef[i] = c[i];
+        ctl->upd_slot[i] = H[i];
+        ctl->upd_coef[i] = sc.c[i];
     }
-    // slot for the next iterate: a free one while the history is short, else the oldest,
-    // which then leaves the history
     int next;
     if (n < M) {
         int used = 0;
-        for (int i = 0; i < n; ++i) used |= 1 << H[first + i];
+        for (int i = 0; i < n; ++i) used |= 1 << H[i];
         next = 0;
         while (used & (1 << next)) ++next;
         ctl->hist_n = n;
-        for (int i = 0; i < n; ++i) ctl->hist_slot[i] = H[first + i];
+        for (int i = 0; i < n; ++i) ctl->hist_slot[i] = H[i];
     } else {
-        next = H[first];
+        next = H[0];
         ctl->hist_n = n - 1;
-        for (int i = 1; i < n; ++i) ctl->hist_slot[i - 1] = H[first + i];
+        for (int i = 1; i < n; ++i) ctl->hist_slot[i - 1] = H[i];
     }
     ctl->cur = next;
     ctl->do_update = 1;
+}
+
+__global__ void k_mdiis(Ctrl *ctl_g, const double *partials, int nblocks) {
+    __shared__ double sums[kMaxHist + 1];
+    __shared__ Ctrl ctl_s;
+    __shared__ MdiisScratch sc;
+    if (ctl_g->status != kRunning) return;
+    {
+        const int n = (int)(sizeof(Ctrl) / sizeof(int));
+        const int *src = reinterpret_cast<const int *>(ctl_g);
+        int *dst = reinterpret_cast<int *>(&ctl_s);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    Ctrl *ctl = &ctl_s;
+    const int hist_n = ctl->hist_n;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp <= hist_n) {
+        const double *pv = partials + (long long)warp * nblocks;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int b = lane;
+        for (; b + 96 < nblocks; b += 128) {
+            s0 += pv[b];
+            s1 += pv[b + 32];
+            s2 += pv[b + 64];
+            s3 += pv[b + 96];
+        }
+        for (; b < nblocks; b += 32) s0 += pv[b];
+        double s = (s0 + s1) + (s2 + s3);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) sums[warp] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        if (lane == 0) mdiis_pre(ctl, sums, sc);
+        __syncwarp();
+        if (sc.mode == 1) mdiis_coef_warp(ctl, sc, lane);
+        if (sc.mode == 2 && lane == 0) anderson_coef(ctl, sc);
+        __syncwarp();
+        if (sc.mode != 0 && lane == 0) mdiis_post(ctl, sc);
+    }
+    __syncthreads();
+    {
+        const int n = (int)(sizeof(Ctrl) / sizeof(int));
+        const int *src = reinterpret_cast<const int *>(&ctl_s);
+        int *dst = reinterpret_cast<int *>(ctl_g);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+    }
 }
 
 // ------------------------------------------------------------------ potential (Eq. 22, 29)
@@ -851,7 +1112,10 @@ k_potential(Fields<T> f, const double *atoms, int n_atoms, const double *site_si
         lj[g] = (T)0;
         ljd[g] = 0.0;
     }
-    double coul = 0.0, phi = 0.0;
+    double coul = 0.0, phi = 0.0;            // near pairs (FP64)
+    SumAcc<T> coul_f, phi_f;                 // far pairs
+    coul_f.zero();
+    phi_f.zero();
     for (int a0 = 0; a0 < n_atoms; a0 += TILE) {
         const int na = min(TILE, n_atoms - a0);
         __syncthreads();
@@ -902,8 +1166,8 @@ k_potential(Fields<T> f, const double *atoms, int n_atoms, const double *site_si
                     const T ir2 = (T)1 / r2;
                     const T r = sqrt(r2);
                     const T ir = (T)1 / r;
-                    coul += (double)(sq[i] * ir);
-                    phi += (double)(sq[i] * (T)(-expm1(-r)) * ir);
+                    coul_f.add(sq[i] * ir);
+                    phi_f.add(sq[i] * (T)(-expm1(-r)) * ir);
 #pragma unroll
                     for (int g = 0; g < kMaxSites; ++g) {
                         if (g < nv) {
@@ -917,6 +1181,8 @@ k_potential(Fields<T> f, const double *atoms, int n_atoms, const double *site_si
         }
     }
     if (!active) return;
+    coul += coul_f.value();
+    phi += phi_f.value();
     const double C = 332.0637;
     const double phiv = C * phi;
     for (int g = 0; g < nv; ++g) {
@@ -929,13 +1195,51 @@ k_potential(Fields<T> f, const double *atoms, int n_atoms, const double *site_si
 }
 
 // ------------------------------------------------------------------ long range (Eq. 30)
-// Psi(k) = beta Phi~(k) / dV = amp0 / (k^2 (k^2 + 1)) sum_a q_a exp(-i k.(R_a - r0)),
-// zero at k = 0 and on Nyquist planes. The phase is evaluated in FP64 as
-// sincospi(2 (mx ux + my uy + mz uz)) with u = (R - r0) / L.
+// Psi(k) = beta Phi~(k) / dV = amp0 / (k^2 (k^2 + 1)) sum_a q_a exp(-i k.(R_a - r0)), zero at
+// k = 0 and on Nyquist planes. The phase factorises over the axes,
+// exp(-i k.u) = E_x(a, mx) E_y(a, my) E_z(a, mz) with E(a, m) = exp(-2 pi i m u_a) and
+// u = (R - r0) / L; the tables are evaluated once per atom chunk in FP64 (sincospi) and
+// rounded to the working precision, so each (atom, k) pair costs two complex products and
+// a compensated sum.
+template <typename T>
+__global__ void k_phase_tables(Fields<T> f, const double *atoms, int a0, int na,
+                               typename Cx<T>::type *tab) {
+    typedef typename Cx<T>::type C;
+    const int per = f.Nx + f.Ny + f.Kz + 1;
+    const long long n = (long long)na * per;
+    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < n;
+         id += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(id / per), e = (int)(id - (long long)a * per);
+        const double *at = atoms + (long long)(a0 + a) * kAtomStride;
+        double u;
+        int m;
+        if (e < f.Nx) {
+            m = signed_index(e, f.Nx);
+            u = at[6];
+        } else if (e < f.Nx + f.Ny) {
+            m = signed_index(e - f.Nx, f.Ny);
+            u = at[7];
+        } else {
+            m = e - f.Nx - f.Ny;
+            u = at[8];
+        }
+        double sn, cs;
+        sincospi(2.0 * m * u, &sn, &cs);
+        C v;
+        v.x = (T)cs;
+        v.y = (T)(-sn);
+        tab[id] = v;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_longrange(Fields<T> f, const double *atoms, int n_atoms, double amp0) {
+k_longrange(Fields<T> f, const double *atoms, int a0, int na, const typename Cx<T>::type *tab,
+            double amp0, int accumulate) {
     typedef typename Cx<T>::type C;
+    __shared__ T qs[kPhaseChunk];
+    for (int i = threadIdx.x; i < na; i += blockDim.x) qs[i] = (T)atoms[(long long)(a0 + i) * kAtomStride + 3];
+    __syncthreads();
     const long long nmain = (long long)f.Nx * f.Ny * f.Kz;
     const long long total = nmain + (long long)f.Nx * f.Ny;
     const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -959,23 +1263,30 @@ k_longrange(Fields<T> f, const double *atoms, int n_atoms, double amp0) {
     const double k2 = kx * kx + ky * ky + kz * kz;
     double re = 0.0, im = 0.0;
     if (!nyq && k2 > 0.0) {
-        for (int a = 0; a < n_atoms; ++a) {
-            const double *at = atoms + (long long)a * kAtomStride;
-            const double ph = 2.0 * (mx * at[6] + my * at[7] + mz * at[8]);
-            double s, c;
-            sincospi(ph, &s, &c);
-            re += at[3] * c;
-            im -= at[3] * s;
+        const int per = f.Nx + f.Ny + f.Kz + 1;
+        const C *ex = tab + ix, *ey = tab + f.Nx + iy, *ez = tab + f.Nx + f.Ny + iz;
+        SumAcc<T> sr, si;
+        sr.zero();
+        si.zero();
+        for (int a = 0; a < na; ++a) {
+            const long long o = (long long)a * per;
+            const C xy = cmul(__ldg(ex + o), __ldg(ey + o));
+            const C e = cmul(xy, __ldg(ez + o));
+            sr.add(qs[a] * e.x);
+            si.add(qs[a] * e.y);
         }
         const double amp = amp0 / (k2 * (k2 + 1.0));
-        re *= amp;
-        im *= amp;
+        re = amp * sr.value();
+        im = amp * si.value();
     }
+    C *dst = id < nmain ? f.psi + id : f.psi_nyq + (id - nmain);
     C v = cmk((T)re, (T)im);
-    if (id < nmain)
-        f.psi[id] = v;
-    else
-        f.psi_nyq[id - nmain] = v;
+    if (accumulate) {
+        const C o = *dst;
+        v.x += o.x;
+        v.y += o.y;
+    }
+    *dst = v;
 }
 
 // ------------------------------------------------------------------ small helpers
@@ -1067,7 +1378,8 @@ k_sfe(Fields<T> f, int slot, int kind, int order, int sfe_kind, int sfe_order, d
         const double h = (double)(gv - (T)1);
         const double c = (double)(gv - (T)1 - tau) - bq * (double)f.phi[p];   // c = h - t
         double v = -c - 0.5 * h * c;
-        if (sfe_kind == 2) v += 0.5 * h * h;                     // HNC, Eq. 17
+        if (sfe_kind == 5) v = c;                                // int c dr (PMV, Eq. 19)
+        else if (sfe_kind == 2) v += 0.5 * h * h;                // HNC, Eq. 17
         else if (sfe_kind == 1) v += h < 0.0 ? 0.5 * h * h : 0.0;  // KH, Eq. 18
         else if (sfe_kind == 4) {                                // PSE-n
             v += 0.5 * h * h;
@@ -1079,15 +1391,149 @@ k_sfe(Fields<T> f, int slot, int kind, int order, int sfe_kind, int sfe_order, d
     if (threadIdx.x == 0) partials[(long long)g * gridDim.x + blockIdx.x] = s;
 }
 
+
+// ------------------------------------------------------------------ SFE gradient (second Eq. 21)
+// d(dmu)/dR_a = sum_g rho_g int g_g(r) du_g(r)/dR_a dr with
+// du/dR = (48 eps s^12 / d^14 - 24 eps s^6 / d^8 + C q_a q_g / d^3) (r - R), d = |r - R_a|.
+// Pass 1 stores rho_g dV g_g(r) (the spectrum buffer is free after a solve); pass 2 takes a
+// tile of atoms per block row and a range of grid points per block, with per-thread partial
+// sums and a block reduction into partials[(atom * 3 + component) * nblk + block]; pass 3
+// sums the blocks in a fixed order.
+template <typename T>
+__global__ void k_grad_weights(Fields<T> f, int slot, int kind, int order, const double *rho_dV) {
+    T *wg = reinterpret_cast<T *>(f.spec);
+    const long long ring = (long long)f.nv * f.G;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ring;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(i / f.G);
+        const T tau = f.X[(long long)slot * ring + i];
+        wg[i] = (T)rho_dV[g] * closure_g(f.w[i] + tau, kind, order);
+    }
+}
+
+template <typename T> struct GradTile;
+template <> struct GradTile<float> { static constexpr int v = 8; };
+template <> struct GradTile<double> { static constexpr int v = 4; };
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_sfe_gradient(Fields<T> f, const double *atoms, int n_atoms, const double *site_sig,
+               const double *site_eps, const double *site_q, double ox, double oy, double oz,
+               double dx, double dy, double dz, double *partials) {
+    constexpr int AT = GradTile<T>::v;
+    __shared__ T ax[AT], ay[AT], az[AT], aq[AT];
+    __shared__ T s2[AT][kMaxSites], e48[AT][kMaxSites], e24[AT][kMaxSites];
+    __shared__ double red[8][3 * AT];
+    const int nv = f.nv;
+    const int a0 = blockIdx.y * AT;
+    const int na = min(AT, n_atoms - a0);
+    for (int i = threadIdx.x; i < AT; i += blockDim.x) {
+        if (i < na) {
+            const double *at = atoms + (long long)(a0 + i) * kAtomStride;
+            ax[i] = (T)(at[0] - ox);
+            ay[i] = (T)(at[1] - oy);
+            az[i] = (T)(at[2] - oz);
+            aq[i] = (T)(332.0637 * at[3]);
+            for (int g = 0; g < nv; ++g) {
+                const double sg = 0.5 * (at[4] + site_sig[g]), eg = sqrt(at[5] * site_eps[g]);
+                s2[i][g] = (T)(sg * sg);
+                e48[i][g] = (T)(48.0 * eg);
+                e24[i][g] = (T)(24.0 * eg);
+            }
+        }
+    }
+    __syncthreads();
+    const T *wg = reinterpret_cast<const T *>(f.spec);
+    T acc[3 * AT];
+#pragma unroll
+    for (int k = 0; k < 3 * AT; ++k) acc[k] = (T)0;
+    const int NyNz = f.Ny * f.Nz;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < f.G;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(p / NyNz);
+        const int rem = (int)(p - (long long)ix * NyNz);
+        const int iy = rem / f.Nz, iz = rem - (rem / f.Nz) * f.Nz;
+        const T px = (T)(ix * dx), py = (T)(iy * dy), pz = (T)(iz * dz);
+        T wv[kMaxSites];
+#pragma unroll
+        for (int g = 0; g < kMaxSites; ++g) wv[g] = g < nv ? wg[(long long)g * f.G + p] : (T)0;
+#pragma unroll
+        for (int i = 0; i < AT; ++i) {
+            if (i < na) {
+                const T ex = px - ax[i], ey = py - ay[i], ez = pz - az[i];
+                T d2 = ex * ex + ey * ey + ez * ez;
+                d2 = d2 < (T)1e-8 ? (T)1e-8 : d2;
+                const T id2 = (T)1 / d2;
+                const T id3 = id2 * ((T)1 / sqrt(d2));
+                T fac = (T)0;
+#pragma unroll
+                for (int g = 0; g < kMaxSites; ++g) {
+                    if (g < nv) {
+                        const T q = s2[i][g] * id2;
+                        const T s6 = q * q * q;
+                        fac += wv[g] * ((e48[i][g] * s6 * s6 - e24[i][g] * s6) * id2 +
+                                        aq[i] * (T)site_q[g] * id3);
+                    }
+                }
+                acc[3 * i] += fac * ex;
+                acc[3 * i + 1] += fac * ey;
+                acc[3 * i + 2] += fac * ez;
+            }
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 3 * AT; ++k) {
+        double v = (double)acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3 * na) {
+        double sum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w][threadIdx.x];
+        const int i = threadIdx.x / 3, comp = threadIdx.x - 3 * (threadIdx.x / 3);
+        partials[((long long)(a0 + i) * 3 + comp) * gridDim.x + blockIdx.x] = sum;
+    }
+}
+
+__global__ void k_sum_rows(const double *partials, int rows, int cols, double *out) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < cols; ++c) s += partials[(long long)r * cols + c];
+        out[r] = s;
+    }
+}
+
+template <typename T>
+cudaError_t launch_sfe_gradient(const Fields<T> &f, int slot, int kind, int order, const double *rho_dV,
+                                const double *atoms, int n_atoms, const double *site_sig,
+                                const double *site_eps, const double *site_q, const double *origin,
+                                const double *spacing, double *partials, double *out, cudaStream_t s) {
+    k_grad_weights<T><<<152 * 8, 256, 0, s>>>(f, slot, kind, order, rho_dV);
+    constexpr int AT = GradTile<T>::v;
+    const int nblk = kGradBlocks;
+    const dim3 grid(nblk, (n_atoms + AT - 1) / AT);
+    k_sfe_gradient<T><<<grid, 256, 0, s>>>(f, atoms, n_atoms, site_sig, site_eps, site_q, origin[0],
+                                           origin[1], origin[2], spacing[0], spacing[1], spacing[2],
+                                           partials);
+    k_sum_rows<<<(3 * n_atoms + 255) / 256, 256, 0, s>>>(partials, 3 * n_atoms, nblk, out);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launchers
 template <typename T> size_t plane_smem_bytes(const Fields<T> &f) {
     typedef typename Cx<T>::type C;
-    return sizeof(C) * ((size_t)f.Ny * f.pitch + f.Kz + f.Ny + f.Kz + 1) +
+    return sizeof(C) * ((size_t)f.slab_rows * f.pitch + f.Kz + f.Ny + f.Kz + 1) +
            (kMaxHist + 1) * (kThreadsPlane / 32) * sizeof(double) + 16;
 }
 template <typename T> size_t pencil_smem_bytes(const Fields<T> &f) {
     typedef typename Cx<T>::type C;
     return sizeof(C) * ((size_t)f.nv * f.W * f.pencil_pitch + f.Nx);
+}
+template <typename T> size_t ypencil_smem_bytes(const Fields<T> &f) {
+    typedef typename Cx<T>::type C;
+    return sizeof(C) * ((size_t)f.nv * f.Wy * f.ypitch + f.Ny);
 }
 
 template <typename K>
@@ -1097,10 +1543,13 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 
 template <typename T> cudaError_t prepare_kernels(const Fields<T> &f) {
     const size_t pl = plane_smem_bytes(f), pe = pencil_smem_bytes(f);
-    cudaError_t e = set_smem(k_plane_fwd<T, 8>, pl);
+    cudaError_t e = set_smem(k_plane_fwd<T, 5>, pl);
+    if (e == cudaSuccess) e = set_smem(k_plane_inv<T, 4>, pl);
+    if (e == cudaSuccess) e = set_smem(k_plane_fwd<T, 8>, pl);
     if (e == cudaSuccess) e = set_smem(k_plane_fwd<T, kMaxHist>, pl);
     if (e == cudaSuccess) e = set_smem(k_plane_inv<T, 8>, pl);
     if (e == cudaSuccess) e = set_smem(k_plane_inv<T, kMaxHist>, pl);
+    if (e == cudaSuccess && f.nyc > 1) e = set_smem(k_ypencil<T>, ypencil_smem_bytes(f));
     if (e != cudaSuccess) return e;
     switch (f.nv) {
         case 1: return set_smem(k_pencil<T, 1>, pe);
@@ -1115,10 +1564,17 @@ template <typename T> cudaError_t prepare_kernels(const Fields<T> &f) {
     }
 }
 
+template <typename T> cudaError_t launch_ypencil(const Fields<T> &f, int sign, cudaStream_t s) {
+    k_ypencil<T><<<f.ytiles_main + f.ytiles_nyq, kThreadsPencil, ypencil_smem_bytes(f), s>>>(f, sign);
+    return cudaGetLastError();
+}
 template <typename T> cudaError_t launch_plane_fwd(const Fields<T> &f, cudaStream_t s) {
     const size_t sm = plane_smem_bytes(f);
-    const dim3 grid(f.Nx, f.nv);
-    if (f.M <= 8)
+    const dim3 grid(f.Nx * f.nyc, f.nv);
+    // the update combines up to M stored pairs
+    if (f.M <= 5)
+        k_plane_fwd<T, 5><<<grid, kThreadsPlane, sm, s>>>(f);
+    else if (f.M <= 8)
         k_plane_fwd<T, 8><<<grid, kThreadsPlane, sm, s>>>(f);
     else
         k_plane_fwd<T, kMaxHist><<<grid, kThreadsPlane, sm, s>>>(f);
@@ -1126,8 +1582,11 @@ template <typename T> cudaError_t launch_plane_fwd(const Fields<T> &f, cudaStrea
 }
 template <typename T> cudaError_t launch_plane_inv(const Fields<T> &f, cudaStream_t s) {
     const size_t sm = plane_smem_bytes(f);
-    const dim3 grid(f.Nx, f.nv);
-    if (f.M <= 8)
+    const dim3 grid(f.Nx * f.nyc, f.nv);
+    // the Gram row pairs the new residual with at most M - 1 stored ones
+    if (f.M <= 5)
+        k_plane_inv<T, 4><<<grid, kThreadsPlane, sm, s>>>(f);
+    else if (f.M <= 8)
         k_plane_inv<T, 8><<<grid, kThreadsPlane, sm, s>>>(f);
     else
         k_plane_inv<T, kMaxHist><<<grid, kThreadsPlane, sm, s>>>(f);
@@ -1150,7 +1609,7 @@ template <typename T> cudaError_t launch_pencil(const Fields<T> &f, cudaStream_t
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_mdiis(const Fields<T> &f, cudaStream_t s) {
-    k_mdiis<<<1, 32 * (kMaxHist + 1), 0, s>>>(f.ctrl, f.partials, f.nv * f.Nx);
+    k_mdiis<<<1, 32 * (kMaxHist + 1), 0, s>>>(f.ctrl, f.partials, f.nv * f.Nx * f.nyc);
     return cudaGetLastError();
 }
 template <typename T>
@@ -1168,7 +1627,12 @@ template <typename T>
 cudaError_t launch_longrange(const Fields<T> &f, const double *atoms, int n_atoms, double amp0,
                              cudaStream_t s) {
     const long long total = (long long)f.Nx * f.Ny * (f.Kz + 1);
-    k_longrange<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(f, atoms, n_atoms, amp0);
+    for (int a0 = 0; a0 < n_atoms; a0 += kPhaseChunk) {
+        const int na = min(kPhaseChunk, n_atoms - a0);
+        k_phase_tables<T><<<152 * 4, 256, 0, s>>>(f, atoms, a0, na, f.phase);
+        k_longrange<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(f, atoms, a0, na, f.phase, amp0,
+                                                                       a0 > 0);
+    }
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_init_guess(const Fields<T> &f, int slot, cudaStream_t s) {
@@ -1200,6 +1664,7 @@ cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sf
     template size_t pencil_smem_bytes<T>(const Fields<T> &);                                     \
     template cudaError_t launch_plane_fwd<T>(const Fields<T> &, cudaStream_t);                   \
     template cudaError_t launch_plane_inv<T>(const Fields<T> &, cudaStream_t);                   \
+    template cudaError_t launch_ypencil<T>(const Fields<T> &, int, cudaStream_t);                \
     template cudaError_t launch_pencil<T>(const Fields<T> &, cudaStream_t);                      \
     template cudaError_t launch_mdiis<T>(const Fields<T> &, cudaStream_t);                       \
     template cudaError_t launch_potential<T>(const Fields<T> &, const double *, int,            \
@@ -1213,7 +1678,11 @@ cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sf
     template cudaError_t launch_get_field<T>(const Fields<T> &, int, int, int, int, double *,   \
                                              cudaStream_t);                                     \
     template cudaError_t launch_sfe<T>(const Fields<T> &, int, int, int, int, int, double *,    \
-                                       int, cudaStream_t);
+                                       int, cudaStream_t);                                     \
+    template cudaError_t launch_sfe_gradient<T>(const Fields<T> &, int, int, int, const double *, \
+                                                const double *, int, const double *,           \
+                                                const double *, const double *, const double *, \
+                                                const double *, double *, double *, cudaStream_t);
 
 RISM_INSTANTIATE(float)
 RISM_INSTANTIATE(double)

@@ -4,6 +4,7 @@ Calls only the FP64 oracle (``oracle/``) and the seeded input generators; nothin
 touches the CUDA path. Run from the repository root:
 
     python tests/golden/make_golden.py chi          # solvent susceptibility tables
+    python tests/golden/make_golden.py thermo       # bulk pressure, kT chi_T, c(r) of water
     python tests/golden/make_golden.py solute50_128 # full-size reference (slow, ~minutes)
 """
 import os
@@ -16,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
-from oracle import rism1d, rism3d, closure as cl   # noqa: E402
+from oracle import rism1d, rism3d, thermo, closure as cl   # noqa: E402
 from paper_2403_01039_gb300 import synth           # noqa: E402
 
 
@@ -29,6 +30,19 @@ def make_chi():
         np.savez_compressed(os.path.join(HERE, "chi_%s.npz" % name), chi=r["chi"], dk=r["dk"], h=r["h"],
                             n=2048, dr=0.05, iterations=r["iterations"], rms=r["rms"])
         print(name, "iterations", r["iterations"], "rms %.2e" % r["rms"], "%.1f s" % (time.time() - t0))
+
+
+def make_thermo():
+    """Bulk pressure (Eq. 20), k_B T chi_T and the full direct correlation c(r) (every 8th
+    radial point from r = dr) of 3-site water from the oracle's 1D solve."""
+    s = synth.solvent_sites("water3")
+    r = rism1d.xrism_solvent(s["q"], s["sigma"], s["eps"], s["rho"], s["species"], s["coords"],
+                             s["temperature"])
+    P = thermo.pressure(r["c"], r["grid"].r, s["rho"], s["species"], s["temperature"])
+    kt = thermo.kT_chi_T(r["chi"], s["rho"])
+    np.savez_compressed(os.path.join(HERE, "thermo_water3.npz"), pressure=P, kT_chi_T=kt,
+                        c_every8=r["c"][:, :, ::8])
+    print("water3 pressure %.10g kcal/mol/A^3, kT chi_T %.10g A^3" % (P, kt))
 
 
 def sample_points(n, count, seed):
@@ -75,5 +89,7 @@ if __name__ == "__main__":
     what = sys.argv[1] if len(sys.argv) > 1 else "chi"
     if what == "chi":
         make_chi()
+    elif what == "thermo":
+        make_thermo()
     else:
         make_full(what)

@@ -76,7 +76,7 @@ def test_defaults_and_workspace_size(lib):
     (lambda sv, g, o: g.update(n=(32, 32, 31)), 8),
     (lambda sv, g, o: g.update(n=(14, 32, 32)), 8),
     (lambda sv, g, o: g.update(n=(32, 32, 28)), 8),          # Nz/2 = 14 has the factor 7
-    (lambda sv, g, o: g.update(n=(32, 512, 512)), 8),        # FP64 y-z plane exceeds shared memory
+    (lambda sv, g, o: g.update(n=(8, 8, 30000)), 8),         # one FP64 row exceeds shared memory
     (lambda sv, g, o: setattr(o, "precision", 16), 1),
     (lambda sv, g, o: setattr(o, "mdiis_nvec", 17), 1),
     (lambda sv, g, o: setattr(o, "max_iter", 0), 1),
@@ -106,3 +106,15 @@ def test_product_xrism_matches_oracle_table(lib):
     ref, rdk = load_chi("water3")
     assert dk == rdk and rms < 1e-10
     assert np.max(np.abs(chi - ref)) < 1e-7
+
+
+def test_product_xrism_thermo_matches_oracle(lib):
+    """Bulk pressure (Eq. 20), k_B T chi_T and the full direct correlation of 3-site water
+    from the library's host 1D solver against the oracle's stored values."""
+    import os
+    from paper_2403_01039_gb300 import capi, synth
+    chi, dk, its, rms, th = capi.xrism(synth.water_3site(), thermo=True)
+    ref = np.load(os.path.join(os.path.dirname(__file__), "golden", "thermo_water3.npz"))
+    assert abs(th["pressure"] - float(ref["pressure"])) <= 1e-7 * abs(float(ref["pressure"]))
+    assert abs(th["kT_chi_T"] - float(ref["kT_chi_T"])) <= 1e-6 * float(ref["kT_chi_T"])
+    assert np.max(np.abs(th["c"][:, :, ::8] - ref["c_every8"])) <= 1e-6
