@@ -114,3 +114,23 @@ def phik_long_range(n, spacing, origin, xyz, q):
         out += q[a] * amp * np.exp(-1j * phase)
     out[zero] = 0.0
     return out
+
+
+def kvectors_shifted(n, spacing):
+    """Wave vectors of the half-integer grid k_m = 2 pi (m + 1/2) / (N d), m in [-N/2, N/2)
+    per axis (numpy FFT order), on the full spectrum [Nx, Ny, Nz, 3]; no k is zero."""
+    ks = [2.0 * np.pi * (signed_index(n[d]) + 0.5) / (n[d] * spacing[d]) for d in range(3)]
+    KX, KY, KZ = np.meshgrid(*ks, indexing="ij")
+    return np.stack([KX, KY, KZ], axis=-1)
+
+
+def phik_long_range_shifted(n, spacing, origin, xyz, q):
+    """Phi~(k) of Eq. 30 (without beta q_gamma) on the half-integer grid (full spectrum)."""
+    kv = kvectors_shifted(n, spacing)
+    k2 = np.sum(kv * kv, axis=-1)
+    amp = 4.0 * np.pi * COULOMB / (k2 * (k2 + 1.0))
+    out = np.zeros(k2.shape, dtype=np.complex128)
+    r0 = np.asarray(origin, dtype=np.float64)
+    for a in range(len(q)):
+        out += q[a] * amp * np.exp(-1j * (kv @ (np.asarray(xyz[a], dtype=np.float64) - r0)))
+    return out

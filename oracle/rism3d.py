@@ -20,14 +20,19 @@ Readings (the paper is silent or garbled):
 * residual: Eq. 41 prints the mean of sqrt((t^j - t^{j-1})^2); the oracle stops on
   RMS = sqrt(sum R^2 / (N n_v)) with R = t' - t (Eq. 33) and also records the printed
   mean-absolute form;
-* the returned solution is the last input t with g, c from its closure and h = g - 1.
+* the returned solution is the last input t with g, c from its closure and h = g - 1;
+* half-integer grid (option kgrid="half"; the numerical-procedure section places k at
+  half-integers): k_m = 2 pi (m + 1/2) / (N d) on every axis, c~(k) = dV sum_n c(r_n)
+  exp(-i k.(r_n - r0)) evaluated as the DFT of c(r_n) exp(-i pi sum_d n_d / N_d), and the
+  inverse with the conjugate factor; no k is zero, so Phi~ needs no special points.
 """
 import numpy as np
 
 from . import anderson
 from . import closure as cl
 from . import mdiis
-from .potential import beta_u, phi_long_range, phik_long_range, kvectors_half
+from .potential import (beta_u, phi_long_range, phik_long_range, kvectors_half, kvectors_shifted,
+                        phik_long_range_shifted)
 from .units import beta as beta_of, KB_KCAL
 
 
@@ -47,9 +52,10 @@ class Problem:
     once per solute (beta*u, f, f~, X on the half spectrum).
 
     ``minimum_image`` evaluates the real-space potentials with the minimum-image
-    convention; it exists only for the whole-cell shift test."""
+    convention; it exists only for the whole-cell shift test. ``kgrid`` = "integer" (the
+    periodic grid) or "half" (half-integer k on every axis)."""
 
-    def __init__(self, solvent, grid, solute, minimum_image=False):
+    def __init__(self, solvent, grid, solute, minimum_image=False, kgrid="integer"):
         self.n = tuple(int(v) for v in grid["n"])
         self.spacing = tuple(float(v) for v in grid["spacing"])
         self.origin = tuple(float(v) for v in grid["origin"])
@@ -74,11 +80,20 @@ class Problem:
         # Eq. 29 / Eq. 30: f_gamma = beta q_gamma phi, f~_gamma = beta q_gamma Phi~
         self.phi = phi_long_range(self.n, self.spacing, self.origin, xyz, q,
                                   minimum_image=minimum_image)
-        self.phik = phik_long_range(self.n, self.spacing, self.origin, xyz, q)
+        if kgrid not in ("integer", "half"):
+            raise ValueError("kgrid must be 'integer' or 'half'")
+        self.kgrid = kgrid
+        if kgrid == "half":
+            self.phik = phik_long_range_shifted(self.n, self.spacing, self.origin, xyz, q)
+            kv = kvectors_shifted(self.n, self.spacing)
+            ph = [np.exp(-1j * np.pi * np.arange(N) / N) for N in self.n]
+            self.shift = ph[0][:, None, None] * ph[1][None, :, None] * ph[2][None, None, :]
+        else:
+            self.phik = phik_long_range(self.n, self.spacing, self.origin, xyz, q)
+            kv, _ = kvectors_half(self.n, self.spacing)
         bq = self.beta * self.site_q
         self.f = bq[:, None, None, None] * self.phi[None]
         self.ftil = bq[:, None, None, None] * self.phik[None]
-        kv, _ = kvectors_half(self.n, self.spacing)
         self.kmag = np.sqrt(np.sum(kv * kv, axis=-1))
         self.chik = chi_interp(self.chi, self.dk, self.kmag)   # [a][g][kx][ky][kz]
 
@@ -92,6 +107,10 @@ class Problem:
     def rism_h(self, csr):
         """h_gamma(r) from c^sr via Eqs. 32 and 13 (steps 3-5)."""
         axes = (1, 2, 3)
+        if self.kgrid == "half":
+            ctil = self.dV * np.fft.fftn(csr * self.shift, axes=axes) - self.ftil
+            htil = np.einsum("a...,ag...->g...", ctil, self.chik)
+            return (np.fft.ifftn(htil, axes=axes) * np.conj(self.shift)).real / self.dV
         ctil = self.dV * np.fft.rfftn(csr, axes=axes) - self.ftil            # Eq. 32
         htil = np.einsum("a...,ag...->g...", ctil, self.chik)                 # Eq. 13
         return np.fft.irfftn(htil, s=self.n, axes=axes) / self.dV           # step 5
