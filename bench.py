@@ -44,6 +44,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-sample-iters", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--inflight", type=int, default=8, help="batch64: jobs in flight")
     return p.parse_args()
 
 
@@ -139,7 +140,7 @@ def ncu_traffic(kernel, workload):
     """dram bytes per launch from a committed ncu summary, if it was taken on the current
     kernel source (its hash is stored beside the figure); else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    src = os.path.join(ROOT, "paper_2403_01039_gb300", "csrc", "rism3d_kernels.cu")
+    src = os.path.join(ROOT, "paper_2403_01039_gb300", "csrc", "rism3d_kernels.cuh")
     if not os.path.exists(path):
         return None
     with open(path) as f:
@@ -353,10 +354,84 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args):
+    """--workload batch64: 64 seeded solutes (20-120 atoms) on uneven cubic grids (64-128,
+    sizes with factors 2, 3, 5 only) in 3-site water, KH, tol 1e-6, FP32. A step is the whole
+    batch: every job's set_solute + solve + SFE, once one at a time and once through
+    rism3d_solve_batch; value is the batched solves/s, the one-at-a-time rate is reported
+    beside it. Contexts are created (one per grid) before timing."""
+    import numpy as np
+    import torch
+
+    from paper_2403_01039_gb300 import build, capi, synth
+
+    build.build()
+    torch.cuda.set_device(0)
+    sites = synth.water_3site()
+    chi, dk, _, _ = capi.xrism(sites)
+    solv = dict(sites, chi=chi, dk=dk)
+    work = synth.batch_workload()
+    solvers = [capi.Solver(solv, w["grid"], precision=args.precision, mdiis_nvec=5) for w in work]
+
+    def one_at_a_time():
+        its = 0
+        for S, w in zip(solvers, work):
+            sol = w["solute"]
+            S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+            its += S.solve("kh", tol=args.tol)["iterations"]
+            S.sfe("kh")
+        return its
+
+    site_points = [len(sites["q"]) * float(np.prod(w["grid"]["n"])) for w in work]
+    spi = []                                  # site-point-iterations of each batched pass
+
+    def batched():
+        jobs = [dict(solver=S, solute=w["solute"], closure="kh", tol=args.tol, sfe="kh")
+                for S, w in zip(solvers, work)]
+        res = capi.solve_batch(jobs, max_inflight=args.inflight)
+        bad = [r for r in res if r["status"] != "OK"]
+        if bad:
+            raise RuntimeError("batch job failed: %s" % bad[0])
+        spi.append(sum(p * r["iterations"] for p, r in zip(site_points, res)))
+        return sum(r["iterations"] for r in res)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = sum(fn() for _ in range(args.steps))
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, its
+
+    clocks = ClockSampler(0)
+    t_seq, it_seq = timed(one_at_a_time)
+    clocks.start()
+    t_bat, it_bat = timed(batched)
+    clk = clocks.stop()
+    n = len(work) * args.steps
+    line = dict(metric=METRIC, value=n / t_bat, unit="solves/s", n_gpus=1, steps=args.steps,
+                warmup=args.warmup, ms_per_step=t_bat * 1e3 / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f32" if args.precision == 32 else "f64",
+                data="synthetic",
+                config=dict(workload="batch64", jobs=len(work), grids="64-128 cubic (2,3,5 sizes) x 0.5 A",
+                            sites=len(sites["q"]), atoms="20-120", closure="kh", tol=args.tol, mdiis=5,
+                            inflight=args.inflight, parallelism="single"),
+                one_at_a_time=dict(value=n / t_seq, unit="solves/s", iterations=it_seq),
+                batched_iterations=it_bat,
+                site_gridpoint_iters_per_s=sum(spi[-args.steps:]) / t_bat,
+                clocks=clk)
+    print(json.dumps(line), flush=True)
+    for S in solvers:
+        S.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -108,6 +108,12 @@ typedef struct {
     int slab_rows;            /* 0: whole y-z planes per block when they fit in shared memory,
                                  else row chunks plus a y-pencil pass (automatic); > 0 forces
                                  chunks of this many rows */
+    int kgrid;                /* 0: periodic integer k grid (the convention above); 1:
+                                 half-integer grid k_m = 2 pi (m + 1/2) / (N d) on every axis
+                                 (the placement of k in the "Numerical procedure" section): no
+                                 k is zero, the transform carries the factor
+                                 exp(-i pi sum_d n_d / N_d) and the fields are antiperiodic
+                                 over the box */
     void *cuda_stream;        /* cudaStream_t to run on; NULL: the library creates one */
     void *workspace;          /* device buffer of >= rism3d_workspace_bytes bytes, 256-byte
                                  aligned, owned by the caller and kept alive until
@@ -193,6 +199,38 @@ rism3d_status rism3d_get(rism3d_ctx *ctx, int field, double *dst, size_t count, 
  * FP64. per_site ([n_sites], host) may be NULL. */
 rism3d_status rism3d_get_sfe(rism3d_ctx *ctx, int kind, int pse_order, double *total,
                              double *per_site);
+
+/* One job of rism3d_solve_batch. Inputs: ctx (a context of its own; the grid may differ from
+ * job to job; jobs run concurrently when their contexts have different streams and in turn
+ * when they share one), an optional solute (n_atoms > 0: set with
+ * rism3d_set_solute when the job starts; 0: keep the context's current solute), the closure,
+ * PSE order and tolerance as for rism3d_solve, and sfe_kind (0 = none, else as
+ * rism3d_get_sfe, evaluated when the solve ends). Outputs: report, sfe (kcal/mol) and the
+ * job's status. */
+typedef struct {
+    rism3d_ctx *ctx;
+    int n_atoms;
+    const double *xyz, *q, *sigma, *eps;   /* host, as rism3d_set_solute */
+    int closure, pse_order;
+    double tol;
+    int sfe_kind;
+    rism3d_report report;     /* out */
+    double sfe;               /* out */
+    rism3d_status status;     /* out */
+} rism3d_batch_job;
+
+/* Solve many independent problems concurrently on one GPU (next row of the method: the
+ * batched form for many solutes on uneven grids; the paper solves one problem at a time).
+ * A host scheduler keeps up to max_inflight jobs in flight, each advancing check_every
+ * iterations per graph launch on its own stream, and starts the next job as soon as one
+ * ends, so small grids that cannot fill the GPU alone share it. Each job computes exactly
+ * what rism3d_solve would (bit-identical results). time_limit_s > 0 bounds each job's wall
+ * time: a job still running past it is stopped after its current chunk and reports
+ * RISM3D_ETIMEOUT with its last iterate readable; 0 means no limit. Returns RISM3D_OK when
+ * every job succeeded, else the first failing job's status (each job's own is in its
+ * record); RISM3D_EINVAL for a bad list (a context in two jobs, several devices). */
+rism3d_status rism3d_solve_batch(rism3d_batch_job *jobs, int n_jobs, int max_inflight,
+                                 double time_limit_s);
 
 /* Partial molar volume of Eq. 19, V = k_B T chi_T (1 - sum_g rho_g int c_g(r) dr), in A^3 per
  * molecule, from the current iterate; kT_chi_T (A^3) is the solvent's k_B T times its

@@ -41,7 +41,7 @@ class Options(ctypes.Structure):
                 ("max_atoms", ctypes.c_int), ("timing", ctypes.c_int),
                 ("accelerator", ctypes.c_int), ("anderson_s1", ctypes.c_double),
                 ("anderson_s2", ctypes.c_double), ("slab_rows", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p),
+                ("kgrid", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
@@ -59,6 +59,13 @@ class Stats(ctypes.Structure):
 class Report(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("rms_residual", ctypes.c_double), ("seconds_iter", ctypes.c_double)]
+
+
+class BatchJob(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("n_atoms", ctypes.c_int), ("xyz", _dp), ("q", _dp),
+                ("sigma", _dp), ("eps", _dp), ("closure", ctypes.c_int), ("pse_order", ctypes.c_int),
+                ("tol", ctypes.c_double), ("sfe_kind", ctypes.c_int), ("report", Report),
+                ("sfe", ctypes.c_double), ("status", ctypes.c_int)]
 
 
 _lib = None
@@ -86,6 +93,7 @@ def load():
         "rism3d_residual": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),
         "rism3d_get": (c_int, [c_void_p, c_int, c_void_p, c_size_t, c_int]),
         "rism3d_get_sfe": (c_int, [c_void_p, c_int, c_int, P(c_double), _dp]),
+        "rism3d_solve_batch": (c_int, [P(BatchJob), c_int, c_int, c_double]),
         "rism3d_get_pmv": (c_int, [c_void_p, c_double, P(c_double), _dp]),
         "rism3d_get_sfe_gradient": (c_int, [c_void_p, _dp]),
         "rism3d_get_stats": (c_int, [c_void_p, P(Stats)]),
@@ -224,13 +232,49 @@ def xrism(sites, n_r=2048, dr=0.05, closure="kh", tol=1e-10, charge_steps=10, th
     return chi, dk.value, its.value, rms.value
 
 
+def solve_batch(jobs, max_inflight=8, time_limit=0.0):
+    """Solve independent problems concurrently (``rism3d_solve_batch``). jobs: list of dicts
+    with keys solver (a Solver of its own), solute (dict xyz/q/sigma/eps, or None to keep the
+    solver's current solute), closure ("kh"), pse_order (3), tol (1e-6), sfe (None or an SFE
+    kind). Returns a list of dicts (status name, iterations, converged, rms, sfe)."""
+    lib = load()
+    arr = (BatchJob * len(jobs))()
+    keep = []
+    for J, d in zip(arr, jobs):
+        S = d["solver"]
+        J.ctx = S.ctx
+        sol = d.get("solute")
+        if sol is not None:
+            xyz, pxyz = _arr(np.asarray(sol["xyz"], dtype=np.float64).reshape(-1, 3))
+            q, pq = _arr(sol["q"])
+            sg, ps = _arr(sol["sigma"])
+            ep, pe = _arr(sol["eps"])
+            keep += [xyz, q, sg, ep]
+            J.n_atoms, J.xyz, J.q, J.sigma, J.eps = len(q), pxyz, pq, ps, pe
+            S.n_atoms = len(q)
+        else:
+            J.n_atoms = 0
+        J.closure = CLOSURES[d.get("closure", "kh")]
+        J.pse_order = int(d.get("pse_order", 3))
+        J.tol = float(d.get("tol", 1e-6))
+        J.sfe_kind = SFE_KINDS[d["sfe"]] if d.get("sfe") else 0
+    lib.rism3d_solve_batch(arr, len(jobs), int(max_inflight), float(time_limit))
+    out = []
+    for J in arr:
+        name = STATUS_NAMES[J.status] if 0 <= J.status < len(STATUS_NAMES) else str(J.status)
+        out.append(dict(status=name, iterations=J.report.iterations,
+                        converged=bool(J.report.converged), rms=J.report.rms_residual, sfe=J.sfe,
+                        seconds=J.report.seconds_iter))
+    return out
+
+
 class Solver:
     """One solvent on one grid (``rism3d_create``); solutes are set and solved in turn."""
 
     def __init__(self, solvent, grid, precision=32, mdiis_nvec=5, mdiis_damp=0.7,
                  dynamic_damp=False, max_iter=10000, check_every=8, max_atoms=100000,
                  timing=False, accelerator="mdiis", anderson_s=(0.2, 0.0), slab_rows=0,
-                 stream=None, device=None):
+                 kgrid="integer", stream=None, device=None):
         import torch
         self._torch = torch
         lib = load()
@@ -253,6 +297,7 @@ class Solver:
         o.accelerator = {"mdiis": 0, "anderson": 1}[accelerator]
         o.anderson_s1, o.anderson_s2 = float(anderson_s[0]), float(anderson_s[1])
         o.slab_rows = int(slab_rows)
+        o.kgrid = {"integer": 0, "half": 1}[kgrid]
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
             o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)

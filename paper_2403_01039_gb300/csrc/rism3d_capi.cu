@@ -1,11 +1,12 @@
 // Host layer of the C ABI declared in include/rism3d.h: validation, device workspace layout,
 // transform plans, the interpolation table of Eq. 13, and the CUDA-graph iteration loop.
-// All arithmetic of the method runs in rism3d_kernels.cu; this file only prepares inputs
+// All arithmetic of the method runs in rism3d_kernels.cuh; this file only prepares inputs
 // (unit conversion, table scaling, twiddle factors) and schedules launches.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -78,7 +79,13 @@ bool make_plan(int L, FftPlan &p) {
     for (int i = 0; i < eights; ++i) t.insert(t.begin(), 8);
     for (int v : r) t.push_back(v);
     if ((int)t.size() > kMaxRadixStages) return false;
-    for (size_t i = 0; i < t.size(); ++i) p.radix[i] = t[i];
+    int ns = 1;
+    for (size_t i = 0; i < t.size(); ++i) {
+        p.radix[i] = t[i];
+        p.dlr[i] = make_fastdiv(L / t[i]);
+        p.dns[i] = make_fastdiv(ns);
+        ns *= t[i];
+    }
     p.nst = (int)t.size();
     return true;
 }
@@ -142,6 +149,10 @@ struct rism3d_ctx {
     rism3d_stats stats{};
     std::vector<cudaEvent_t> ev;               // [check_every][5] around the iteration kernels
     cudaEvent_t ev_aux[2] = {nullptr, nullptr};
+    cudaEvent_t chunk_ev = nullptr;            // end of the last launched iteration chunk
+    // state of the solve in progress (rism3d_solve and the batch scheduler)
+    int run_iter_before = 0, run_closure = kKH, run_order = 1;
+    std::chrono::steady_clock::time_point run_t0;
 
     bool fp32() const { return precision == 32; }
 };
@@ -209,7 +220,7 @@ Layout make_layout(const Geometry &g) {
     L.anchor = take((size_t)2 * g.nv * g.G * g.s);
     L.phase = take((size_t)kPhaseChunk * (g.Nx + g.Ny + g.Kz + 1) * c);
     L.table = take((size_t)g.nk * (g.nv + 1) * g.nv * g.s);
-    L.tw = take((size_t)(g.Nx + g.Ny + g.Kz + g.Kz + 1) * c);
+    L.tw = take((size_t)(g.Nx + g.Ny + g.Kz + g.Kz + 1 + g.Kz + g.Ny + g.Nx) * c);
     L.partials = take((size_t)g.nv * g.Nx * g.nyc * (kMaxHist + 1) * sizeof(double));
     L.sfe = take((size_t)g.nv * kSfeBlocksPerSite * sizeof(double));
     L.atoms = take((size_t)g.max_atoms * kAtomStride * sizeof(double));
@@ -243,6 +254,7 @@ rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, cons
     if (!(op->mdiis_damp > 0.0 && op->mdiis_damp <= 2.0))
         return fail(nullptr, RISM3D_EINVAL, "mdiis_damp must be in (0, 2]");
     if (op->slab_rows < 0) return fail(nullptr, RISM3D_EINVAL, "slab_rows must be >= 0");
+    if (op->kgrid != 0 && op->kgrid != 1) return fail(nullptr, RISM3D_EINVAL, "kgrid must be 0 or 1");
     if (op->accelerator != 0 && op->accelerator != 1)
         return fail(nullptr, RISM3D_EINVAL, "accelerator must be 0 (MDIIS) or 1 (modified Anderson)");
     if (op->max_iter < 1 || op->check_every < 1 || op->max_atoms < 1)
@@ -263,8 +275,8 @@ rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, cons
     const size_t c = 2 * (size_t)g.s;
     g.pitch = g.Kz + 1;
     if (g.pitch % 2 == 0) g.pitch += 1;        // odd pitch: column access without bank conflicts
-    auto plane_bytes = [&](int rows) {
-        return c * ((size_t)rows * g.pitch + g.Kz + g.Ny + g.Kz + 1) +
+    auto plane_bytes = [&](int rows) {   // rows, then twiddles (h, y, z, q), then reduction
+        return c * ((size_t)rows * g.pitch + g.Kz + g.Ny + g.Kz + 1 + g.Kz) +
                (kMaxHist + 1) * (kThreadsPlane / 32) * sizeof(double) + 16;
     };
     // whole y-z planes when they fit in shared memory, else row chunks + a y-pencil pass
@@ -348,6 +360,10 @@ void fill_fields(rism3d_ctx *ctx, const Geometry &g, const Layout &L, Fields<T> 
     f.tw_y = f.tw_x + g.Nx;
     f.tw_h = f.tw_y + g.Ny;
     f.tw_z = f.tw_h + g.Kz;
+    f.tw_q = f.tw_z + g.Kz + 1;
+    f.tw_ys = f.tw_q + g.Kz;
+    f.tw_xs = f.tw_ys + g.Ny;
+    f.half = ctx->opt.kgrid == 1;
     f.px = g.px;
     f.py = g.py;
     f.ph = g.ph;
@@ -360,12 +376,19 @@ void fill_fields(rism3d_ctx *ctx, const Geometry &g, const Layout &L, Fields<T> 
     f.Wy = g.Wy;
     f.ypitch = g.ypitch;
     f.ytiles_main = g.Nx * ((g.Kz + g.Wy - 1) / g.Wy);
-    f.ytiles_nyq = (g.Nx + g.Wy - 1) / g.Wy;
+    f.ytiles_nyq = f.half ? 0 : (g.Nx + g.Wy - 1) / g.Wy;   // the half grid has no Nyquist plane
     f.chunk_y = g.chunk_y;
     f.W = g.W;
     f.pencil_pitch = g.pencil_pitch;
     f.tiles_main = g.Ny * ((g.Kz + g.W - 1) / g.W);
-    f.tiles_nyq = (g.Ny + g.W - 1) / g.W;
+    f.tiles_nyq = f.half ? 0 : (g.Ny + g.W - 1) / g.W;
+    f.dKz = make_fastdiv(g.Kz);
+    f.dKz1h = make_fastdiv(g.Kz / 2 + 1);
+    f.dKzp = make_fastdiv((g.Kz + 1) / 2);
+    f.dW = make_fastdiv(g.W);
+    f.dNx = make_fastdiv(g.Nx);
+    f.dWy = make_fastdiv(g.Wy > 0 ? g.Wy : 1);
+    f.dNy = make_fastdiv(g.Ny);
     for (int i = 0; i < kMaxSites; ++i) f.bq[i] = i < g.nv ? ctx->beta * ctx->q[i] : 0.0;
     for (int d = 0; d < 3; ++d) {
         const int N = d == 0 ? g.Nx : (d == 1 ? g.Ny : g.Nz);
@@ -421,6 +444,16 @@ rism3d_status upload_tables(rism3d_ctx *ctx, const rism3d_solvent *sv, const Lay
     push_twiddles<T>(tw, ctx->Ny, ctx->Ny);
     push_twiddles<T>(tw, ctx->Kz, ctx->Kz);
     push_twiddles<T>(tw, ctx->Nz, ctx->Kz + 1);
+    // half grid: exp(-i pi (2m + 1) / Nz) and the per-axis shifts exp(-i pi n / N)
+    auto push_angle = [&](double a) {
+        C c;
+        c.x = (T)std::cos(a);
+        c.y = (T)std::sin(a);
+        tw.push_back(c);
+    };
+    for (int m = 0; m < ctx->Kz; ++m) push_angle(-kPi * (2.0 * m + 1.0) / ctx->Nz);
+    for (int m = 0; m < ctx->Ny; ++m) push_angle(-kPi * (double)m / ctx->Ny);
+    for (int m = 0; m < ctx->Nx; ++m) push_angle(-kPi * (double)m / ctx->Nx);
     CUDA_TRY(ctx, cudaMemcpy(b + L.tw, tw.data(), tw.size() * sizeof(C), cudaMemcpyHostToDevice));
     f.inv_dk = 1.0 / sv->dk;
     CUDA_TRY(ctx, prepare_kernels<T>(f));
@@ -497,7 +530,7 @@ rism3d_status iteration(rism3d_ctx *ctx, bool with_mdiis) {
 void account_iterations(rism3d_ctx *ctx, const Ctrl &c) {
     const double P = (double)ctx->nv * (double)ctx->G;
     const double s = ctx->fp32() ? 4.0 : 8.0;
-    const double z = (double)(ctx->Kz + 1) / (double)ctx->Kz;
+    const double z = ctx->opt.kgrid == 1 ? 1.0 : (double)(ctx->Kz + 1) / (double)ctx->Kz;   // half spectrum per real
     const double it = (double)c.acc_iters;
     ctx->stats.iterations += c.acc_iters;
     ctx->stats.bytes[0] += P * s * ((double)c.acc_fwd_units + it * (1.0 + z) +
@@ -801,7 +834,7 @@ rism3d_status rism3d_set_solute(rism3d_ctx *ctx, int n_atoms, const double *xyz,
                                   cudaMemcpyHostToDevice, ctx->stream));
     const double amp0 = 4.0 * kPi * kCoulomb * ctx->beta / ctx->dV;
     const double P = (double)ctx->nv * ctx->G, sb = ctx->fp32() ? 4.0 : 8.0;
-    const double z = (double)(ctx->Kz + 1) / ctx->Kz;
+    const double z = ctx->opt.kgrid == 1 ? 1.0 : (double)(ctx->Kz + 1) / ctx->Kz;
     {
         AuxTimer tm(ctx, 4);
         if (ctx->fp32())
@@ -849,41 +882,65 @@ rism3d_status rism3d_set_guess(rism3d_ctx *ctx, const double *t, int on_device) 
     return RISM3D_OK;
 }
 
-rism3d_status rism3d_solve(rism3d_ctx *ctx, int closure, int pse_order, double tol, rism3d_report *rep) {
-    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+// A solve in phases, so that the batch scheduler can interleave contexts: begin (graph,
+// control block), launch a chunk of check_every iterations (graph + status read-back +
+// event), take a finished chunk's accounting, finish (final control block, report).
+static rism3d_status solve_begin(rism3d_ctx *ctx, int closure, int pse_order, double tol) {
     if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "solve before set_solute");
     if (!valid_closure(closure, pse_order)) return fail(ctx, RISM3D_EINVAL, "bad closure %d / order %d", closure, pse_order);
     if (!(tol > 0.0)) return fail(ctx, RISM3D_EINVAL, "tol must be positive");
-    DeviceGuard dg(ctx->device);
-    auto t0 = std::chrono::steady_clock::now();
+    ctx->run_t0 = std::chrono::steady_clock::now();
     rism3d_status st = build_graph(ctx);
     if (st != RISM3D_OK) return st;
+    if (!ctx->chunk_ev) CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->chunk_ev, cudaEventDisableTiming));
     Ctrl &c = *ctx->ctrl_host;
     reset_ctrl(ctx, c);
     closure_stages(closure, pse_order, tol, c);
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, ctx->stream));
+    ctx->run_iter_before = 0;
+    ctx->run_closure = closure;
+    ctx->run_order = pse_order;
+    return RISM3D_OK;
+}
+
+static rism3d_status solve_launch_chunk(rism3d_ctx *ctx) {
+    CUDA_TRY(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ctrl_host, ctx->ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaEventRecord(ctx->chunk_ev, ctx->stream));
+    return RISM3D_OK;
+}
+
+// After the chunk's event has completed: launch counts and kernel times; *running tells
+// whether the solve needs another chunk.
+static rism3d_status solve_chunk_done(rism3d_ctx *ctx, bool *running) {
+    const Ctrl &c = *ctx->ctrl_host;
     const int K = ctx->opt.check_every;
-    int iter_before = 0;
-    for (;;) {
-        CUDA_TRY(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
-        CUDA_TRY(ctx, cudaMemcpyAsync(&c, ctx->ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-        const int ran = c.iter - iter_before;
-        iter_before = c.iter;
-        int slots[8];
-        const int nk = iteration_slots(ctx, true, slots);
-        for (int k = 0; k < nk; ++k) ctx->stats.launches[slots[k]] += K;
-        if (ctx->opt.timing) {
-            for (int i = 0; i < ran && i < K; ++i)
-                for (int k = 0; k < nk; ++k) {
-                    float ms = 0.f;
-                    const size_t e0 = (size_t)i * kEventsPerIter + k;
-                    CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev[e0], ctx->ev[e0 + 1]));
-                    ctx->stats.ms[slots[k]] += ms;
-                    ctx->stats.timed[slots[k]] += 1;
-                }
-        }
-        if (c.status != kRunning) break;
+    const int ran = c.iter - ctx->run_iter_before;
+    ctx->run_iter_before = c.iter;
+    int slots[8];
+    const int nk = iteration_slots(ctx, true, slots);
+    for (int k = 0; k < nk; ++k) ctx->stats.launches[slots[k]] += K;
+    if (ctx->opt.timing) {
+        for (int i = 0; i < ran && i < K; ++i)
+            for (int k = 0; k < nk; ++k) {
+                float ms = 0.f;
+                const size_t e0 = (size_t)i * kEventsPerIter + k;
+                CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev[e0], ctx->ev[e0 + 1]));
+                ctx->stats.ms[slots[k]] += ms;
+                ctx->stats.timed[slots[k]] += 1;
+            }
+    }
+    *running = c.status == kRunning;
+    return RISM3D_OK;
+}
+
+// stop = true ends a running solve early (batch time limit): the device control block is
+// marked stopped so that kernels still queued return at once.
+static rism3d_status solve_finish(rism3d_ctx *ctx, rism3d_report *rep, bool stop) {
+    Ctrl &c = *ctx->ctrl_host;
+    if (stop) {
+        c.status = kStopped;
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ctrl, &c, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     }
     CUDA_TRY(ctx, cudaMemcpyAsync(&c, ctx->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -891,17 +948,116 @@ rism3d_status rism3d_solve(rism3d_ctx *ctx, int closure, int pse_order, double t
     account_iterations(ctx, c);
     ctx->stats.solves += 1;
     ctx->cur_slot = c.cur;
-    ctx->last_kind = closure;
-    ctx->last_order = closure == kPSE ? pse_order : (closure == kKH ? 1 : 0);
+    ctx->last_kind = ctx->run_closure;
+    ctx->last_order = ctx->run_closure == kPSE ? ctx->run_order : (ctx->run_closure == kKH ? 1 : 0);
     if (rep) {
         rep->iterations = c.iter;
         rep->converged = c.status == kConverged;
         rep->rms_residual = c.rms;
-        rep->seconds_iter = std::chrono::duration<double>(t1 - t0).count();
+        rep->seconds_iter = std::chrono::duration<double>(t1 - ctx->run_t0).count();
     }
+    if (c.status == kStopped)
+        return fail(ctx, RISM3D_ETIMEOUT, "stopped by the time limit at iteration %d (rms %.3e)", c.iter, c.rms);
     if (c.status == kDiverged) return fail(ctx, RISM3D_EDIVERGED, "non-finite residual at iteration %d", c.iter);
     if (c.status == kMaxIter)
         return fail(ctx, RISM3D_ENOTCONV, "not converged after %d iterations (rms %.3e)", c.iter, c.rms);
+    return RISM3D_OK;
+}
+
+rism3d_status rism3d_solve(rism3d_ctx *ctx, int closure, int pse_order, double tol, rism3d_report *rep) {
+    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+    DeviceGuard dg(ctx->device);
+    rism3d_status st = solve_begin(ctx, closure, pse_order, tol);
+    if (st != RISM3D_OK) return st;
+    for (;;) {
+        if ((st = solve_launch_chunk(ctx)) != RISM3D_OK) return st;
+        CUDA_TRY(ctx, cudaEventSynchronize(ctx->chunk_ev));
+        bool running = false;
+        if ((st = solve_chunk_done(ctx, &running)) != RISM3D_OK) return st;
+        if (!running) break;
+    }
+    return solve_finish(ctx, rep, false);
+}
+
+rism3d_status rism3d_solve_batch(rism3d_batch_job *jobs, int n_jobs, int max_inflight, double time_limit_s) {
+    if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(nullptr, RISM3D_EINVAL, "bad job list");
+    if (max_inflight < 1) return fail(nullptr, RISM3D_EINVAL, "max_inflight must be >= 1");
+    for (int j = 0; j < n_jobs; ++j) {    // a job that never starts reports ESTATE
+        jobs[j].status = RISM3D_ESTATE;
+        jobs[j].sfe = 0.0;
+        jobs[j].report = rism3d_report{};
+    }
+    int device = -1;
+    for (int j = 0; j < n_jobs; ++j) {
+        rism3d_ctx *c = jobs[j].ctx;
+        if (!c) return fail(nullptr, RISM3D_EINVAL, "job %d has no context", j);
+        if (device < 0) device = c->device;
+        if (c->device != device) return fail(nullptr, RISM3D_EINVAL, "jobs span more than one device");
+        for (int i = 0; i < j; ++i)
+            if (jobs[i].ctx == c) return fail(nullptr, RISM3D_EINVAL, "jobs %d and %d share a context", i, j);
+    }
+    if (n_jobs == 0) return RISM3D_OK;
+    DeviceGuard dg(device);
+    using clock = std::chrono::steady_clock;
+    std::vector<int> active;
+    std::vector<clock::time_point> started(n_jobs);
+    int next = 0, done = 0;
+    auto end_job = [&](int j, rism3d_status st) {
+        rism3d_batch_job &J = jobs[j];
+        if (J.sfe_kind && (st == RISM3D_OK || st == RISM3D_ENOTCONV)) {
+            const rism3d_status s2 = rism3d_get_sfe(J.ctx, J.sfe_kind, J.pse_order, &J.sfe, nullptr);
+            if (st == RISM3D_OK) st = s2;
+        }
+        J.status = st;
+        ++done;
+    };
+    auto start_job = [&](int j) {
+        rism3d_batch_job &J = jobs[j];
+        started[j] = clock::now();
+        rism3d_status st = RISM3D_OK;
+        if (J.n_atoms > 0) st = rism3d_set_solute(J.ctx, J.n_atoms, J.xyz, J.q, J.sigma, J.eps);
+        if (st == RISM3D_OK) st = solve_begin(J.ctx, J.closure, J.pse_order, J.tol);
+        if (st == RISM3D_OK) st = solve_launch_chunk(J.ctx);
+        if (st != RISM3D_OK) {
+            end_job(j, st);
+            return;
+        }
+        active.push_back(j);
+    };
+    while (done < n_jobs) {
+        while ((int)active.size() < max_inflight && next < n_jobs) start_job(next++);
+        bool progressed = false;
+        for (size_t a = 0; a < active.size();) {
+            const int j = active[a];
+            rism3d_ctx *c = jobs[j].ctx;
+            const cudaError_t q = cudaEventQuery(c->chunk_ev);
+            if (q == cudaErrorNotReady) {
+                ++a;
+                continue;
+            }
+            progressed = true;
+            rism3d_status st = q == cudaSuccess ? RISM3D_OK
+                                                : fail(c, RISM3D_ECUDA, "chunk: %s", cudaGetErrorString(q));
+            bool running = false;
+            if (st == RISM3D_OK) st = solve_chunk_done(c, &running);
+            const bool late = time_limit_s > 0.0 &&
+                              std::chrono::duration<double>(clock::now() - started[j]).count() > time_limit_s;
+            if (st == RISM3D_OK && running && !late) {
+                st = solve_launch_chunk(c);
+                if (st == RISM3D_OK) {
+                    ++a;
+                    continue;
+                }
+            }
+            if (st == RISM3D_OK) st = solve_finish(c, &jobs[j].report, running && late);
+            active.erase(active.begin() + a);
+            end_job(j, st);
+            if (next < n_jobs) start_job(next++);
+        }
+        if (!progressed) std::this_thread::yield();
+    }
+    for (int j = 0; j < n_jobs; ++j)
+        if (jobs[j].status != RISM3D_OK) return jobs[j].status;
     return RISM3D_OK;
 }
 
@@ -1072,6 +1228,7 @@ void rism3d_destroy(rism3d_ctx *ctx) {
             if (e) cudaEventDestroy(e);
         for (auto e : ctx->ev_aux)
             if (e) cudaEventDestroy(e);
+        if (ctx->chunk_ev) cudaEventDestroy(ctx->chunk_ev);
         if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
         if (ctx->ctrl_host) cudaFreeHost(ctx->ctrl_host);
         if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

@@ -1,4 +1,4 @@
-// Internal declarations shared by the kernels (rism3d_kernels.cu) and the host layer
+// Internal declarations shared by the kernels (rism3d_kernels.cuh) and the host layer
 // (rism3d_capi.cu). Not part of the public ABI.
 #pragma once
 #include <cuda_runtime.h>
@@ -14,15 +14,38 @@ constexpr int kThreadsPlane = 256;
 constexpr int kThreadsPencil = 256;
 
 // Solver status words written by the device (Ctrl::status).
-enum { kRunning = 0, kConverged = 1, kDiverged = 2, kMaxIter = 3 };
+enum { kRunning = 0, kConverged = 1, kDiverged = 2, kMaxIter = 3, kStopped = 4 };
 enum { kKH = 1, kHNC = 2, kPSE = 3 };
 
 // Mixed-radix plan of one transform length: L = prod(radix[0..nst)).
+// Division by a run-time constant d (1 <= d < 2^31) for 0 <= n < 2^31 with one high
+// multiply: q = (umulhi(n, mul) + n) >> l, l = ceil(log2 d), mul = floor(2^32 (2^l - d) / d) + 1
+// (the round-up method of Granlund and Montgomery). Used in the index arithmetic of the
+// element loops, where a hardware-less integer division costs tens of instructions.
+struct FastDiv {
+    unsigned d, mul, l;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+    FastDiv f;
+    f.d = d;
+    f.l = 0;
+    while ((1ull << f.l) < d) ++f.l;
+    f.mul = (unsigned)((((1ull << 32) * ((1ull << f.l) - d)) / d) + 1);
+    return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ int fdiv(int n, const FastDiv &f) {
+    return (int)((__umulhi((unsigned)n, f.mul) + (unsigned)n) >> f.l);
+}
+#endif
+
 struct FftPlan {
     int L;
     int nst;
     int radix[kMaxRadixStages];
     int seq_per_warp;               // > 0: warp-cooperative transform of this many sequences
+    FastDiv dlr[kMaxRadixStages];   // per stage: L / radix (butterflies per sequence)
+    FastDiv dns[kMaxRadixStages];   // per stage: product of the earlier radices
 };
 
 // Device-resident solver state. The iteration kernels read it on every launch, so one
@@ -92,6 +115,9 @@ struct Fields {
     int nk;
     double inv_dk;
     C *tw_x, *tw_y, *tw_h, *tw_z;   // exp(-2 pi i m / L) for L = Nx, Ny, Kz, Nz
+    int half;                       // 1: half-integer k grid
+    C *tw_q;                        // half grid: exp(-i pi (2m + 1) / Nz), m < Kz
+    C *tw_ys, *tw_xs;               // half grid: exp(-i pi n / N) for N = Ny, Nx
     FftPlan px, py, ph;
     int chunk_rows, chunk_cols_fwd, chunk_x;   // batch chunk sizes of the in-place FFTs
     int pitch;                      // complex row pitch of a plane in shared memory
@@ -100,6 +126,7 @@ struct Fields {
     int W;                          // columns per pencil tile
     int tiles_main, tiles_nyq;
     int pencil_pitch;
+    FastDiv dKz, dKz1h, dKzp, dW, dNx, dWy, dNy;   // Kz, Kz/2 + 1, (Kz + 1)/2, W, Nx, Wy, Ny
     double bq[kMaxSites];           // beta * q_gamma
     double ks[3];                   // 2 pi / (N d) per axis
     double *partials;               // [kMaxHist + 1][nv * Nx * nyc] (value-major)

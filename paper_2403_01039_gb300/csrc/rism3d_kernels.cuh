@@ -136,6 +136,7 @@ struct StageIdx {
     int LR, Ns, step;
     bool pow2;
     int lgLR, lgNs;
+    FastDiv dLR, dNs;
     __device__ __forceinline__ void split(int it, int &b, int &j, int &k, int &jq) const {
         if (pow2) {
             b = it >> lgLR;
@@ -143,22 +144,25 @@ struct StageIdx {
             k = j & (Ns - 1);
             jq = j >> lgNs;
         } else {
-            b = it / LR;
+            b = fdiv(it, dLR);
             j = it - b * LR;
-            jq = j / Ns;
+            jq = fdiv(j, dNs);
             k = j - jq * Ns;
         }
     }
 };
 
-__device__ __forceinline__ StageIdx make_stage(int L, int R, int Ns) {
+__device__ __forceinline__ StageIdx make_stage(const FftPlan &p, int st, int Ns) {
     StageIdx s;
+    const int L = p.L, R = p.radix[st];
     s.LR = L / R;
     s.Ns = Ns;
     s.step = L / (Ns * R);
     s.pow2 = ((L & (L - 1)) == 0) && ((R & (R - 1)) == 0);
     s.lgLR = __ffs(s.LR) - 1;
     s.lgNs = __ffs(Ns) - 1;
+    s.dLR = p.dlr[st];
+    s.dNs = p.dns[st];
     return s;
 }
 
@@ -211,7 +215,7 @@ __device__ __forceinline__ void fft_stages_inl(C *base, const FftPlan &p, int es
     int Ns = 1;
     for (int st = 0; st < p.nst; ++st) {
         const int R = p.radix[st];
-        const StageIdx si = make_stage(p.L, R, Ns);
+        const StageIdx si = make_stage(p, st, Ns);
         switch (R) {
             case 8: fft_stage<C, 8, MAXC / 8, WARP>(base, si, es, nbc, bs, tw, sign, tid, nthr); break;
             case 4: fft_stage<C, 4, MAXC / 4, WARP>(base, si, es, nbc, bs, tw, sign, tid, nthr); break;
@@ -224,12 +228,99 @@ __device__ __forceinline__ void fft_stages_inl(C *base, const FftPlan &p, int es
     }
 }
 
+// Power-of-two lengths 16..256 take a transform whose passes are fixed at compile time:
+// radix 8 passes, then one pass of the remaining radix (2, 4 or 8). T = L/8 threads share a
+// sequence (all within one warp, so passes are separated by warp barriers) and each holds 8
+// values per pass; the first pass needs no twiddles. Its outputs are written stride-8
+// apart, which would put several lanes on one shared-memory bank, so the hand-off between
+// the first and second pass uses the permuted position i ^ ((i >> 3) & 7) (a bijection of
+// 0..L-1 that only permutes within groups of 8); every other layout is the natural one.
+__host__ __device__ constexpr int p2_pow8(int p) { return p == 0 ? 1 : 8 * p2_pow8(p - 1); }
+__host__ __device__ constexpr int p2_npass(int L) { return L <= 8 ? 1 : 1 + p2_npass(L / 8); }
+__host__ __device__ constexpr int p2_radix(int L, int p) {
+    return p + 1 < p2_npass(L) ? 8 : L / p2_pow8(p);
+}
+__device__ __forceinline__ int p2_swz(int i) { return i ^ ((i >> 3) & 7); }
+
+template <typename C, int L, int P>
+__device__ __forceinline__ void p2_pass(C *seq, int es, int u, const C *tw, int sign, bool act) {
+    constexpr int NP = p2_npass(L);
+    constexpr int R = p2_radix(L, P);
+    constexpr int NS = p2_pow8(P);
+    constexpr int T = L / 8, LR = L / R, NB = 8 / R;
+    constexpr bool SWZ_IN = P == 1;
+    constexpr bool SWZ_OUT = P == 0 && NP > 1;
+    C v[8];
+    if (act) {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int j = u + q * T;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int li = j + r * LR;
+                C a = seq[(SWZ_IN ? p2_swz(li) : li) * es];
+                if (NS > 1 && r > 0) {
+                    C w = tw[(j & (NS - 1)) * r * (L / (NS * R))];
+                    if (sign > 0) w.y = -w.y;
+                    a = cmul(a, w);
+                }
+                v[q * R + r] = a;
+            }
+        }
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int j = u + q * T;
+            Dft<R>::run(&v[q * R], sign);
+            const int d0 = (j / NS) * (NS * R) + (j & (NS - 1));
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int li = d0 + r * NS;
+                seq[(SWZ_OUT ? p2_swz(li) : li) * es] = v[q * R + r];
+            }
+        }
+    }
+    __syncwarp();
+}
+
+template <typename C, int L>
+__device__ __forceinline__ void p2_seq(C *seq, int es, int u, const C *tw, int sign, bool act) {
+    p2_pass<C, L, 0>(seq, es, u, tw, sign, act);
+    if constexpr (p2_npass(L) > 1) p2_pass<C, L, 1>(seq, es, u, tw, sign, act);
+    if constexpr (p2_npass(L) > 2) p2_pass<C, L, 2>(seq, es, u, tw, sign, act);
+}
+
+// nb sequences of length L (element stride es, sequence stride bs); ends with a block
+// barrier like fft_smem.
+template <typename C, int L>
+__device__ void fft_p2(C *buf, int es, int nb, int bs, const C *tw, int sign) {
+    static_assert(L >= 16 && L <= 256, "warp-resident power-of-two lengths only");
+    constexpr int T = L / 8, SPW = 32 / T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int u = lane & (T - 1), sl = lane / T;
+    for (int g0 = warp * SPW; g0 < nb; g0 += nw * SPW) {
+        const int b = g0 + sl;
+        p2_seq<C, L>(buf + (long)(b < nb ? b : 0) * bs, es, u, tw, sign, b < nb);
+    }
+    __syncthreads();
+}
+
 // Transform the nb sequences. When the plan allows (seq_per_warp > 0), each warp takes its
 // own groups of seq_per_warp sequences and separates stages with warp barriers only;
 // otherwise the whole block takes chunks of `chunk` sequences with block barriers.
 template <typename C, int MAXC>
 __device__ void fft_smem(C *buf, const FftPlan &p, int es, int nb, int bs, int chunk, const C *tw,
                          int sign) {
+    switch (p.L) {
+        case 16: fft_p2<C, 16>(buf, es, nb, bs, tw, sign); return;
+        case 32: fft_p2<C, 32>(buf, es, nb, bs, tw, sign); return;
+        case 64: fft_p2<C, 64>(buf, es, nb, bs, tw, sign); return;
+        case 128: fft_p2<C, 128>(buf, es, nb, bs, tw, sign); return;
+        case 256: fft_p2<C, 256>(buf, es, nb, bs, tw, sign); return;
+        default: break;
+    }
     if (p.seq_per_warp > 0) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         const int S = p.seq_per_warp;
@@ -342,14 +433,212 @@ template <> struct Vec2<double> { typedef double2 type; };
 __device__ __forceinline__ float2 ld2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
 __device__ __forceinline__ double2 ld2(const double *p) { return __ldg(reinterpret_cast<const double2 *>(p)); }
 
+// ------------------------------------------------------------------ row helpers
+// z transform of nr <= 256 / L rows (row stride bs) by one warp with the power-of-two
+// transform of length L (L/8 lanes per row).
+template <typename C, int L>
+__device__ __forceinline__ void fft_rows_warp(C *rows, int nr, int bs, const C *tw, int sign, int lane) {
+    constexpr int T = L / 8;
+    constexpr int LG = L == 16 ? 1 : (L == 32 ? 2 : (L == 64 ? 3 : (L == 128 ? 4 : 5)));
+    const int sl = lane >> LG;
+    p2_seq<C, L>(rows + (long)min(sl, nr - 1) * bs, 1, lane & (T - 1), tw, sign, sl < nr);
+}
+
+// Real-to-complex post-processing of nr rows after the half-length complex transform:
+// X[k] = E[k] + w^k O[k] for k = 0..Kz. X[0] and X[Kz] are real; packed = true stores them
+// as one complex value X[0] + i X[Kz] in row[0] (the y transform then takes both real
+// columns as one complex column), else row[0] = X[0] and row[Kz] = X[Kz].
+template <typename C>
+__device__ __forceinline__ void r2c_rows(C *rows, int nr, int Kz, int pitch, const C *tw_z, const FastDiv &dh1,
+                                         int tid, int nthr, bool packed) {
+    typedef decltype(rows[0].x) R;
+    const int half = Kz / 2;
+    for (int idx = tid; idx < nr * (half + 1); idx += nthr) {
+        const int y = fdiv(idx, dh1), k = idx - y * (half + 1);
+        C *row = rows + y * pitch;
+        if (k == 0) {
+            C z = row[0];
+            if (packed) {
+                row[0] = cmk(z.x + z.y, z.x - z.y);
+            } else {
+                row[0] = cmk(z.x + z.y, (R)0);
+                row[Kz] = cmk(z.x - z.y, (R)0);
+            }
+        } else {
+            const int k2 = Kz - k;
+            C a = row[k], b = row[k2];
+            C e1 = cscale(cadd(a, cconj(b)), (R)0.5);
+            C o1 = cscale(csub(a, cconj(b)), (R)0.5);
+            C X1 = cadd(e1, cmul(cmuli(o1, -1), tw_z[k]));
+            if (k2 != k) {
+                C e2 = cscale(cadd(b, cconj(a)), (R)0.5);
+                C o2 = cscale(csub(b, cconj(a)), (R)0.5);
+                row[k2] = cadd(e2, cmul(cmuli(o2, -1), tw_z[k2]));
+            }
+            row[k] = X1;
+        }
+    }
+}
+
+// Complex-to-real pre-processing of nr rows before the inverse half-length transform:
+// Z[k] = (X[k] + conj X[Kz-k]) + i w^-k (X[k] - conj X[Kz-k]). packed = true: row[0] holds
+// X[0] + i X[Kz] (both real), as r2c_rows writes it.
+template <typename C>
+__device__ __forceinline__ void c2r_rows(C *rows, int nr, int Kz, int pitch, const C *tw_z, const FastDiv &dh1,
+                                         int tid, int nthr, bool packed) {
+    typedef decltype(rows[0].x) R;
+    const int half = Kz / 2;
+    for (int idx = tid; idx < nr * (half + 1); idx += nthr) {
+        const int y = fdiv(idx, dh1), k = idx - y * (half + 1);
+        C *row = rows + y * pitch;
+        const int k2 = Kz - k;
+        C a = row[k], b = row[k2];
+        if (packed && k == 0) {
+            b = cmk(a.y, (R)0);
+            a = cmk(a.x, (R)0);
+        }
+        C Z1 = cadd(cadd(a, cconj(b)), cmuli(cmul(csub(a, cconj(b)), cconj(tw_z[k])), +1));
+        if (k != 0 && k2 != k)
+            row[k2] = cadd(cadd(b, cconj(a)), cmuli(cmul(csub(b, cconj(a)), cconj(tw_z[k2])), +1));
+        row[k] = Z1;
+    }
+}
+
+// Half-integer grid, real-to-complex step of nr rows: with Z the half-length transform of
+// the pre-twiddled packed row, X(m + 1/2) = E(m) + exp(-i pi (2m + 1) / Nz) O(m),
+// E(m) = (Z(m) + conj Z(M-1-m)) / 2, O(m) = -i (Z(m) - conj Z(M-1-m)) / 2 (M = Kz values, no
+// real or Nyquist terms); the result is multiplied by the row's y and x shift factors ph.
+template <typename C>
+__device__ __forceinline__ void r2c_rows_half(C *rows, int nr, int yg, int Kz, int pitch, const C *tw_q,
+                                              const C *tw_ys, C phx, const FastDiv &dp, int tid, int nthr) {
+    typedef decltype(rows[0].x) R;
+    const int np = (Kz + 1) / 2;
+    for (int idx = tid; idx < nr * np; idx += nthr) {
+        const int y = fdiv(idx, dp), m = idx - y * np, m2 = Kz - 1 - m;
+        C *row = rows + y * pitch;
+        const C ph = cmul(tw_ys[yg + y], phx);
+        const C a = row[m], b = row[m2];
+        const C X1 = cadd(cscale(cadd(a, cconj(b)), (R)0.5), cmul(tw_q[m], cscale(cmuli(csub(a, cconj(b)), -1), (R)0.5)));
+        if (m2 != m)
+            row[m2] = cmul(cadd(cscale(cadd(b, cconj(a)), (R)0.5),
+                                cmul(tw_q[m2], cscale(cmuli(csub(b, cconj(a)), -1), (R)0.5))), ph);
+        row[m] = cmul(X1, ph);
+    }
+}
+
+// Half-integer grid, complex-to-real step of nr rows (inverse of r2c_rows_half, up to the
+// factor Nz of the unnormalised transforms): the row is first multiplied by conj(ph), then
+// Z(m) = (X(m) + conj X(M-1-m)) + i conj(exp(-i pi (2m + 1) / Nz)) (X(m) - conj X(M-1-m)).
+template <typename C>
+__device__ __forceinline__ void c2r_rows_half(C *rows, int nr, int yg, int Kz, int pitch, const C *tw_q,
+                                              const C *tw_ys, C phx, const FastDiv &dp, int tid, int nthr) {
+    const int np = (Kz + 1) / 2;
+    for (int idx = tid; idx < nr * np; idx += nthr) {
+        const int y = fdiv(idx, dp), m = idx - y * np, m2 = Kz - 1 - m;
+        C *row = rows + y * pitch;
+        const C ph = cconj(cmul(tw_ys[yg + y], phx));
+        const C a = cmul(row[m], ph), b = cmul(row[m2], ph);
+        const C Z1 = cadd(cadd(a, cconj(b)), cmuli(cmul(csub(a, cconj(b)), cconj(tw_q[m])), +1));
+        if (m2 != m)
+            row[m2] = cadd(cadd(b, cconj(a)), cmuli(cmul(csub(b, cconj(a)), cconj(tw_q[m2])), +1));
+        row[m] = Z1;
+    }
+}
+
 // ------------------------------------------------------------------ pass 1: plane_fwd
-// One block per (x plane or row chunk of one, site). MAXH bounds the stored MDIIS pairs the
-// update combines (5, 8 or 16), so the loop over them unrolls.
+// Per-launch values of the update and closure, shared by the element loops.
 template <typename T, int MAXH>
+struct FwdArgs {
+    const T *coef;               // [MAXH] update coefficients (shared memory)
+    const long long *slot_off;   // [MAXH] ring offsets of the combined pairs (shared memory)
+    int upd_n, do_update, kind, order, anchor, refresh;
+    T eta;
+    T *tcur, *ca;                // this block's part of the new iterate and of c^sr_a
+    const T *wp;                 // this block's part of w = f - beta u
+    const typename Cx<T>::type *pre;   // half grid: exp(-i pi p / Kz) per packed element, else null
+};
+
+// Update (Eq. 40) + closure + c^sr (Eq. 31) of the elements e in [e0, e1) of the block's
+// rows (e = row * Kz + m; complex element m packs the reals 2m, 2m + 1), written into the
+// row buffer. tid / nthr split them, two elements per thread and step with every load
+// issued before any store.
+template <typename T, int MAXH>
+__device__ __forceinline__ void fwd_elements(const Fields<T> &f, const FwdArgs<T, MAXH> &A,
+                                             typename Cx<T>::type *buf, int y0, int e0, int e1, int tid,
+                                             int nthr) {
+    typedef typename Cx<T>::type C;
+    typedef typename Vec2<T>::type V2;
+    const int Kz = f.Kz, pitch = f.pitch;
+    for (int i0 = e0 + tid; i0 < e1; i0 += 2 * nthr) {
+        const int i1 = i0 + nthr;
+        const bool has1 = i1 < e1;
+        const int yA = fdiv(i0, f.dKz), mA = i0 - yA * Kz;
+        const int yB = has1 ? fdiv(i1, f.dKz) : yA, mB = has1 ? i1 - yB * Kz : mA;
+        const long long oA = (long long)(y0 + yA) * f.Nz + 2 * mA;
+        const long long oB = (long long)(y0 + yB) * f.Nz + 2 * mB;
+        V2 tA, tB;
+        if (A.do_update) {
+            tA.x = tA.y = tB.x = tB.y = (T)0;
+#pragma unroll
+            for (int i = 0; i < MAXH; ++i) {
+                if (i < A.upd_n) {
+                    const T *xb = f.X + A.slot_off[i], *rb = f.R + A.slot_off[i];
+                    const V2 xa = ld2(xb + oA), ra = ld2(rb + oA);
+                    const V2 xv = ld2(xb + oB), rv = ld2(rb + oB);
+                    const T c = A.coef[i];
+                    tA.x += c * (xa.x + A.eta * ra.x);
+                    tA.y += c * (xa.y + A.eta * ra.y);
+                    tB.x += c * (xv.x + A.eta * rv.x);
+                    tB.y += c * (xv.y + A.eta * rv.y);
+                }
+            }
+        } else {
+            tA = ld2(A.tcur + oA);
+            tB = ld2(A.tcur + oB);
+        }
+        const V2 wA = ld2(A.wp + oA), wB = ld2(A.wp + oB);
+        V2 aA, aB;
+        if (A.anchor) {
+            aA = ld2(A.ca + oA);
+            aB = ld2(A.ca + oB);
+        }
+        V2 cA, cB;
+        cA.x = closure_g(wA.x + tA.x, A.kind, A.order) - (T)1 - tA.x;
+        cA.y = closure_g(wA.y + tA.y, A.kind, A.order) - (T)1 - tA.y;
+        cB.x = closure_g(wB.x + tB.x, A.kind, A.order) - (T)1 - tB.x;
+        cB.y = closure_g(wB.y + tB.y, A.kind, A.order) - (T)1 - tB.y;
+        C dA = cmk(cA.x, cA.y), dB = cmk(cB.x, cB.y);
+        if (A.anchor) {                        // transform only c^sr - c^sr_a
+            dA.x -= aA.x;
+            dA.y -= aA.y;
+            dB.x -= aB.x;
+            dB.y -= aB.y;
+        }
+        if (A.pre) {                           // half grid: z shift of the packed element
+            dA = cmul(dA, A.pre[mA]);
+            dB = cmul(dB, A.pre[mB]);
+        }
+        if (A.do_update) *reinterpret_cast<V2 *>(A.tcur + oA) = tA;
+        if (A.refresh) *reinterpret_cast<V2 *>(A.ca + oA) = cA;
+        buf[yA * pitch + mA] = dA;
+        if (has1) {
+            if (A.do_update) *reinterpret_cast<V2 *>(A.tcur + oB) = tB;
+            if (A.refresh) *reinterpret_cast<V2 *>(A.ca + oB) = cB;
+            buf[yB * pitch + mB] = dB;
+        }
+    }
+}
+
+// One block per (x plane or row chunk of one, site). MAXH bounds the stored MDIIS pairs the
+// update combines (5, 8 or 16), so the loop over them unrolls. LZ = Nz / 2 when the kernel is
+// specialised for that power-of-two length (64 or 128): each warp then takes its own
+// 256 / LZ rows at a time through update, closure, z transform and real-to-complex step
+// with warp barriers only, so that its loads overlap other warps' arithmetic. LZ = 0 is the
+// block-wide form for any length. The y transform needs the whole plane in both.
+template <typename T, int MAXH, int LZ>
 __global__ void __launch_bounds__(kThreadsPlane, sizeof(T) == 4 ? RISM_MINBLOCKS_F32 : 2)
 k_plane_fwd(Fields<T> f) {
     typedef typename Cx<T>::type C;
-    typedef typename Vec2<T>::type V2;
     const Ctrl *ctl = f.ctrl;
     if (ctl->status != kRunning) return;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -358,129 +647,100 @@ k_plane_fwd(Fields<T> f) {
     C *tw_h = buf + (long)f.slab_rows * pitch;    // after the block's rows
     C *tw_y = tw_h + Kz;
     C *tw_z = tw_y + Ny;
+    C *tw_q = tw_z + (Kz + 1);
+    const bool half = f.half;
     for (int i = threadIdx.x; i < Kz; i += blockDim.x) tw_h[i] = f.tw_h[i];
     for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw_y[i] = f.tw_y[i];
     for (int i = threadIdx.x; i <= Kz; i += blockDim.x) tw_z[i] = f.tw_z[i];
+    if (half)
+        for (int i = threadIdx.x; i < Kz; i += blockDim.x) tw_q[i] = f.tw_q[i];
 
     // block = (x plane, row chunk yc, site): rows y0 .. y0 + nyb of plane x
     const int nyc = f.nyc;
     const int x = blockIdx.x / nyc, yc = blockIdx.x - (blockIdx.x / nyc) * nyc, gam = blockIdx.y;
     const int y0 = yc * f.slab_rows, nyb = min(f.slab_rows, Ny - y0);
     const int stage = ctl->stage;
-    const int kind = ctl->stage_kind[stage], order = ctl->stage_order[stage];
-    const int cur = ctl->cur;
-    const int do_update = ctl->do_update;
-    const int upd_n = ctl->upd_n;
-    const T eta = (T)ctl->eta;
     const long long ring = (long long)f.nv * f.G;
     const long long siteoff = (long long)gam * f.G + (long long)x * Ny * f.Nz;
     __shared__ T coef[MAXH];
     __shared__ long long slot_off[MAXH];
+    FwdArgs<T, MAXH> A;
+    A.upd_n = ctl->upd_n;
     if (threadIdx.x < MAXH) {
         const int i = threadIdx.x;
-        coef[i] = i < upd_n ? (T)ctl->upd_coef[i] : (T)0;
-        slot_off[i] = i < upd_n ? (long long)ctl->upd_slot[i] * ring + siteoff : 0;
+        coef[i] = i < A.upd_n ? (T)ctl->upd_coef[i] : (T)0;
+        slot_off[i] = i < A.upd_n ? (long long)ctl->upd_slot[i] * ring + siteoff : 0;
     }
+    A.coef = coef;
+    A.slot_off = slot_off;
+    A.do_update = ctl->do_update;
+    A.kind = ctl->stage_kind[stage];
+    A.order = ctl->stage_order[stage];
+    A.anchor = ctl->anchor_valid;
+    A.refresh = ctl->refresh;
+    A.eta = (T)ctl->eta;
+    A.tcur = f.X + (long long)ctl->cur * ring + siteoff;
+    A.ca = f.csr_a + siteoff;
+    A.wp = f.w + siteoff;
+    A.pre = half ? tw_z : nullptr;
+    const C phx = half ? f.tw_xs[x] : cmk((T)1, (T)0);
     __syncthreads();
-    T *tcur = f.X + (long long)cur * ring + siteoff;
-    const T *wp = f.w + siteoff;
-    const int anchor = ctl->anchor_valid, refresh = ctl->refresh;
-    T *ca = f.csr_a + siteoff;
 
-    // update (Eq. 40) + closure + c^sr (Eq. 31), packed two reals per complex along z; two
-    // elements per thread and iteration with every load issued before any store
-    const int npairs = nyb * Kz;
-    const int step = 2 * blockDim.x;
-    for (int i0 = threadIdx.x; i0 < npairs; i0 += step) {
-        const int i1 = i0 + blockDim.x;
-        const bool has1 = i1 < npairs;
-        const int yA = i0 / Kz, mA = i0 - yA * Kz;
-        const int yB = has1 ? i1 / Kz : yA, mB = has1 ? i1 - yB * Kz : mA;
-        const long long oA = (long long)(y0 + yA) * f.Nz + 2 * mA;
-        const long long oB = (long long)(y0 + yB) * f.Nz + 2 * mB;
-        V2 tA, tB;
-        if (do_update) {
-            tA.x = tA.y = tB.x = tB.y = (T)0;
-#pragma unroll
-            for (int i = 0; i < MAXH; ++i) {
-                if (i < upd_n) {
-                    const T *xb = f.X + slot_off[i], *rb = f.R + slot_off[i];
-                    const V2 xa = ld2(xb + oA), ra = ld2(rb + oA);
-                    const V2 xv = ld2(xb + oB), rv = ld2(rb + oB);
-                    tA.x += coef[i] * (xa.x + eta * ra.x);
-                    tA.y += coef[i] * (xa.y + eta * ra.y);
-                    tB.x += coef[i] * (xv.x + eta * rv.x);
-                    tB.y += coef[i] * (xv.y + eta * rv.y);
-                }
-            }
-        } else {
-            tA = ld2(tcur + oA);
-            tB = ld2(tcur + oB);
+    if constexpr (LZ > 0) {
+        constexpr int RW = 256 / LZ;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int r0 = warp * RW; r0 < nyb; r0 += nw * RW) {
+            const int nr = min(RW, nyb - r0);
+            fwd_elements<T, MAXH>(f, A, buf, y0, r0 * LZ, (r0 + nr) * LZ, lane, 32);
+            __syncwarp();
+            fft_rows_warp<C, LZ>(buf + (long)r0 * pitch, nr, pitch, tw_h, -1, lane);
+            if (half)
+                r2c_rows_half(buf + (long)r0 * pitch, nr, y0 + r0, LZ, pitch, tw_q, f.tw_ys, phx, f.dKzp, lane, 32);
+            else
+                r2c_rows(buf + (long)r0 * pitch, nr, LZ, pitch, tw_z, f.dKz1h, lane, 32, nyc == 1);
+            __syncwarp();
         }
-        const V2 wA = ld2(wp + oA), wB = ld2(wp + oB);
-        V2 aA, aB;
-        if (anchor) {
-            aA = ld2(ca + oA);
-            aB = ld2(ca + oB);
-        }
-        V2 cA, cB;
-        cA.x = closure_g(wA.x + tA.x, kind, order) - (T)1 - tA.x;
-        cA.y = closure_g(wA.y + tA.y, kind, order) - (T)1 - tA.y;
-        cB.x = closure_g(wB.x + tB.x, kind, order) - (T)1 - tB.x;
-        cB.y = closure_g(wB.y + tB.y, kind, order) - (T)1 - tB.y;
-        C dA = cmk(cA.x, cA.y), dB = cmk(cB.x, cB.y);
-        if (anchor) {                          // transform only c^sr - c^sr_a
-            dA.x -= aA.x;
-            dA.y -= aA.y;
-            dB.x -= aB.x;
-            dB.y -= aB.y;
-        }
-        if (do_update) *reinterpret_cast<V2 *>(tcur + oA) = tA;
-        if (refresh) *reinterpret_cast<V2 *>(ca + oA) = cA;
-        buf[yA * pitch + mA] = dA;
-        if (has1) {
-            if (do_update) *reinterpret_cast<V2 *>(tcur + oB) = tB;
-            if (refresh) *reinterpret_cast<V2 *>(ca + oB) = cB;
-            buf[yB * pitch + mB] = dB;
-        }
+        __syncthreads();
+    } else {
+        fwd_elements<T, MAXH>(f, A, buf, y0, 0, nyb * Kz, threadIdx.x, blockDim.x);
+        __syncthreads();
+        fft_smem<C, MaxC<T>::v>(buf, f.ph, 1, nyb, pitch, f.chunk_rows, tw_h, -1);
+        if (half)
+            r2c_rows_half(buf, nyb, y0, Kz, pitch, tw_q, f.tw_ys, phx, f.dKzp, threadIdx.x, blockDim.x);
+        else
+            r2c_rows(buf, nyb, Kz, pitch, tw_z, f.dKz1h, threadIdx.x, blockDim.x, nyc == 1);
+        __syncthreads();
     }
-    __syncthreads();
-    // rows: complex FFT of length Kz
-    fft_smem<C, MaxC<T>::v>(buf, f.ph, 1, nyb, pitch, f.chunk_rows, tw_h, -1);
-    // real-to-complex post-processing: X[k] = E[k] + w^k O[k], k = 0..Kz
-    const int half = Kz / 2;
-    for (int idx = threadIdx.x; idx < nyb * (half + 1); idx += blockDim.x) {
-        const int y = idx / (half + 1), k = idx - y * (half + 1);
-        C *row = buf + y * pitch;
-        if (k == 0) {
-            C z = row[0];
-            row[0] = cmk(z.x + z.y, (T)0);
-            row[Kz] = cmk(z.x - z.y, (T)0);
-        } else {
-            const int k2 = Kz - k;
-            C a = row[k], b = row[k2];
-            C e1 = cscale(cadd(a, cconj(b)), (T)0.5);
-            C o1 = cscale(csub(a, cconj(b)), (T)0.5);
-            C X1 = cadd(e1, cmul(cmuli(o1, -1), tw_z[k]));
-            if (k2 != k) {
-                C e2 = cscale(cadd(b, cconj(a)), (T)0.5);
-                C o2 = cscale(csub(b, cconj(a)), (T)0.5);
-                row[k2] = cadd(e2, cmul(cmuli(o2, -1), tw_z[k2]));
-            }
-            row[k] = X1;
-        }
-    }
-    __syncthreads();
     // columns: complex FFT of length Ny for kz = 0..Kz (whole planes only; a split plane
-    // leaves the y transform to the y-pencil pass)
-    if (nyc == 1) fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz + 1, 1, f.chunk_cols_fwd, tw_y, -1);
+    // leaves the y transform to the y-pencil pass). The real columns kz = 0 and Kz travel
+    // as one complex column P = A + iB and are separated afterwards with the Hermitian
+    // symmetry of a real sequence's transform: A[k] = (P[k] + conj P[-k]) / 2,
+    // B[k] = -i (P[k] - conj P[-k]) / 2.
+    if (nyc == 1 && half) {
+        fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, -1);
+    } else if (nyc == 1) {
+        fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, -1);
+        for (int k = threadIdx.x; k <= Ny / 2; k += blockDim.x) {
+            const int k2 = k == 0 ? 0 : Ny - k;
+            const C P = buf[k * pitch], Q = buf[k2 * pitch];
+            buf[k * pitch] = cscale(cadd(P, cconj(Q)), (T)0.5);
+            buf[k * pitch + Kz] = cscale(cmuli(csub(P, cconj(Q)), -1), (T)0.5);
+            if (k2 != k) {
+                buf[k2 * pitch] = cscale(cadd(Q, cconj(P)), (T)0.5);
+                buf[k2 * pitch + Kz] = cscale(cmuli(csub(Q, cconj(P)), -1), (T)0.5);
+            }
+        }
+        __syncthreads();
+    }
     C *dst = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz + (long long)y0 * Kz;
     for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
-        const int y = idx / Kz, k = idx - y * Kz;
+        const int y = fdiv(idx, f.dKz), k = idx - y * Kz;
         dst[idx] = buf[y * pitch + k];
     }
-    C *dn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny + y0;
-    for (int y = threadIdx.x; y < nyb; y += blockDim.x) dn[y] = buf[y * pitch + Kz];
+    if (!half) {
+        C *dn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny + y0;
+        for (int y = threadIdx.x; y < nyb; y += blockDim.x) dn[y] = buf[y * pitch + Kz];
+    }
 }
 
 // ------------------------------------------------------------------ pass 2: pencil
@@ -520,12 +780,13 @@ k_pencil(Fields<T> f) {
     }
     const C *src_base = nyq ? f.spec_nyq : f.spec;
     const long long site_stride = (long long)Nx * xstride;
-    const int nload = NV * Nx * ncol;
+    // element loops run over whole tiles (W columns) and skip the columns past a ragged
+    // tile's end, so that the index split is a multiply by constants
+    const int nload = NV * Nx * W;
     for (int idx = threadIdx.x; idx < nload; idx += blockDim.x) {
-        const int c = idx % ncol;
-        const int rest = idx / ncol;
-        const int xx = rest % Nx, a = rest / Nx;
-        buf[(a * W + c) * pp + xx] = src_base[a * site_stride + xx * xstride + col_base + c];
+        const int rest = fdiv(idx, f.dW), c = idx - rest * W;
+        const int a = fdiv(rest, f.dNx), xx = rest - a * Nx;
+        if (c < ncol) buf[(a * W + c) * pp + xx] = src_base[a * site_stride + xx * xstride + col_base + c];
     }
     __syncthreads();
     fft_smem<C, MaxC<T>::v>(buf, f.px, 1, NV * W, pp, f.chunk_x, tw_x, -1);
@@ -533,16 +794,18 @@ k_pencil(Fields<T> f) {
     // first anchor, after which f~ is part of h_a]
     const C *psi = nyq ? f.psi_nyq : f.psi;
     const bool psi_on = f.ctrl->anchor_valid == 0;
-    const int npts = Nx * ncol;
+    const int npts = Nx * W;
     constexpr int rowlen = (NV + 1) * NV;
     const T ks0 = (T)f.ks[0], ks1 = (T)f.ks[1], ks2 = (T)f.ks[2], inv_dk = (T)f.inv_dk;
+    const T hs = f.half ? (T)0.5 : (T)0;
     for (int idx = threadIdx.x; idx < npts; idx += blockDim.x) {
-        const int c = idx % ncol, xx = idx / ncol;
+        const int xx = fdiv(idx, f.dW), c = idx - xx * W;
+        if (c >= ncol) continue;
         const int yy = nyq ? y0 + c : y;
         const int kz = nyq ? Kz : kz0 + c;
-        const T kx = ks0 * (T)signed_index(xx, Nx);
-        const T ky = ks1 * (T)signed_index(yy, Ny);
-        const T kzv = ks2 * (T)kz;
+        const T kx = ks0 * ((T)signed_index(xx, Nx) + hs);   // hs = 1/2 on the half grid
+        const T ky = ks1 * ((T)signed_index(yy, Ny) + hs);
+        const T kzv = ks2 * ((T)kz + hs);
         const T xk = sqrt(kx * kx + ky * ky + kzv * kzv) * inv_dk;
         int j = (int)floor(xk);
         if (j > f.nk - 2) j = f.nk - 2;
@@ -575,10 +838,9 @@ k_pencil(Fields<T> f) {
     fft_smem<C, MaxC<T>::v>(buf, f.px, 1, NV * W, pp, f.chunk_x, tw_x, +1);
     C *dst_base = nyq ? f.spec_nyq : f.spec;
     for (int idx = threadIdx.x; idx < nload; idx += blockDim.x) {
-        const int c = idx % ncol;
-        const int rest = idx / ncol;
-        const int xx = rest % Nx, a = rest / Nx;
-        dst_base[a * site_stride + xx * xstride + col_base + c] = buf[(a * W + c) * pp + xx];
+        const int rest = fdiv(idx, f.dW), c = idx - rest * W;
+        const int a = fdiv(rest, f.dNx), xx = rest - a * Nx;
+        if (c < ncol) dst_base[a * site_stride + xx * xstride + col_base + c] = buf[(a * W + c) * pp + xx];
     }
 }
 
@@ -621,120 +883,74 @@ k_ypencil(Fields<T> f, int sign) {
         base = f.spec_nyq;
     }
     C *gbase = const_cast<C *>(base);
-    const int nload = nv * Ny * ncol;
+    const int nload = nv * Ny * W;
     for (int idx = threadIdx.x; idx < nload; idx += blockDim.x) {
-        const int c = idx % ncol;
-        const int rest = idx / ncol;
-        const int y = rest % Ny, a = rest / Ny;
-        buf[(a * W + c) * pp + y] = gbase[a * site_stride + col_base + c * col_stride + y * ystride];
+        const int rest = fdiv(idx, f.dWy), c = idx - rest * W;
+        const int a = fdiv(rest, f.dNy), y = rest - a * Ny;
+        if (c < ncol) buf[(a * W + c) * pp + y] = gbase[a * site_stride + col_base + c * col_stride + y * ystride];
     }
     __syncthreads();
     fft_smem<C, MaxC<T>::v>(buf, f.py, 1, nv * W, pp, f.chunk_y, tw_y, sign);
     for (int idx = threadIdx.x; idx < nload; idx += blockDim.x) {
-        const int c = idx % ncol;
-        const int rest = idx / ncol;
-        const int y = rest % Ny, a = rest / Ny;
-        gbase[a * site_stride + col_base + c * col_stride + y * ystride] = buf[(a * W + c) * pp + y];
+        const int rest = fdiv(idx, f.dWy), c = idx - rest * W;
+        const int a = fdiv(rest, f.dNy), y = rest - a * Ny;
+        if (c < ncol) gbase[a * site_stride + col_base + c * col_stride + y * ystride] = buf[(a * W + c) * pp + y];
     }
 }
 
 // ------------------------------------------------------------------ pass 3: plane_inv
-// One block per (x plane, site): inverse y and z transforms, residual, and the block's
-// contribution to <R_cur, R_i> and sum R^2 (Dot2 accumulation, FP64 across threads).
-// Partials are stored value-major: partials[i * n_blocks + block].
+// Per-launch values of the residual pass.
+template <typename T>
+struct InvArgs {
+    const long long *hoff;       // [MAXH] ring offsets of the stored residuals (shared memory)
+    int hist_n, kind, order, anchor, refresh;
+    const T *tcur, *wp;
+    T *rcur, *ha;
+    const typename Cx<T>::type *post;   // half grid: conj of exp(-i pi p / Kz) applies, else null
+};
+
+// Residual R = h + 1 - g (Eq. 33) of the elements e in [e0, e1) of the block's rows, stored
+// into the ring, and the thread's Gram sums <R, R_i> (acc[i + 1]) and sum R^2 (acc[0]).
 template <typename T, int MAXH>
-__global__ void __launch_bounds__(kThreadsPlane, sizeof(T) == 4 ? RISM_MINBLOCKS_F32 : 2)
-k_plane_inv(Fields<T> f) {
+__device__ __forceinline__ void inv_elements(const Fields<T> &f, const InvArgs<T> &A,
+                                             const typename Cx<T>::type *buf, int y0, int e0, int e1,
+                                             int tid, int nthr, GramAcc<T> (&acc)[MAXH + 1]) {
     typedef typename Cx<T>::type C;
     typedef typename Vec2<T>::type V2;
-    const Ctrl *ctl = f.ctrl;
-    if (ctl->status != kRunning) return;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C *buf = reinterpret_cast<C *>(smraw);
-    const int Ny = f.Ny, Kz = f.Kz, pitch = f.pitch;
-    C *tw_h = buf + (long)f.slab_rows * pitch;    // after the block's rows
-    C *tw_y = tw_h + Kz;
-    C *tw_z = tw_y + Ny;
-    double *red = reinterpret_cast<double *>(tw_z + (Kz + 1));
-    for (int i = threadIdx.x; i < Kz; i += blockDim.x) tw_h[i] = f.tw_h[i];
-    for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw_y[i] = f.tw_y[i];
-    for (int i = threadIdx.x; i <= Kz; i += blockDim.x) tw_z[i] = f.tw_z[i];
-    const int nyc = f.nyc;
-    const int x = blockIdx.x / nyc, yc = blockIdx.x - (blockIdx.x / nyc) * nyc, gam = blockIdx.y;
-    const int y0 = yc * f.slab_rows, nyb = min(f.slab_rows, Ny - y0);
-
-    const C *src = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz + (long long)y0 * Kz;
-    for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
-        const int y = idx / Kz, k = idx - y * Kz;
-        buf[y * pitch + k] = src[idx];
-    }
-    const C *sn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny + y0;
-    for (int y = threadIdx.x; y < nyb; y += blockDim.x) buf[y * pitch + Kz] = sn[y];
-    __syncthreads();
-    if (nyc == 1) fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz + 1, 1, f.chunk_cols_fwd, tw_y, +1);
-    // complex-to-real pre-processing: Z[k] = (X[k] + conj X[Kz-k]) + i w^-k (X[k] - conj X[Kz-k])
-    const int half = Kz / 2;
-    for (int idx = threadIdx.x; idx < nyb * (half + 1); idx += blockDim.x) {
-        const int y = idx / (half + 1), k = idx - y * (half + 1);
-        C *row = buf + y * pitch;
-        const int k2 = Kz - k;
-        C a = row[k], b = row[k2];
-        C Z1 = cadd(cadd(a, cconj(b)), cmuli(cmul(csub(a, cconj(b)), cconj(tw_z[k])), +1));
-        if (k != 0 && k2 != k)
-            row[k2] = cadd(cadd(b, cconj(a)), cmuli(cmul(csub(b, cconj(a)), cconj(tw_z[k2])), +1));
-        row[k] = Z1;
-    }
-    __syncthreads();
-    fft_smem<C, MaxC<T>::v>(buf, f.ph, 1, nyb, pitch, f.chunk_rows, tw_h, +1);
-
-    const int stage = ctl->stage;
-    const int kind = ctl->stage_kind[stage], order = ctl->stage_order[stage];
-    const int cur = ctl->cur;
-    const int hist_n = ctl->hist_n;
-    const long long ring = (long long)f.nv * f.G;
-    const long long siteoff = (long long)gam * f.G + (long long)x * Ny * f.Nz;
-    const T *tcur = f.X + (long long)cur * ring + siteoff;
-    T *rcur = f.R + (long long)cur * ring + siteoff;
-    const T *wp = f.w + siteoff;
-    const int anchor = ctl->anchor_valid, refresh = ctl->refresh;
-    T *ha = f.h_a + siteoff;
-    __shared__ long long hoff[MAXH];
-    if (threadIdx.x < MAXH) hoff[threadIdx.x] = threadIdx.x < hist_n ? (long long)ctl->hist_slot[threadIdx.x] * ring + siteoff : 0;
-    __syncthreads();
-    GramAcc<T> acc[MAXH + 1];
-#pragma unroll
-    for (int i = 0; i <= MAXH; ++i) acc[i].zero();
-    const int nel = nyb * Kz;
-    const int step = 2 * blockDim.x;
-    for (int i0 = threadIdx.x; i0 < nel; i0 += step) {
-        const int i1 = i0 + blockDim.x;
-        const bool has1 = i1 < nel;
-        const int yA = i0 / Kz, mA = i0 - yA * Kz;
-        const int yB = has1 ? i1 / Kz : yA, mB = has1 ? i1 - yB * Kz : mA;
+    const int Kz = f.Kz, pitch = f.pitch;
+    for (int i0 = e0 + tid; i0 < e1; i0 += 2 * nthr) {
+        const int i1 = i0 + nthr;
+        const bool has1 = i1 < e1;
+        const int yA = fdiv(i0, f.dKz), mA = i0 - yA * Kz;
+        const int yB = has1 ? fdiv(i1, f.dKz) : yA, mB = has1 ? i1 - yB * Kz : mA;
         const long long oA = (long long)(y0 + yA) * f.Nz + 2 * mA;
         const long long oB = (long long)(y0 + yB) * f.Nz + 2 * mB;
         // loads of both elements first: t, w, anchor, history residuals
-        const V2 tA = ld2(tcur + oA), tB = ld2(tcur + oB);
-        const V2 wA = ld2(wp + oA), wB = ld2(wp + oB);
+        const V2 tA = ld2(A.tcur + oA), tB = ld2(A.tcur + oB);
+        const V2 wA = ld2(A.wp + oA), wB = ld2(A.wp + oB);
         V2 aA, aB;
-        if (anchor) {
-            aA = ld2(ha + oA);
-            aB = ld2(ha + oB);
+        if (A.anchor) {
+            aA = ld2(A.ha + oA);
+            aB = ld2(A.ha + oB);
         }
         V2 qA[MAXH], qB[MAXH];
 #pragma unroll
         for (int i = 0; i < MAXH; ++i)
-            if (i < hist_n) {
-                qA[i] = ld2(f.R + hoff[i] + oA);
-                qB[i] = ld2(f.R + hoff[i] + oB);
+            if (i < A.hist_n) {
+                qA[i] = ld2(f.R + A.hoff[i] + oA);
+                qB[i] = ld2(f.R + A.hoff[i] + oB);
             }
-        const C hcA = buf[yA * pitch + mA], hcB = buf[yB * pitch + mB];
-        const T gA0 = closure_g(wA.x + tA.x, kind, order), gA1 = closure_g(wA.y + tA.y, kind, order);
-        const T gB0 = closure_g(wB.x + tB.x, kind, order), gB1 = closure_g(wB.y + tB.y, kind, order);
+        C hcA = buf[yA * pitch + mA], hcB = buf[yB * pitch + mB];
+        if (A.post) {                          // half grid: undo the z shift
+            hcA = cmul(hcA, cconj(A.post[mA]));
+            hcB = cmul(hcB, cconj(A.post[mB]));
+        }
+        const T gA0 = closure_g(wA.x + tA.x, A.kind, A.order), gA1 = closure_g(wA.y + tA.y, A.kind, A.order);
+        const T gB0 = closure_g(wB.x + tB.x, A.kind, A.order), gB1 = closure_g(wB.y + tB.y, A.kind, A.order);
         // R = h + 1 - g (Eq. 33) with h = h_a + dh; (h_a - g) first: near association peaks
         // both are large and close, and the difference is then exact
         V2 rA, rB, hA, hB;
-        if (anchor) {
+        if (A.anchor) {
             rA.x = ((aA.x - gA0) + (T)1) + hcA.x;
             rA.y = ((aA.y - gA1) + (T)1) + hcA.y;
             rB.x = ((aB.x - gB0) + (T)1) + hcB.x;
@@ -757,37 +973,134 @@ k_plane_inv(Fields<T> f) {
         acc[0].add(rA.y, rA.y);
 #pragma unroll
         for (int i = 0; i < MAXH; ++i)
-            if (i < hist_n) {
+            if (i < A.hist_n) {
                 acc[i + 1].add(rA.x, qA[i].x);
                 acc[i + 1].add(rA.y, qA[i].y);
             }
-        if (refresh) *reinterpret_cast<V2 *>(ha + oA) = hA;
-        *reinterpret_cast<V2 *>(rcur + oA) = rA;
+        if (A.refresh) *reinterpret_cast<V2 *>(A.ha + oA) = hA;
+        *reinterpret_cast<V2 *>(A.rcur + oA) = rA;
         if (has1) {
             acc[0].add(rB.x, rB.x);
             acc[0].add(rB.y, rB.y);
 #pragma unroll
             for (int i = 0; i < MAXH; ++i)
-                if (i < hist_n) {
+                if (i < A.hist_n) {
                     acc[i + 1].add(rB.x, qB[i].x);
                     acc[i + 1].add(rB.y, qB[i].y);
                 }
-            if (refresh) *reinterpret_cast<V2 *>(ha + oB) = hB;
-            *reinterpret_cast<V2 *>(rcur + oB) = rB;
+            if (A.refresh) *reinterpret_cast<V2 *>(A.ha + oB) = hB;
+            *reinterpret_cast<V2 *>(A.rcur + oB) = rB;
         }
+    }
+}
+
+// One block per (x plane or row chunk of one, site): inverse y and z transforms, residual,
+// and the block's contribution to <R_cur, R_i> and sum R^2 (Dot2 accumulation, FP64 across
+// threads). Partials are stored value-major: partials[i * n_blocks + block]. With LZ > 0
+// (as for plane_fwd) each warp takes its own rows through the complex-to-real step, the z
+// transform and the residual after the block-wide y transform.
+template <typename T, int MAXH, int LZ>
+__global__ void __launch_bounds__(kThreadsPlane, sizeof(T) == 4 ? RISM_MINBLOCKS_F32 : 2)
+k_plane_inv(Fields<T> f) {
+    typedef typename Cx<T>::type C;
+    const Ctrl *ctl = f.ctrl;
+    if (ctl->status != kRunning) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *buf = reinterpret_cast<C *>(smraw);
+    const int Ny = f.Ny, Kz = f.Kz, pitch = f.pitch;
+    C *tw_h = buf + (long)f.slab_rows * pitch;    // after the block's rows
+    C *tw_y = tw_h + Kz;
+    C *tw_z = tw_y + Ny;
+    C *tw_q = tw_z + (Kz + 1);
+    double *red = reinterpret_cast<double *>(tw_q + Kz);
+    const bool half = f.half;
+    for (int i = threadIdx.x; i < Kz; i += blockDim.x) tw_h[i] = f.tw_h[i];
+    for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw_y[i] = f.tw_y[i];
+    for (int i = threadIdx.x; i <= Kz; i += blockDim.x) tw_z[i] = f.tw_z[i];
+    if (half)
+        for (int i = threadIdx.x; i < Kz; i += blockDim.x) tw_q[i] = f.tw_q[i];
+    const int nyc = f.nyc;
+    const int x = blockIdx.x / nyc, yc = blockIdx.x - (blockIdx.x / nyc) * nyc, gam = blockIdx.y;
+    const int y0 = yc * f.slab_rows, nyb = min(f.slab_rows, Ny - y0);
+    const long long ring = (long long)f.nv * f.G;
+    const long long siteoff = (long long)gam * f.G + (long long)x * Ny * f.Nz;
+    __shared__ long long hoff[MAXH];
+    InvArgs<T> A;
+    A.hist_n = ctl->hist_n;
+    if (threadIdx.x < MAXH)
+        hoff[threadIdx.x] = threadIdx.x < A.hist_n ? (long long)ctl->hist_slot[threadIdx.x] * ring + siteoff : 0;
+    const int stage = ctl->stage;
+    A.hoff = hoff;
+    A.kind = ctl->stage_kind[stage];
+    A.order = ctl->stage_order[stage];
+    A.anchor = ctl->anchor_valid;
+    A.refresh = ctl->refresh;
+    A.tcur = f.X + (long long)ctl->cur * ring + siteoff;
+    A.rcur = f.R + (long long)ctl->cur * ring + siteoff;
+    A.wp = f.w + siteoff;
+    A.ha = f.h_a + siteoff;
+    A.post = half ? tw_z : nullptr;
+    const C phx = half ? f.tw_xs[x] : cmk((T)1, (T)0);
+
+    const C *src = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz + (long long)y0 * Kz;
+    for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
+        const int y = fdiv(idx, f.dKz), k = idx - y * Kz;
+        buf[y * pitch + k] = src[idx];
+    }
+    if (!half) {
+        const C *sn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny + y0;
+        for (int y = threadIdx.x; y < nyb; y += blockDim.x) buf[y * pitch + Kz] = sn[y];
+    }
+    __syncthreads();
+    if (nyc == 1 && half) {
+        fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, +1);
+    } else if (nyc == 1) {
+        // columns kz = 0 and Kz (transforms of real sequences) as one: P = A + iB
+        for (int y = threadIdx.x; y < Ny; y += blockDim.x) {
+            const C A0 = buf[y * pitch], B0 = buf[y * pitch + Kz];
+            buf[y * pitch] = cmk(A0.x - B0.y, A0.y + B0.x);
+        }
+        __syncthreads();
+        fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, +1);
+    }
+
+    GramAcc<T> acc[MAXH + 1];
+#pragma unroll
+    for (int i = 0; i <= MAXH; ++i) acc[i].zero();
+    if constexpr (LZ > 0) {
+        constexpr int RW = 256 / LZ;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int r0 = warp * RW; r0 < nyb; r0 += nw * RW) {
+            const int nr = min(RW, nyb - r0);
+            if (half)
+                c2r_rows_half(buf + (long)r0 * pitch, nr, y0 + r0, LZ, pitch, tw_q, f.tw_ys, phx, f.dKzp, lane, 32);
+            else
+                c2r_rows(buf + (long)r0 * pitch, nr, LZ, pitch, tw_z, f.dKz1h, lane, 32, nyc == 1);
+            __syncwarp();
+            fft_rows_warp<C, LZ>(buf + (long)r0 * pitch, nr, pitch, tw_h, +1, lane);
+            inv_elements<T, MAXH>(f, A, buf, y0, r0 * LZ, (r0 + nr) * LZ, lane, 32, acc);
+        }
+    } else {
+        if (half)
+            c2r_rows_half(buf, nyb, y0, Kz, pitch, tw_q, f.tw_ys, phx, f.dKzp, threadIdx.x, blockDim.x);
+        else
+            c2r_rows(buf, nyb, Kz, pitch, tw_z, f.dKz1h, threadIdx.x, blockDim.x, nyc == 1);
+        __syncthreads();
+        fft_smem<C, MaxC<T>::v>(buf, f.ph, 1, nyb, pitch, f.chunk_rows, tw_h, +1);
+        inv_elements<T, MAXH>(f, A, buf, y0, 0, nyb * Kz, threadIdx.x, blockDim.x, acc);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const long long nblocks = (long long)f.nv * f.Nx * nyc;
     const long long blk = ((long long)gam * f.Nx + x) * nyc + yc;
 #pragma unroll
     for (int i = 0; i <= MAXH; ++i) {
-        if (i <= hist_n) {
+        if (i <= A.hist_n) {
             acc[i].warp_reduce();
             if (lane == 0) red[i * nw + warp] = acc[i].value();
         }
     }
     __syncthreads();
-    if (threadIdx.x <= hist_n) {
+    if (threadIdx.x <= A.hist_n) {
         double s = 0.0;
         for (int k = 0; k < nw; ++k) s += red[threadIdx.x * nw + k];
         f.partials[threadIdx.x * nblocks + blk] = s;
@@ -814,7 +1127,7 @@ struct MdiisScratch {
 // Bookkeeping before the coefficient solve (thread 0): byte counters, RMS, convergence and
 // closure stages, the Gram row of the new residual, and the candidate history H (oldest
 // first). mode: 0 = nothing more to do, 1 = MDIIS bordered solve, 2 = modified Anderson.
-__device__ void mdiis_pre(Ctrl *ctl, const double *sums, MdiisScratch &sc) {
+static __device__ void mdiis_pre(Ctrl *ctl, const double *sums, MdiisScratch &sc) {
     const int hist_n = ctl->hist_n;
     sc.mode = 0;
     ctl->acc_iters += 1;
@@ -875,7 +1188,7 @@ __device__ void mdiis_pre(Ctrl *ctl, const double *sums, MdiisScratch &sc) {
 // Modified Anderson coefficients (Eqs. 34-39, two histories): theta from the 2 x 2 system
 // of Eq. 36 on D_i = R_new - R_{new-i}, a_i = theta_i + s_i; Picard while fewer than three
 // pairs are stored or if the system is singular.
-__device__ void anderson_coef(const Ctrl *ctl, MdiisScratch &sc) {
+static __device__ void anderson_coef(const Ctrl *ctl, MdiisScratch &sc) {
     const int k = sc.k;
     for (int i = 0; i < k; ++i) sc.c[i] = 0.0;
     sc.c[k - 1] = 1.0;
@@ -923,7 +1236,7 @@ __device__ void anderson_coef(const Ctrl *ctl, MdiisScratch &sc) {
 // MDIIS coefficients by one warp: lane j owns column j of [B / max diag, 1; 1^T, 0 | rhs];
 // Gaussian elimination with partial pivoting (pivot search by shuffles, one reciprocal per
 // pivot); a pivot below 1e-12 drops the oldest vector and retries.
-__device__ void mdiis_coef_warp(const Ctrl *ctl, MdiisScratch &sc, int lane) {
+static __device__ void mdiis_coef_warp(const Ctrl *ctl, MdiisScratch &sc, int lane) {
     for (;;) {
         const int n = sc.k - sc.first;
         if (n == 1) {
@@ -996,7 +1309,7 @@ __device__ void mdiis_coef_warp(const Ctrl *ctl, MdiisScratch &sc, int lane) {
 
 // After the solve (thread 0): damping, the update list and the ring slot of the next
 // iterate (a free slot while the history is short, else the oldest, which leaves it).
-__device__ void mdiis_post(Ctrl *ctl, MdiisScratch &sc) {
+static __device__ void mdiis_post(Ctrl *ctl, MdiisScratch &sc) {
     const int M = ctl->M;
     const int n = sc.k - sc.first;
     const int *H = sc.H + sc.first;
@@ -1025,7 +1338,7 @@ __device__ void mdiis_post(Ctrl *ctl, MdiisScratch &sc) {
     ctl->do_update = 1;
 }
 
-__global__ void k_mdiis(Ctrl *ctl_g, const double *partials, int nblocks) {
+static __global__ void k_mdiis(Ctrl *ctl_g, const double *partials, int nblocks) {
     __shared__ double sums[kMaxHist + 1];
     __shared__ Ctrl ctl_s;
     __shared__ MdiisScratch sc;
@@ -1224,7 +1537,7 @@ __global__ void k_phase_tables(Fields<T> f, const double *atoms, int a0, int na,
             u = at[8];
         }
         double sn, cs;
-        sincospi(2.0 * m * u, &sn, &cs);
+        sincospi(2.0 * (m + (f.half ? 0.5 : 0.0)) * u, &sn, &cs);
         C v;
         v.x = (T)cs;
         v.y = (T)(-sn);
@@ -1241,7 +1554,7 @@ k_longrange(Fields<T> f, const double *atoms, int a0, int na, const typename Cx<
     for (int i = threadIdx.x; i < na; i += blockDim.x) qs[i] = (T)atoms[(long long)(a0 + i) * kAtomStride + 3];
     __syncthreads();
     const long long nmain = (long long)f.Nx * f.Ny * f.Kz;
-    const long long total = nmain + (long long)f.Nx * f.Ny;
+    const long long total = nmain + (f.half ? 0 : (long long)f.Nx * f.Ny);
     const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= total) return;
     int ix, iy, iz;
@@ -1257,9 +1570,11 @@ k_longrange(Fields<T> f, const double *atoms, int a0, int na, const typename Cx<
         iz = f.Kz;
     }
     const int mx = signed_index(ix, f.Nx), my = signed_index(iy, f.Ny), mz = iz;
-    const bool nyq = ((f.Nx % 2 == 0) && 2 * abs(mx) == f.Nx) ||
-                     ((f.Ny % 2 == 0) && 2 * abs(my) == f.Ny) || (2 * mz == f.Nz);
-    const double kx = f.ks[0] * mx, ky = f.ks[1] * my, kz = f.ks[2] * mz;
+    // integer grid: zero at k = 0 and on Nyquist planes; the half grid has neither
+    const bool nyq = !f.half && (((f.Nx % 2 == 0) && 2 * abs(mx) == f.Nx) ||
+                                 ((f.Ny % 2 == 0) && 2 * abs(my) == f.Ny) || (2 * mz == f.Nz));
+    const double hs = f.half ? 0.5 : 0.0;
+    const double kx = f.ks[0] * (mx + hs), ky = f.ks[1] * (my + hs), kz = f.ks[2] * (mz + hs);
     const double k2 = kx * kx + ky * ky + kz * kz;
     double re = 0.0, im = 0.0;
     if (!nyq && k2 > 0.0) {
@@ -1497,7 +1812,7 @@ k_sfe_gradient(Fields<T> f, const double *atoms, int n_atoms, const double *site
     }
 }
 
-__global__ void k_sum_rows(const double *partials, int rows, int cols, double *out) {
+static __global__ void k_sum_rows(const double *partials, int rows, int cols, double *out) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int c = 0; c < cols; ++c) s += partials[(long long)r * cols + c];
@@ -1524,7 +1839,7 @@ cudaError_t launch_sfe_gradient(const Fields<T> &f, int slot, int kind, int orde
 // ------------------------------------------------------------------ launchers
 template <typename T> size_t plane_smem_bytes(const Fields<T> &f) {
     typedef typename Cx<T>::type C;
-    return sizeof(C) * ((size_t)f.slab_rows * f.pitch + f.Kz + f.Ny + f.Kz + 1) +
+    return sizeof(C) * ((size_t)f.slab_rows * f.pitch + f.Kz + f.Ny + f.Kz + 1 + f.Kz) +
            (kMaxHist + 1) * (kThreadsPlane / 32) * sizeof(double) + 16;
 }
 template <typename T> size_t pencil_smem_bytes(const Fields<T> &f) {
@@ -1536,20 +1851,49 @@ template <typename T> size_t ypencil_smem_bytes(const Fields<T> &f) {
     return sizeof(C) * ((size_t)f.nv * f.Wy * f.ypitch + f.Ny);
 }
 
+// The dynamic shared memory cap is a property of the kernel function, shared by every
+// context in the process: each kernel gets the device's opt-in maximum (occupancy follows
+// the amount a launch asks for, not the cap), so contexts of different grid sizes coexist.
+// The size check of a context is on its own needs against that maximum.
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const size_t cap = (size_t)optin - fa.sharedSizeBytes;   // less the kernel's static arrays
+    if (bytes > cap) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+}
+
+// z-row length classes with a specialised plane kernel (FP32 only; FP64 and other lengths
+// take the block-wide form)
+template <typename T> int plane_lz(const Fields<T> &f) {
+    if (sizeof(T) != 4) return 0;
+    return (f.Kz == 64 || f.Kz == 128) ? f.Kz : 0;
+}
+
+template <typename T, int LZ> cudaError_t prepare_planes(size_t pl) {
+    cudaError_t e = set_smem(k_plane_fwd<T, 5, LZ>, pl);
+    if (e == cudaSuccess) e = set_smem(k_plane_fwd<T, 8, LZ>, pl);
+    if (e == cudaSuccess) e = set_smem(k_plane_fwd<T, kMaxHist, LZ>, pl);
+    if (e == cudaSuccess) e = set_smem(k_plane_inv<T, 4, LZ>, pl);
+    if (e == cudaSuccess) e = set_smem(k_plane_inv<T, 8, LZ>, pl);
+    if (e == cudaSuccess) e = set_smem(k_plane_inv<T, kMaxHist, LZ>, pl);
+    return e;
 }
 
 template <typename T> cudaError_t prepare_kernels(const Fields<T> &f) {
     const size_t pl = plane_smem_bytes(f), pe = pencil_smem_bytes(f);
-    cudaError_t e = set_smem(k_plane_fwd<T, 5>, pl);
-    if (e == cudaSuccess) e = set_smem(k_plane_inv<T, 4>, pl);
-    if (e == cudaSuccess) e = set_smem(k_plane_fwd<T, 8>, pl);
-    if (e == cudaSuccess) e = set_smem(k_plane_fwd<T, kMaxHist>, pl);
-    if (e == cudaSuccess) e = set_smem(k_plane_inv<T, 8>, pl);
-    if (e == cudaSuccess) e = set_smem(k_plane_inv<T, kMaxHist>, pl);
-    if (e == cudaSuccess && f.nyc > 1) e = set_smem(k_ypencil<T>, ypencil_smem_bytes(f));
+    cudaError_t e;
+    switch (plane_lz(f)) {
+        case 64: e = prepare_planes<T, sizeof(T) == 4 ? 64 : 0>(pl); break;
+        case 128: e = prepare_planes<T, sizeof(T) == 4 ? 128 : 0>(pl); break;
+        default: e = prepare_planes<T, 0>(pl); break;
+    }
+    if (e == cudaSuccess) e = set_smem(k_ypencil<T>, f.nyc > 1 ? ypencil_smem_bytes(f) : 0);
     if (e != cudaSuccess) return e;
     switch (f.nv) {
         case 1: return set_smem(k_pencil<T, 1>, pe);
@@ -1568,28 +1912,42 @@ template <typename T> cudaError_t launch_ypencil(const Fields<T> &f, int sign, c
     k_ypencil<T><<<f.ytiles_main + f.ytiles_nyq, kThreadsPencil, ypencil_smem_bytes(f), s>>>(f, sign);
     return cudaGetLastError();
 }
+template <typename T, int LZ> void plane_fwd_lz(const Fields<T> &f, dim3 grid, size_t sm, cudaStream_t s) {
+    // the update combines up to M stored pairs
+    if (f.M <= 5)
+        k_plane_fwd<T, 5, LZ><<<grid, kThreadsPlane, sm, s>>>(f);
+    else if (f.M <= 8)
+        k_plane_fwd<T, 8, LZ><<<grid, kThreadsPlane, sm, s>>>(f);
+    else
+        k_plane_fwd<T, kMaxHist, LZ><<<grid, kThreadsPlane, sm, s>>>(f);
+}
+template <typename T, int LZ> void plane_inv_lz(const Fields<T> &f, dim3 grid, size_t sm, cudaStream_t s) {
+    // the Gram row pairs the new residual with at most M - 1 stored ones
+    if (f.M <= 5)
+        k_plane_inv<T, 4, LZ><<<grid, kThreadsPlane, sm, s>>>(f);
+    else if (f.M <= 8)
+        k_plane_inv<T, 8, LZ><<<grid, kThreadsPlane, sm, s>>>(f);
+    else
+        k_plane_inv<T, kMaxHist, LZ><<<grid, kThreadsPlane, sm, s>>>(f);
+}
 template <typename T> cudaError_t launch_plane_fwd(const Fields<T> &f, cudaStream_t s) {
     const size_t sm = plane_smem_bytes(f);
     const dim3 grid(f.Nx * f.nyc, f.nv);
-    // the update combines up to M stored pairs
-    if (f.M <= 5)
-        k_plane_fwd<T, 5><<<grid, kThreadsPlane, sm, s>>>(f);
-    else if (f.M <= 8)
-        k_plane_fwd<T, 8><<<grid, kThreadsPlane, sm, s>>>(f);
-    else
-        k_plane_fwd<T, kMaxHist><<<grid, kThreadsPlane, sm, s>>>(f);
+    switch (plane_lz(f)) {
+        case 64: plane_fwd_lz<T, sizeof(T) == 4 ? 64 : 0>(f, grid, sm, s); break;
+        case 128: plane_fwd_lz<T, sizeof(T) == 4 ? 128 : 0>(f, grid, sm, s); break;
+        default: plane_fwd_lz<T, 0>(f, grid, sm, s); break;
+    }
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_plane_inv(const Fields<T> &f, cudaStream_t s) {
     const size_t sm = plane_smem_bytes(f);
     const dim3 grid(f.Nx * f.nyc, f.nv);
-    // the Gram row pairs the new residual with at most M - 1 stored ones
-    if (f.M <= 5)
-        k_plane_inv<T, 4><<<grid, kThreadsPlane, sm, s>>>(f);
-    else if (f.M <= 8)
-        k_plane_inv<T, 8><<<grid, kThreadsPlane, sm, s>>>(f);
-    else
-        k_plane_inv<T, kMaxHist><<<grid, kThreadsPlane, sm, s>>>(f);
+    switch (plane_lz(f)) {
+        case 64: plane_inv_lz<T, sizeof(T) == 4 ? 64 : 0>(f, grid, sm, s); break;
+        case 128: plane_inv_lz<T, sizeof(T) == 4 ? 128 : 0>(f, grid, sm, s); break;
+        default: plane_inv_lz<T, 0>(f, grid, sm, s); break;
+    }
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_pencil(const Fields<T> &f, cudaStream_t s) {
@@ -1683,8 +2041,5 @@ cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sf
                                                 const double *, int, const double *,           \
                                                 const double *, const double *, const double *, \
                                                 const double *, double *, double *, cudaStream_t);
-
-RISM_INSTANTIATE(float)
-RISM_INSTANTIATE(double)
 
 }  // namespace rism

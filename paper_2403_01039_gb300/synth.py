@@ -99,6 +99,35 @@ WORKLOADS = {
 }
 
 
+def smooth_even(n):
+    """Smallest m >= n that is even with m / 2 free of prime factors above 5 (the grid sizes
+    the transform passes take)."""
+    m = int(n) + (int(n) & 1)
+    while True:
+        k = m // 2
+        for p in (2, 3, 5):
+            while k % p == 0:
+                k //= p
+        if k == 1:
+            return m
+        m += 2
+
+
+def batch_workload(count=64, seed0=4000, spacing=0.5):
+    """Many small solutes on uneven grids: for seed s = seed0 .. seed0 + count - 1, draw with
+    PCG64(s) the atom count n ~ U{20..120} and the grid size N ~ U{64..128} rounded up by
+    smooth_even; the solute is random_solute(n, 10 (n/50)^(1/3), s), net charge 0; 3-site
+    water, spacing 0.5 A. Returns a list of dict(seed, grid, solute)."""
+    out = []
+    for s in range(seed0, seed0 + count):
+        rng = np.random.Generator(np.random.PCG64(s))
+        n_atoms = int(rng.integers(20, 121))
+        N = smooth_even(int(rng.integers(64, 129)))
+        sol = random_solute(n_atoms, 10.0 * (n_atoms / 50.0) ** (1.0 / 3.0), s)
+        out.append(dict(seed=s, grid=cubic_grid(N, spacing), solute=sol))
+    return out
+
+
 def solvent_sites(name):
     return water_3site() if name == "water3" else water_nacl_5site()
 
