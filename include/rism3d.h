@@ -99,7 +99,9 @@ typedef struct {
     int check_every;          /* iterations per CUDA-graph launch between status polls */
     int max_atoms;            /* capacity for rism3d_set_solute */
     int timing;               /* 1: record CUDA events around every kernel of the solve so
-                                 rism3d_get_stats reports measured per-kernel device time */
+                                 rism3d_get_stats reports measured per-kernel device time;
+                                 2: the same for the first iteration of each check_every
+                                 chunk only (a sample with less recording overhead) */
     int accelerator;          /* 0: MDIIS (Eq. 40, mdiis_nvec vectors); 1: the modified
                                  Anderson method with two histories (Eqs. 34-39; Picard for
                                  the first two steps; mdiis_damp is its mixing b) */
@@ -199,6 +201,17 @@ rism3d_status rism3d_get(rism3d_ctx *ctx, int field, double *dst, size_t count, 
  * FP64. per_site ([n_sites], host) may be NULL. */
 rism3d_status rism3d_get_sfe(rism3d_ctx *ctx, int kind, int pse_order, double *total,
                              double *per_site);
+
+/* Learned initial guess (next row of the method; the paper starts every solve from t = f):
+ * crops of side `crop` at grid index corner[3] (inside the grid), FP32 device arrays
+ * [n_sites][crop][crop][crop], for the network of unet3d.h. */
+/* Network input: tanh(beta u_g / 4) on the crop (after rism3d_set_solute). */
+rism3d_status rism3d_guess_input(rism3d_ctx *ctx, const int *corner, int crop, float *x);
+/* Training target: the current iterate tau = t - f on the crop (after a solve). */
+rism3d_status rism3d_guess_target(rism3d_ctx *ctx, const int *corner, int crop, float *tau);
+/* Start the next rism3d_solve from tau = the given values on the crop and 0 elsewhere
+ * (step 1 otherwise uses tau = 0, i.e. t = f). */
+rism3d_status rism3d_set_guess_crop(rism3d_ctx *ctx, const int *corner, int crop, const float *tau);
 
 /* One job of rism3d_solve_batch. Inputs: ctx (a context of its own; the grid may differ from
  * job to job; jobs run concurrently when their contexts have different streams and in turn

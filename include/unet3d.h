@@ -1,0 +1,76 @@
+/*
+ * unet3d.h - the 3D U-Net of the learned initial guess for the 3D-RISM solve.
+ *
+ * The paper has no learned component: it starts every solve from t = f (step 1 of the
+ * "Numerical procedure" section). This network predicts the starting iterate
+ * tau = t - f on a cubic crop around the solute from the potential beta*u on that crop,
+ * so that the fixed-point iteration starts closer to its solution; the solve itself is
+ * unchanged (its result is the same fixed point). rism3d.h has the entry points that
+ * cut the network's input out of a solver context and put its output back as the guess.
+ *
+ * Architecture (channels c0, c1, c2; crop side n divisible by 4):
+ *   enc1 = relu(conv(relu(conv(x))))                              [c0, n^3]
+ *   enc2 = relu(conv(relu(conv(pool(enc1)))))                      [c1, (n/2)^3]
+ *   mid  = relu(conv(relu(conv(pool(enc2)))))                      [c2, (n/4)^3]
+ *   dec2 = relu(conv(relu(conv([up(mid), enc2]))))                 [c1, (n/2)^3]
+ *   dec1 = relu(conv(relu(conv([up(dec2), enc1]))))                [c0, n^3]
+ *   y    = conv1x1(dec1)                                           [n_out, n^3]
+ * conv: 3x3x3, zero padding, bias; pool: 2x2x2 mean; up: nearest x2; [a, b]: channel
+ * concatenation. Parameters are one flat FP32 vector, layer by layer, each layer's weights
+ * ([out][in][3][3][3], or [out][in] for the last) followed by its biases.
+ *
+ * Arithmetic: FP32 with FP32 accumulation (direct convolutions over shared-memory tiles).
+ * Every array argument is device memory of the current CUDA device unless stated; every
+ * call returns 0 on success, else a nonzero code with a message in unet3d_last_error().
+ * Calls enqueue on the network's stream and return without synchronising unless stated.
+ */
+#ifndef UNET3D_PUBLIC_API_H_
+#define UNET3D_PUBLIC_API_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct unet3d unet3d;
+
+/* Allocates parameters, gradients, Adam moments and the activations of one crop.
+ * n_in, n_out >= 1; crop >= 4 and divisible by 4; channels >= 1. stream: cudaStream_t or
+ * NULL (the legacy default stream). Returns 1 on bad arguments, 2 on allocation failure. */
+int unet3d_create(int n_in, int n_out, int crop, int c0, int c1, int c2, void *stream, unet3d **out);
+
+/* Number of FP32 parameters (weights and biases of all layers). */
+size_t unet3d_param_count(const unet3d *net);
+
+/* Copy the flat parameter vector in or out (host memory; synchronous). */
+int unet3d_set_params(unet3d *net, const float *host_params);
+int unet3d_get_params(const unet3d *net, float *host_params);
+
+/* y [n_out][crop^3] = network(x [n_in][crop^3]); keeps the activations for backward. */
+int unet3d_forward(unet3d *net, const float *x, float *y);
+
+/* Parameter gradient of a loss with dL/dy = gy [n_out][crop^3] at the last forward's
+ * input, written into the network's gradient vector (overwritten, not accumulated). */
+int unet3d_backward(unet3d *net, const float *gy);
+
+/* Copy the gradient vector to host memory (synchronous). */
+int unet3d_get_grads(const unet3d *net, float *host_grads);
+
+/* Mean squared error of y against target (count values): loss to host (synchronous,
+ * FP64 sum in a fixed order) and gy = 2 (y - target) / count on the device. */
+int unet3d_mse(unet3d *net, const float *y, const float *target, size_t count, double *loss, float *gy);
+
+/* One Adam step on the parameters with the current gradient: step t >= 1, moments with
+ * decay beta1, beta2, bias-corrected; p -= lr m^ / (sqrt(v^) + eps). */
+int unet3d_adam(unet3d *net, float lr, float beta1, float beta2, float eps, int t);
+
+const char *unet3d_last_error(void);
+
+void unet3d_destroy(unet3d *net);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UNET3D_PUBLIC_API_H_ */

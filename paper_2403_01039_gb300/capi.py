@@ -94,6 +94,20 @@ def load():
         "rism3d_get": (c_int, [c_void_p, c_int, c_void_p, c_size_t, c_int]),
         "rism3d_get_sfe": (c_int, [c_void_p, c_int, c_int, P(c_double), _dp]),
         "rism3d_solve_batch": (c_int, [P(BatchJob), c_int, c_int, c_double]),
+        "rism3d_guess_input": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
+        "rism3d_guess_target": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
+        "rism3d_set_guess_crop": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
+        "unet3d_create": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, c_void_p, P(c_void_p)]),
+        "unet3d_param_count": (c_size_t, [c_void_p]),
+        "unet3d_set_params": (c_int, [c_void_p, P(ctypes.c_float)]),
+        "unet3d_get_params": (c_int, [c_void_p, P(ctypes.c_float)]),
+        "unet3d_forward": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "unet3d_backward": (c_int, [c_void_p, c_void_p]),
+        "unet3d_get_grads": (c_int, [c_void_p, P(ctypes.c_float)]),
+        "unet3d_mse": (c_int, [c_void_p, c_void_p, c_void_p, c_size_t, P(c_double), c_void_p]),
+        "unet3d_adam": (c_int, [c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, c_int]),
+        "unet3d_last_error": (ctypes.c_char_p, []),
+        "unet3d_destroy": (None, [c_void_p]),
         "rism3d_get_pmv": (c_int, [c_void_p, c_double, P(c_double), _dp]),
         "rism3d_get_sfe_gradient": (c_int, [c_void_p, _dp]),
         "rism3d_get_stats": (c_int, [c_void_p, P(Stats)]),
@@ -293,7 +307,7 @@ class Solver:
         o.max_iter = max_iter
         o.check_every = check_every
         o.max_atoms = max_atoms
-        o.timing = int(bool(timing))
+        o.timing = 2 if timing == "sampled" else int(bool(timing))
         o.accelerator = {"mdiis": 0, "anderson": 1}[accelerator]
         o.anderson_s1, o.anderson_s2 = float(anderson_s[0]), float(anderson_s[1])
         o.slab_rows = int(slab_rows)
@@ -403,6 +417,26 @@ class Solver:
                                                            ctypes.byref(tot), per.ctypes.data_as(_dp)))
         return tot.value, per
 
+    def _corner(self, corner):
+        return (ctypes.c_int * 3)(*[int(v) for v in corner])
+
+    def guess_input(self, corner, crop, out):
+        """Network input tanh(beta u / 4) on the crop into ``out`` (float32 CUDA tensor
+        [n_sites, crop, crop, crop])."""
+        _check(self.lib, self.ctx, self.lib.rism3d_guess_input(self.ctx, self._corner(corner), int(crop),
+                                                               ctypes.c_void_p(out.data_ptr())))
+
+    def guess_target(self, corner, crop, out):
+        """The current iterate tau = t - f on the crop into ``out`` (float32 CUDA tensor)."""
+        _check(self.lib, self.ctx, self.lib.rism3d_guess_target(self.ctx, self._corner(corner), int(crop),
+                                                                ctypes.c_void_p(out.data_ptr())))
+
+    def set_guess_crop(self, corner, crop, tau):
+        """Start the next solve from tau on the crop (float32 CUDA tensor) and 0 elsewhere."""
+        self._sync_torch()
+        _check(self.lib, self.ctx, self.lib.rism3d_set_guess_crop(self.ctx, self._corner(corner), int(crop),
+                                                                  ctypes.c_void_p(tau.data_ptr())))
+
     def pmv(self, kT_chi_T):
         """Partial molar volume (Eq. 19, A^3) and the per-site c integrals of the current
         iterate, given the solvent's k_B T chi_T (A^3)."""
@@ -446,3 +480,84 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class UNet3D:
+    """The learned-guess network of ``unet3d.h`` (device kernels of the library); tensors
+    are float32 CUDA tensors, parameters a flat float32 numpy vector."""
+
+    def __init__(self, n_in, n_out, crop, channels=(16, 32, 64), stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load()
+        self.n_in, self.n_out, self.crop = n_in, n_out, crop
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        net = ctypes.c_void_p()
+        st = self.lib.unet3d_create(n_in, n_out, crop, channels[0], channels[1], channels[2],
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(net))
+        if st != 0:
+            raise RuntimeError("unet3d_create: " + self.lib.unet3d_last_error().decode())
+        self.net = net
+        self.n_params = int(self.lib.unet3d_param_count(net))
+
+    def _ok(self, st):
+        if st != 0:
+            raise RuntimeError("unet3d: " + self.lib.unet3d_last_error().decode())
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.n_params
+        self._ok(self.lib.unet3d_set_params(self.net, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def get_params(self):
+        a = np.empty(self.n_params, dtype=np.float32)
+        self._ok(self.lib.unet3d_get_params(self.net, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return a
+
+    def get_grads(self):
+        a = np.empty(self.n_params, dtype=np.float32)
+        self._ok(self.lib.unet3d_get_grads(self.net, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return a
+
+    def forward(self, x, y):
+        self._ok(self.lib.unet3d_forward(self.net, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr())))
+
+    def backward(self, gy):
+        self._ok(self.lib.unet3d_backward(self.net, ctypes.c_void_p(gy.data_ptr())))
+
+    def mse(self, y, target, gy):
+        loss = ctypes.c_double()
+        self._ok(self.lib.unet3d_mse(self.net, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                     y.numel(), ctypes.byref(loss), ctypes.c_void_p(gy.data_ptr())))
+        return loss.value
+
+    def adam(self, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._ok(self.lib.unet3d_adam(self.net, float(lr), float(beta1), float(beta2), float(eps), int(t)))
+
+    def close(self):
+        if getattr(self, "net", None):
+            self.lib.unet3d_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def flatten_params(params):
+    """Oracle-layout parameters [[w, b], ...] to the library's flat float32 vector."""
+    return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in params]).astype(np.float32)
+
+
+def unflatten(flat, like):
+    """Flat vector back to the oracle layout of ``like``."""
+    out, o = [], 0
+    for w, b in like:
+        gw = flat[o:o + w.size].reshape(w.shape)
+        o += w.size
+        gb = flat[o:o + b.size]
+        o += b.size
+        out.append([gw, gb])
+    return out

@@ -255,6 +255,7 @@ rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, cons
         return fail(nullptr, RISM3D_EINVAL, "mdiis_damp must be in (0, 2]");
     if (op->slab_rows < 0) return fail(nullptr, RISM3D_EINVAL, "slab_rows must be >= 0");
     if (op->kgrid != 0 && op->kgrid != 1) return fail(nullptr, RISM3D_EINVAL, "kgrid must be 0 or 1");
+    if (op->timing < 0 || op->timing > 2) return fail(nullptr, RISM3D_EINVAL, "timing must be 0, 1 or 2");
     if (op->accelerator != 0 && op->accelerator != 1)
         return fail(nullptr, RISM3D_EINVAL, "accelerator must be 0 (MDIIS) or 1 (modified Anderson)");
     if (op->max_iter < 1 || op->check_every < 1 || op->max_atoms < 1)
@@ -594,7 +595,9 @@ rism3d_status build_graph(rism3d_ctx *ctx) {
     CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     rism3d_status st = RISM3D_OK;
     for (int i = 0; i < K && st == RISM3D_OK; ++i) {
-        if (ctx->opt.timing)
+        // timing 1: every iteration of the graph; 2: its first iteration only
+        const bool timed = ctx->opt.timing == 1 || (ctx->opt.timing == 2 && i == 0);
+        if (timed)
             st = ctx->fp32() ? timed_iteration<float>(ctx, ctx->f32, &ctx->ev[(size_t)i * kEventsPerIter])
                              : timed_iteration<double>(ctx, ctx->f64, &ctx->ev[(size_t)i * kEventsPerIter]);
         else
@@ -921,7 +924,8 @@ static rism3d_status solve_chunk_done(rism3d_ctx *ctx, bool *running) {
     const int nk = iteration_slots(ctx, true, slots);
     for (int k = 0; k < nk; ++k) ctx->stats.launches[slots[k]] += K;
     if (ctx->opt.timing) {
-        for (int i = 0; i < ran && i < K; ++i)
+        const int timed_its = ctx->opt.timing == 2 ? 1 : K;
+        for (int i = 0; i < ran && i < timed_its; ++i)
             for (int k = 0; k < nk; ++k) {
                 float ms = 0.f;
                 const size_t e0 = (size_t)i * kEventsPerIter + k;
@@ -1135,6 +1139,38 @@ rism3d_status rism3d_get_sfe(rism3d_ctx *ctx, int kind, int pse_order, double *t
     }
     *total = tot;
     return RISM3D_OK;
+}
+
+static rism3d_status guess_crop(rism3d_ctx *ctx, int mode, const int *corner, int crop, float *out,
+                                const float *in) {
+    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+    if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "learned-guess crop before set_solute");
+    if (!corner || crop < 1 || (mode == 2 ? !in : !out)) return fail(ctx, RISM3D_EINVAL, "bad crop arguments");
+    const int N[3] = {ctx->Nx, ctx->Ny, ctx->Nz};
+    for (int d = 0; d < 3; ++d)
+        if (corner[d] < 0 || corner[d] + crop > N[d])
+            return fail(ctx, RISM3D_EINVAL, "crop [%d, %d) outside the grid on axis %d", corner[d], corner[d] + crop, d);
+    DeviceGuard dg(ctx->device);
+    const int slot = mode == 2 ? 0 : ctx->cur_slot;
+    if (ctx->fp32())
+        CUDA_TRY(ctx, launch_guess_crop<float>(ctx->f32, mode, slot, corner, crop, out, in, ctx->stream));
+    else
+        CUDA_TRY(ctx, launch_guess_crop<double>(ctx->f64, mode, slot, corner, crop, out, in, ctx->stream));
+    if (mode == 2) ctx->cur_slot = 0;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return RISM3D_OK;
+}
+
+rism3d_status rism3d_guess_input(rism3d_ctx *ctx, const int *corner, int crop, float *x) {
+    return guess_crop(ctx, 0, corner, crop, x, nullptr);
+}
+
+rism3d_status rism3d_guess_target(rism3d_ctx *ctx, const int *corner, int crop, float *tau) {
+    return guess_crop(ctx, 1, corner, crop, tau, nullptr);
+}
+
+rism3d_status rism3d_set_guess_crop(rism3d_ctx *ctx, const int *corner, int crop, const float *tau) {
+    return guess_crop(ctx, 2, corner, crop, nullptr, tau);
 }
 
 rism3d_status rism3d_get_pmv(rism3d_ctx *ctx, double kT_chi_T, double *pmv, double *c_integral) {

@@ -12,6 +12,7 @@ constexpr int kMaxRadixStages = 10;
 constexpr int kMaxClosureStages = 12;
 constexpr int kThreadsPlane = 256;
 constexpr int kThreadsPencil = 256;
+constexpr int kThreadsMdiis = 32 * (kMaxHist + 1);   // at least one warp per Gram value
 
 // Solver status words written by the device (Ctrl::status).
 enum { kRunning = 0, kConverged = 1, kDiverged = 2, kMaxIter = 3, kStopped = 4 };
@@ -169,6 +170,11 @@ void set_global_error(const char *msg);
 
 // d(SFE)/dR of every atom (second Eq. 21); rho_dV[g] = rho_g dV (device); partials needs
 // n_atoms * 3 * kGradBlocks doubles; out receives [n_atoms][3] (device).
+// Learned-guess crops: mode 0 network input, 1 iterate of `slot` (both to out), 2 iterate of
+// `slot` from `in` (zero outside the crop).
+template <typename T>
+cudaError_t launch_guess_crop(const Fields<T> &f, int mode, int slot, const int *corner, int n, float *out,
+                              const float *in, cudaStream_t s);
 template <typename T>
 cudaError_t launch_sfe_gradient(const Fields<T> &f, int slot, int kind, int order, const double *rho_dV,
                                 const double *atoms, int n_atoms, const double *site_sig,

@@ -1235,9 +1235,11 @@ static __device__ void anderson_coef(const Ctrl *ctl, MdiisScratch &sc) {
 
 // MDIIS coefficients by one warp: lane j owns column j of [B / max diag, 1; 1^T, 0 | rhs];
 // Gaussian elimination with partial pivoting (pivot search by shuffles, one reciprocal per
-// pivot); a pivot below 1e-12 drops the oldest vector and retries.
+// pivot); a pivot below 1e-12 drops the oldest vector and retries. Every branch decision is
+// lane 0's (broadcast), a NaN entry counts as a zero pivot, and there are at most k
+// attempts, so the warp stays converged and the loop ends whatever the Gram entries are.
 static __device__ void mdiis_coef_warp(const Ctrl *ctl, MdiisScratch &sc, int lane) {
-    for (;;) {
+    for (int attempt = 0; attempt < kMaxHist + 1; ++attempt) {
         const int n = sc.k - sc.first;
         if (n == 1) {
             if (lane == 0) sc.c[0] = 1.0;
@@ -1262,6 +1264,7 @@ static __device__ void mdiis_coef_warp(const Ctrl *ctl, MdiisScratch &sc, int la
         bool ok = true;
         for (int col = 0; col < dim; ++col) {
             double v = (lane >= col && lane < dim) ? fabs(sc.A[lane][col]) : -1.0;
+            if (!(v == v)) v = 0.0;                          // NaN: no usable pivot
             int p = lane;
             for (int o = 16; o > 0; o >>= 1) {
                 const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
@@ -1271,7 +1274,9 @@ static __device__ void mdiis_coef_warp(const Ctrl *ctl, MdiisScratch &sc, int la
                     p = p2;
                 }
             }
-            if (v < 1e-12) {
+            v = __shfl_sync(0xffffffffu, v, 0);             // one decision for the warp
+            p = __shfl_sync(0xffffffffu, p, 0);
+            if (!(v >= 1e-12)) {
                 ok = false;
                 break;
             }
@@ -1305,6 +1310,11 @@ static __device__ void mdiis_coef_warp(const Ctrl *ctl, MdiisScratch &sc, int la
         if (lane == 0) sc.first += 1;
         __syncwarp();
     }
+    if (lane == 0) {                          // not reached for valid input: keep the newest
+        sc.first = sc.k - 1;
+        sc.c[0] = 1.0;
+    }
+    __syncwarp();
 }
 
 // After the solve (thread 0): damping, the update list and the ring slot of the next
@@ -1340,34 +1350,45 @@ static __device__ void mdiis_post(Ctrl *ctl, MdiisScratch &sc) {
 
 static __global__ void k_mdiis(Ctrl *ctl_g, const double *partials, int nblocks) {
     __shared__ double sums[kMaxHist + 1];
+    __shared__ double part[kMaxHist + 1][kThreadsMdiis / 32];
     __shared__ Ctrl ctl_s;
     __shared__ MdiisScratch sc;
     if (ctl_g->status != kRunning) return;
-    {
+    const int hist_n = ctl_g->hist_n;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    {   // the control block to shared memory, while the partial sums are being loaded
         const int n = (int)(sizeof(Ctrl) / sizeof(int));
         const int *src = reinterpret_cast<const int *>(ctl_g);
         int *dst = reinterpret_cast<int *>(&ctl_s);
         for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
     }
-    __syncthreads();
-    Ctrl *ctl = &ctl_s;
-    const int hist_n = ctl->hist_n;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp <= hist_n) {
-        const double *pv = partials + (long long)warp * nblocks;
+    // value v = <R_cur, R_v-1> (v > 0) or sum R^2 (v = 0): wpv warps per value, each summing
+    // a fixed stride of block partials; the warps' sums are then added in a fixed order
+    const int nval = hist_n + 1, wpv = nw / nval;
+    const int v = warp / wpv, sub = warp - v * wpv;
+    if (v < nval) {
+        const double *pv = partials + (long long)v * nblocks;
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int b = lane;
-        for (; b + 96 < nblocks; b += 128) {
+        const int st = 32 * wpv;
+        int b = sub * 32 + lane;
+        for (; b + 3 * st < nblocks; b += 4 * st) {
             s0 += pv[b];
-            s1 += pv[b + 32];
-            s2 += pv[b + 64];
-            s3 += pv[b + 96];
+            s1 += pv[b + st];
+            s2 += pv[b + 2 * st];
+            s3 += pv[b + 3 * st];
         }
-        for (; b < nblocks; b += 32) s0 += pv[b];
+        for (; b < nblocks; b += st) s0 += pv[b];
         double s = (s0 + s1) + (s2 + s3);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) sums[warp] = s;
+        if (lane == 0) part[v][sub] = s;
     }
+    __syncthreads();
+    if (threadIdx.x < nval) {
+        double s = 0.0;
+        for (int k = 0; k < wpv; ++k) s += part[threadIdx.x][k];
+        sums[threadIdx.x] = s;
+    }
+    Ctrl *ctl = &ctl_s;
     __syncthreads();
     if (warp == 0) {
         if (lane == 0) mdiis_pre(ctl, sums, sc);
@@ -1602,6 +1623,61 @@ k_longrange(Fields<T> f, const double *atoms, int a0, int na, const typename Cx<
         v.y += o.y;
     }
     *dst = v;
+}
+
+// ------------------------------------------------------------------ learned guess crops
+// Crop of side n at grid index (i0, j0, k0) (inside the grid), FP32 [nv][n^3]:
+// mode 0: network input tanh(beta u / 4); mode 1: the iterate tau of `slot`.
+template <typename T>
+__global__ void k_guess_crop_out(Fields<T> f, int mode, int slot, int i0, int j0, int k0, int n, float *out) {
+    const long long V = (long long)n * n * n, total = (long long)f.nv * V;
+    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < total;
+         id += (long long)gridDim.x * blockDim.x) {
+        long long r = id;
+        const int k = (int)(r % n);
+        r /= n;
+        const int j = (int)(r % n);
+        r /= n;
+        const int i = (int)(r % n);
+        const int g = (int)(r / n);
+        const long long src = (long long)g * f.G + ((long long)(i0 + i) * f.Ny + (j0 + j)) * f.Nz + (k0 + k);
+        if (mode == 0)
+            out[id] = tanhf((float)f.bu[src] * 0.25f);
+        else
+            out[id] = (float)f.X[(long long)slot * f.nv * f.G + src];
+    }
+}
+
+// The iterate of `slot` (whole field): tau = crop values inside the crop, 0 outside.
+template <typename T>
+__global__ void k_guess_crop_in(Fields<T> f, int slot, int i0, int j0, int k0, int n, const float *in) {
+    const long long total = (long long)f.nv * f.G;
+    T *dst = f.X + (long long)slot * total;
+    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < total;
+         id += (long long)gridDim.x * blockDim.x) {
+        long long r = id;
+        const int k = (int)(r % f.Nz);
+        r /= f.Nz;
+        const int j = (int)(r % f.Ny);
+        r /= f.Ny;
+        const int i = (int)(r % f.Nx);
+        const int g = (int)(r / f.Nx);
+        const int ci = i - i0, cj = j - j0, ck = k - k0;
+        T v = (T)0;
+        if (ci >= 0 && ci < n && cj >= 0 && cj < n && ck >= 0 && ck < n)
+            v = (T)in[(((long long)g * n + ci) * n + cj) * n + ck];
+        dst[id] = v;
+    }
+}
+
+template <typename T>
+cudaError_t launch_guess_crop(const Fields<T> &f, int mode, int slot, const int *corner, int n, float *out,
+                              const float *in, cudaStream_t s) {
+    if (mode == 2)
+        k_guess_crop_in<T><<<152 * 8, 256, 0, s>>>(f, slot, corner[0], corner[1], corner[2], n, in);
+    else
+        k_guess_crop_out<T><<<152 * 8, 256, 0, s>>>(f, mode, slot, corner[0], corner[1], corner[2], n, out);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ small helpers
@@ -1967,7 +2043,7 @@ template <typename T> cudaError_t launch_pencil(const Fields<T> &f, cudaStream_t
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_mdiis(const Fields<T> &f, cudaStream_t s) {
-    k_mdiis<<<1, 32 * (kMaxHist + 1), 0, s>>>(f.ctrl, f.partials, f.nv * f.Nx * f.nyc);
+    k_mdiis<<<1, kThreadsMdiis, 0, s>>>(f.ctrl, f.partials, f.nv * f.Nx * f.nyc);
     return cudaGetLastError();
 }
 template <typename T>
@@ -2040,6 +2116,8 @@ cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sf
     template cudaError_t launch_sfe_gradient<T>(const Fields<T> &, int, int, int, const double *, \
                                                 const double *, int, const double *,           \
                                                 const double *, const double *, const double *, \
-                                                const double *, double *, double *, cudaStream_t);
+                                                const double *, double *, double *, cudaStream_t);    \
+    template cudaError_t launch_guess_crop<T>(const Fields<T> &, int, int, const int *, int, float *,  \
+                                              const float *, cudaStream_t);
 
 }  // namespace rism

@@ -1,0 +1,170 @@
+"""Learned initial guess for the 3D-RISM solve: data from the solver, training of the
+unet3d network, and its use as the starting iterate.
+
+The network maps tanh(beta u / 4) on a cubic crop around the solute (all solvent sites as
+channels) to the converged iterate tau = t - f on that crop; the solve then starts from the
+prediction inside the crop and tau = 0 (t = f, step 1 of the numerical procedure) outside.
+Every numerical step runs in the library's kernels (crops, network, loss, optimiser);
+this module only orchestrates them.
+
+  python -m paper_2403_01039_gb300.guess --train 2000 --test 200 --epochs 6 --out weights.npz
+
+Workload: solutes of the solute50_128 kind (50 atoms in a 10 A sphere, sigma ~ U(2.5, 3.8),
+eps ~ U(0.05, 0.2), q ~ N(0, 0.3) shifted to net 0) with seeds 50000.. (training) and
+60000.. (test), water + 0.1 M NaCl, 128^3 at 0.5 A, KH, tol 1e-6, FP32, 64^3 crops at the
+grid centre.
+"""
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+from . import capi, synth
+
+CROP = 64
+CHANNELS = (16, 32, 64)
+TRAIN_SEED0, TEST_SEED0 = 50000, 60000
+
+
+def _solvent():
+    sites = synth.water_nacl_5site()
+    chi, dk, _, _ = capi.xrism(sites)
+    return dict(sites, chi=chi, dk=dk)
+
+
+def _solute(seed):
+    return synth.random_solute(50, 10.0, seed, net_charge=0.0)
+
+
+def corner(n, crop=CROP):
+    c = (n - crop) // 2
+    return (c, c, c)
+
+
+def make_data(S, seeds, tol=1e-6, crop=CROP):
+    """Inputs and converged targets on the crop for each seed (float32 CUDA tensors
+    [count, n_sites, crop, crop, crop]) and the zero-guess iteration counts."""
+    import torch
+    nv, n = S.n_sites, S.n[0]
+    X = torch.empty((len(seeds), nv, crop, crop, crop), dtype=torch.float32, device="cuda")
+    Y = torch.empty_like(X)
+    its = []
+    c = corner(n, crop)
+    for i, s in enumerate(seeds):
+        sol = _solute(s)
+        S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+        S.guess_input(c, crop, X[i])
+        its.append(S.solve("kh", tol=tol)["iterations"])
+        S.guess_target(c, crop, Y[i])
+    return X, Y, its
+
+
+def train(net, X, Y, epochs, lr=1e-3, seed=0, log=None):
+    """Adam on the mean squared error, one crop per step, shuffled each epoch."""
+    import torch
+    rng = np.random.default_rng(seed)
+    y = torch.empty_like(Y[0])
+    gy = torch.empty_like(Y[0])
+    step = 0
+    history = []
+    for ep in range(epochs):
+        order = rng.permutation(len(X))
+        tot = 0.0
+        for i in order:
+            net.forward(X[i], y)
+            tot += net.mse(y, Y[i], gy)
+            net.backward(gy)
+            step += 1
+            net.adam(lr * (0.5 ** (ep // 2)), step)
+        history.append(tot / len(X))
+        if log:
+            log("epoch %d: mse %.4e" % (ep, history[-1]))
+    return history
+
+
+def evaluate(S, net, seeds, tol=1e-6, crop=CROP):
+    """Iterations and wall time of each test solve from the zero guess and from the
+    network's guess (set_solute + [network] + solve)."""
+    import torch
+    nv, n = S.n_sites, S.n[0]
+    c = corner(n, crop)
+    x = torch.empty((nv, crop, crop, crop), dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    out = dict(zero_iters=[], guess_iters=[], zero_s=[], guess_s=[])
+    for s in seeds:
+        sol = _solute(s)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+        r0 = S.solve("kh", tol=tol)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+        S.guess_input(c, crop, x)
+        net.forward(x, y)
+        S.set_guess_crop(c, crop, y)
+        r1 = S.solve("kh", tol=tol)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        out["zero_iters"].append(r0["iterations"])
+        out["guess_iters"].append(r1["iterations"])
+        out["zero_s"].append(t1 - t0)
+        out["guess_s"].append(t2 - t1)
+    return out
+
+
+def main():
+    import torch
+    p = argparse.ArgumentParser()
+    p.add_argument("--train", type=int, default=2000)
+    p.add_argument("--test", type=int, default=200)
+    p.add_argument("--epochs", type=int, default=6)
+    p.add_argument("--lr", type=float, default=1e-3)
+    p.add_argument("--out", default="guess_unet.npz")
+    p.add_argument("--json", default=None)
+    a = p.parse_args()
+    torch.cuda.set_device(0)
+    solv = _solvent()
+    S = capi.Solver(solv, synth.cubic_grid(128, 0.5), precision=32, mdiis_nvec=5)
+    t0 = time.perf_counter()
+    X, Y, its = make_data(S, [TRAIN_SEED0 + i for i in range(a.train)])
+    t_data = time.perf_counter() - t0
+    print("data: %d solves in %.1f s, mean %.1f iterations" % (a.train, t_data, np.mean(its)), flush=True)
+    net = capi.UNet3D(len(solv["q"]), len(solv["q"]), CROP, CHANNELS)
+    net.set_params(init_flat(len(solv["q"]), len(solv["q"]), seed=1))
+    t0 = time.perf_counter()
+    hist = train(net, X, Y, a.epochs, a.lr, log=lambda m: print(m, flush=True))
+    t_train = time.perf_counter() - t0
+    np.savez_compressed(a.out, params=net.get_params(), crop=CROP, channels=np.array(CHANNELS), history=np.array(hist))
+    ev = evaluate(S, net, [TEST_SEED0 + i for i in range(a.test)])
+    res = dict(train=a.train, test=a.test, epochs=a.epochs, data_s=t_data, train_s=t_train, mse=hist,
+               zero_iters_mean=float(np.mean(ev["zero_iters"])), guess_iters_mean=float(np.mean(ev["guess_iters"])),
+               zero_solves_per_s=len(ev["zero_s"]) / float(np.sum(ev["zero_s"])),
+               guess_solves_per_s=len(ev["guess_s"]) / float(np.sum(ev["guess_s"])))
+    print(json.dumps(res), flush=True)
+    if a.json:
+        with open(a.json, "w") as f:
+            json.dump(dict(res, **{k: v for k, v in ev.items()}), f)
+    net.close()
+    S.close()
+
+
+def init_flat(n_in, n_out, seed, channels=CHANNELS, crop=CROP):
+    """He-normal initial weights and zero biases in the library's flat layout (PCG64(seed))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c0, c1, c2 = channels
+    shapes = [(c0, n_in), (c0, c0), (c1, c0), (c1, c1), (c2, c1), (c2, c2), (c1, c2 + c1), (c1, c1),
+              (c0, c1 + c0), (c0, c0)]
+    parts = []
+    for co, ci in shapes:
+        parts.append((rng.standard_normal(co * ci * 27) * np.sqrt(2.0 / (27 * ci))).astype(np.float32))
+        parts.append(np.zeros(co, dtype=np.float32))
+    parts.append((rng.standard_normal(n_out * c0) * np.sqrt(1.0 / c0)).astype(np.float32))
+    parts.append(np.zeros(n_out, dtype=np.float32))
+    return np.concatenate(parts)
+
+
+if __name__ == "__main__":
+    main()
