@@ -384,6 +384,12 @@ def run_batch(args):
     solv = dict(sites, chi=chi, dk=dk)
     work = synth.batch_workload()
     solvers = [capi.Solver(solv, w["grid"], precision=args.precision, mdiis_nvec=5) for w in work]
+    # pencil tiles autotuned per grid, once per context (before timing)
+    tuned = []
+    for S, w in zip(solvers, work):
+        sol = w["solute"]
+        S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+        tuned.append(S.tune()[0])
 
     def one_at_a_time():
         its = 0
@@ -428,7 +434,8 @@ def run_batch(args):
                 data="synthetic",
                 config=dict(workload="batch64", jobs=len(work), grids="64-128 cubic (2,3,5 sizes) x 0.5 A",
                             sites=len(sites["q"]), atoms="20-120", closure="kh", tol=args.tol, mdiis=5,
-                            inflight=args.inflight, parallelism="single"),
+                            inflight=args.inflight, parallelism="single",
+                            pencil_widths={str(k): tuned.count(k) for k in sorted(set(tuned))}),
                 one_at_a_time=dict(value=n / t_seq, unit="solves/s", iterations=it_seq),
                 batched_iterations=it_bat,
                 site_gridpoint_iters_per_s=sum(spi[-args.steps:]) / t_bat,

@@ -260,6 +260,15 @@ rism3d_status rism3d_get_pmv(rism3d_ctx *ctx, double kT_chi_T, double *pmv, doub
  * the long-range split (Eqs. 29-30) on the atom positions. */
 rism3d_status rism3d_get_sfe_gradient(rism3d_ctx *ctx, double *grad);
 
+/* Autotune the transform tiles of this context by measurement: the x-pencil pass (x
+ * transforms, contraction of Eq. 13, inverse x transforms) is timed on the context's own
+ * buffers for every tile width W = 1, 2, 4, ... columns that fits in shared memory, and the
+ * fastest W is kept for later solves (results do not depend on W). Call after
+ * rism3d_set_solute and outside a solve; it overwrites the spectrum buffer (no state a
+ * later solve needs). pencil_width and pencil_ms (time of one pass at the chosen W) may be
+ * NULL. No counterpart in the paper. */
+rism3d_status rism3d_tune(rism3d_ctx *ctx, int *pencil_width, double *pencil_ms);
+
 /* Copy the counters; timing fields are zero unless the context was created with timing = 1. */
 rism3d_status rism3d_get_stats(const rism3d_ctx *ctx, rism3d_stats *out);
 

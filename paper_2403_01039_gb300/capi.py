@@ -94,6 +94,7 @@ def load():
         "rism3d_get": (c_int, [c_void_p, c_int, c_void_p, c_size_t, c_int]),
         "rism3d_get_sfe": (c_int, [c_void_p, c_int, c_int, P(c_double), _dp]),
         "rism3d_solve_batch": (c_int, [P(BatchJob), c_int, c_int, c_double]),
+        "rism3d_tune": (c_int, [c_void_p, P(c_int), P(c_double)]),
         "rism3d_guess_input": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
         "rism3d_guess_target": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
         "rism3d_set_guess_crop": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
@@ -416,6 +417,12 @@ class Solver:
         _check(self.lib, self.ctx, self.lib.rism3d_get_sfe(self.ctx, SFE_KINDS[kind], int(pse_order),
                                                            ctypes.byref(tot), per.ctypes.data_as(_dp)))
         return tot.value, per
+
+    def tune(self):
+        """Pick the pencil tile width by measurement (rism3d_tune); returns (W, ms)."""
+        w, ms = ctypes.c_int(), ctypes.c_double()
+        _check(self.lib, self.ctx, self.lib.rism3d_tune(self.ctx, ctypes.byref(w), ctypes.byref(ms)))
+        return w.value, ms.value
 
     def _corner(self, corner):
         return (ctypes.c_int * 3)(*[int(v) for v in corner])

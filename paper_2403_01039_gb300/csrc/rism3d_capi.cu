@@ -186,7 +186,7 @@ static rism3d_status fail(rism3d_ctx *ctx, rism3d_status st, const char *fmt, ..
 namespace {
 
 struct Layout {
-    size_t ctrl, bu, phi, w, psi, spec, X, R, anchor, phase, table, tw, partials, sfe, atoms, sites, staging,
+    size_t ctrl, bu, phi, w, psi, spec, X, R, T, anchor, phase, table, tw, partials, sfe, atoms, sites, staging,
         total;
 };
 
@@ -217,6 +217,7 @@ Layout make_layout(const Geometry &g) {
     L.spec = take((size_t)g.nv * specN * c);
     L.X = take((size_t)g.M * g.nv * g.G * g.s);
     L.R = take((size_t)g.M * g.nv * g.G * g.s);
+    L.T = take((size_t)g.nv * g.G * g.s);
     L.anchor = take((size_t)2 * g.nv * g.G * g.s);
     L.phase = take((size_t)kPhaseChunk * (g.Nx + g.Ny + g.Kz + 1) * c);
     L.table = take((size_t)g.nk * (g.nv + 1) * g.nv * g.s);
@@ -351,6 +352,7 @@ void fill_fields(rism3d_ctx *ctx, const Geometry &g, const Layout &L, Fields<T> 
     f.spec_nyq = f.spec + (long long)g.nv * f.specN;
     f.X = reinterpret_cast<T *>(b + L.X);
     f.R = reinterpret_cast<T *>(b + L.R);
+    f.Tc = reinterpret_cast<T *>(b + L.T);
     f.csr_a = reinterpret_cast<T *>(b + L.anchor);
     f.h_a = f.csr_a + (long long)g.nv * g.G;
     f.phase = reinterpret_cast<C *>(b + L.phase);
@@ -523,21 +525,22 @@ rism3d_status iteration(rism3d_ctx *ctx, bool with_mdiis) {
 
 // Algorithmic HBM bytes of the iterations that ran (from the device counters): per
 // site-point (P = n_v Nx Ny Nz of them, s bytes per real, z = (Kz + 1) / Kz for the half
-// spectrum) plane_fwd moves the history it combines (2 per stored pair + 1 for tau, or 1
-// to load tau), w (1), the spectrum it writes (z) and the anchor (1 read, 1 write on
+// spectrum) plane_fwd moves the history it combines (Y_i per stored pair, R_i as well
+// under dynamic damping, + 1 for the new tau, or 1 to load tau), w (1), the spectrum it
+// writes (z) and the anchor (1 read, 1 write on
 // refresh); pencil reads and writes the spectrum (2 z) plus Psi (z/n_v) until the first
 // anchor; plane_inv reads the spectrum (z), tau and w (2), the history residuals, the
-// anchor h_a, and writes R (1) and h_a on refresh.
+// anchor h_a, and writes R and Y (2) and h_a on refresh.
 void account_iterations(rism3d_ctx *ctx, const Ctrl &c) {
     const double P = (double)ctx->nv * (double)ctx->G;
     const double s = ctx->fp32() ? 4.0 : 8.0;
     const double z = ctx->opt.kgrid == 1 ? 1.0 : (double)(ctx->Kz + 1) / (double)ctx->Kz;   // half spectrum per real
     const double it = (double)c.acc_iters;
     ctx->stats.iterations += c.acc_iters;
-    ctx->stats.bytes[0] += P * s * ((double)c.acc_fwd_units + it * (1.0 + z) +
+    ctx->stats.bytes[0] += P * s * ((double)c.acc_fwd_units + (double)c.acc_upd_r + it * (1.0 + z) +
                                     (double)c.acc_anchor + (double)c.acc_refresh);
     ctx->stats.bytes[1] += P * s * z * (2.0 * it + (double)c.acc_psi / ctx->nv);
-    ctx->stats.bytes[2] += P * s * (it * (z + 3.0) + (double)c.acc_hist + (double)c.acc_anchor +
+    ctx->stats.bytes[2] += P * s * (it * (z + 4.0) + (double)c.acc_hist + (double)c.acc_anchor +
                                     (double)c.acc_refresh);
     const int nyc = ctx->fp32() ? ctx->f32.nyc : ctx->f64.nyc;
     ctx->stats.bytes[3] += 8.0 * ctx->nv * ctx->Nx * nyc * (it + (double)c.acc_hist);
@@ -628,6 +631,7 @@ void reset_ctrl(rism3d_ctx *ctx, Ctrl &c) {
     c.s2 = ctx->opt.anderson_s2;
     c.dynamic = ctx->opt.dynamic_damp ? 1 : 0;
     c.damp = ctx->opt.mdiis_damp;
+    c.eta = ctx->opt.mdiis_damp;       // the first pair's Y uses the static damping
     c.inv_count = 1.0 / ((double)ctx->nv * (double)ctx->G);
     c.cur = ctx->cur_slot;
     c.anchor_valid = 0;
@@ -1236,6 +1240,77 @@ rism3d_status rism3d_get_sfe_gradient(rism3d_ctx *ctx, double *grad) {
         CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     }
     return RISM3D_OK;
+}
+
+}  // extern "C"
+
+// Pencil tile width W chosen by measurement: the x-transform pass is timed on this
+// context's own buffers for every W whose tile fits in shared memory, and the fastest is
+// kept (the captured graph is rebuilt on the next solve).
+template <typename T>
+static rism3d_status tune_pencil(rism3d_ctx *ctx, Fields<T> &f, int *chosen, double *ms_out) {
+    typedef typename Cx<T>::type C;
+    Ctrl &c = *ctx->ctrl_host;
+    const int saved_status = c.status;
+    c.status = kRunning;                      // the pass runs only for a running solve
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ctrl, &c, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(ctx, cudaEventCreate(&e0));
+    CUDA_TRY(ctx, cudaEventCreate(&e1));
+    int best_w = f.W;
+    float best = 1e30f;
+    rism3d_status st = RISM3D_OK;
+    for (int w = 1; w <= 32 && st == RISM3D_OK; w *= 2) {
+        const size_t smem = sizeof(C) * ((size_t)f.nv * w * f.pencil_pitch + f.Nx);
+        if (smem > kMaxSmem - 1024) break;
+        f.W = w;
+        f.tiles_main = f.Ny * ((f.Kz + w - 1) / w);
+        f.tiles_nyq = f.half ? 0 : (f.Ny + w - 1) / w;
+        f.dW = make_fastdiv(w);
+        cudaError_t e = launch_pencil<T>(f, ctx->stream);            // warm-up
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            if (r == 1) e = cudaEventRecord(e0, ctx->stream);
+            if (e == cudaSuccess) e = launch_pencil<T>(f, ctx->stream);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            st = fail(ctx, RISM3D_ECUDA, "pencil tuning (W = %d): %s", w, cudaGetErrorString(e));
+            break;
+        }
+        if (ms < best) {
+            best = ms;
+            best_w = w;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    f.W = best_w;
+    f.tiles_main = f.Ny * ((f.Kz + best_w - 1) / best_w);
+    f.tiles_nyq = f.half ? 0 : (f.Ny + best_w - 1) / best_w;
+    f.dW = make_fastdiv(best_w);
+    c.status = saved_status;
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ctrl, &c, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    if (chosen) *chosen = best_w;
+    if (ms_out) *ms_out = best / 2.0;
+    return st;
+}
+
+extern "C" {
+
+rism3d_status rism3d_tune(rism3d_ctx *ctx, int *pencil_width, double *pencil_ms) {
+    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+    if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "tune before set_solute");
+    DeviceGuard dg(ctx->device);
+    return ctx->fp32() ? tune_pencil<float>(ctx, ctx->f32, pencil_width, pencil_ms)
+                       : tune_pencil<double>(ctx, ctx->f64, pencil_width, pencil_ms);
 }
 
 rism3d_status rism3d_get_stats(const rism3d_ctx *ctx, rism3d_stats *out) {

@@ -68,12 +68,15 @@ struct Ctrl {
     double inv_count;               // 1 / (n_v * Nx * Ny * Nz)
     int n_partials;                 // blocks that wrote Gram partials
     // iterate bookkeeping
-    int cur;                        // ring slot of the current input t (and its R)
-    int do_update;                  // plane_fwd forms t = sum c_i (X_i + eta R_i) into slot cur
+    int cur;                        // ring slot that receives the pair (Y, R) of the current t
+    int do_update;                  // plane_fwd forms t = sum c_i Y_i + sum d_i R_i into Tc
     int upd_n;
     int upd_slot[kMaxHist];
-    double upd_coef[kMaxHist];
-    double eta;
+    double upd_coef[kMaxHist];      // c_i of Eq. 40
+    double upd_dcoef[kMaxHist];     // d_i = c_i (eta - eta_i): nonzero only if the damping changed
+    int upd_r;                      // 1 if some d_i != 0 (the update then also reads R_i)
+    double eta;                     // damping of the next update; plane_inv stores Y = t + eta R
+    double eta_slot[kMaxHist];      // the eta each slot's Y was stored with
     int hist_n;                     // history slots (oldest first) paired with R_cur in the Gram
     int hist_slot[kMaxHist];
     double rms;                     // RMS of the last residual
@@ -85,6 +88,7 @@ struct Ctrl {
     // work counters for the byte model, summed over the iterations that ran
     long long acc_iters;
     long long acc_fwd_units;        // fields read + written by plane_fwd's t (update or load)
+    long long acc_upd_r;            // history residuals read by plane_fwd (dynamic damping)
     long long acc_hist;             // history residuals read by plane_inv
     long long acc_anchor;           // iterations that read the anchor (plane_fwd and plane_inv)
     long long acc_refresh;          // iterations that wrote the anchor
@@ -109,7 +113,8 @@ struct Fields {
     T *w;                           // [nv][G] f - beta*u; the iteration uses d = w + tau
     C *psi, *psi_nyq;               // beta Phi~ / dV on [Nx][Ny][Kz] and the kz = Kz plane [Nx][Ny]
     C *spec, *spec_nyq;             // [nv][Nx][Ny][Kz], [nv][Nx][Ny]
-    T *X, *R;                       // ring [M][nv][G]: X holds tau = t - f, R the residual
+    T *X, *R;                       // ring [M][nv][G]: X holds Y = tau + eta R, R the residual
+    T *Tc;                          // [nv][G] the current iterate tau = t - f
     T *csr_a, *h_a;                 // anchor fields [nv][G]
     C *phase;                       // per-atom axis phase tables [kPhaseChunk][Nx + Ny + Kz + 1]
     T *table;                       // [nk][nv + 1][nv]: X_ag / G and the charge row -Q_g / G

@@ -549,10 +549,10 @@ __device__ __forceinline__ void c2r_rows_half(C *rows, int nr, int yg, int Kz, i
 // Per-launch values of the update and closure, shared by the element loops.
 template <typename T, int MAXH>
 struct FwdArgs {
-    const T *coef;               // [MAXH] update coefficients (shared memory)
+    const T *coef;               // [MAXH] update coefficients of Y_i (shared memory)
+    const T *dcoef;              // [MAXH] coefficients of R_i (dynamic damping only)
     const long long *slot_off;   // [MAXH] ring offsets of the combined pairs (shared memory)
-    int upd_n, do_update, kind, order, anchor, refresh;
-    T eta;
+    int upd_n, upd_r, do_update, kind, order, anchor, refresh;
     T *tcur, *ca;                // this block's part of the new iterate and of c^sr_a
     const T *wp;                 // this block's part of w = f - beta u
     const typename Cx<T>::type *pre;   // half grid: exp(-i pi p / Kz) per packed element, else null
@@ -578,18 +578,30 @@ __device__ __forceinline__ void fwd_elements(const Fields<T> &f, const FwdArgs<T
         const long long oB = (long long)(y0 + yB) * f.Nz + 2 * mB;
         V2 tA, tB;
         if (A.do_update) {
+            // t = sum_i c_i Y_i (+ sum_i d_i R_i when the damping changed since Y_i was
+            // stored), Y_i = t_i + eta_i R_i: one stored field per pair
             tA.x = tA.y = tB.x = tB.y = (T)0;
 #pragma unroll
             for (int i = 0; i < MAXH; ++i) {
                 if (i < A.upd_n) {
-                    const T *xb = f.X + A.slot_off[i], *rb = f.R + A.slot_off[i];
-                    const V2 xa = ld2(xb + oA), ra = ld2(rb + oA);
-                    const V2 xv = ld2(xb + oB), rv = ld2(rb + oB);
+                    const T *yb = f.X + A.slot_off[i];
+                    const V2 ya = ld2(yb + oA), yv = ld2(yb + oB);
                     const T c = A.coef[i];
-                    tA.x += c * (xa.x + A.eta * ra.x);
-                    tA.y += c * (xa.y + A.eta * ra.y);
-                    tB.x += c * (xv.x + A.eta * rv.x);
-                    tB.y += c * (xv.y + A.eta * rv.y);
+                    tA.x += c * ya.x;
+                    tA.y += c * ya.y;
+                    tB.x += c * yv.x;
+                    tB.y += c * yv.y;
+                }
+            }
+            if (A.upd_r) {
+                for (int i = 0; i < A.upd_n; ++i) {
+                    const T *rb = f.R + A.slot_off[i];
+                    const V2 ra = ld2(rb + oA), rv = ld2(rb + oB);
+                    const T d = A.dcoef[i];
+                    tA.x += d * ra.x;
+                    tA.y += d * ra.y;
+                    tB.x += d * rv.x;
+                    tB.y += d * rv.y;
                 }
             }
         } else {
@@ -662,24 +674,26 @@ k_plane_fwd(Fields<T> f) {
     const int stage = ctl->stage;
     const long long ring = (long long)f.nv * f.G;
     const long long siteoff = (long long)gam * f.G + (long long)x * Ny * f.Nz;
-    __shared__ T coef[MAXH];
+    __shared__ T coef[MAXH], dcoef[MAXH];
     __shared__ long long slot_off[MAXH];
     FwdArgs<T, MAXH> A;
     A.upd_n = ctl->upd_n;
     if (threadIdx.x < MAXH) {
         const int i = threadIdx.x;
         coef[i] = i < A.upd_n ? (T)ctl->upd_coef[i] : (T)0;
+        dcoef[i] = i < A.upd_n ? (T)ctl->upd_dcoef[i] : (T)0;
         slot_off[i] = i < A.upd_n ? (long long)ctl->upd_slot[i] * ring + siteoff : 0;
     }
     A.coef = coef;
+    A.dcoef = dcoef;
     A.slot_off = slot_off;
+    A.upd_r = ctl->upd_r;
     A.do_update = ctl->do_update;
     A.kind = ctl->stage_kind[stage];
     A.order = ctl->stage_order[stage];
     A.anchor = ctl->anchor_valid;
     A.refresh = ctl->refresh;
-    A.eta = (T)ctl->eta;
-    A.tcur = f.X + (long long)ctl->cur * ring + siteoff;
+    A.tcur = f.Tc + (long long)gam * f.G + (long long)x * Ny * f.Nz;
     A.ca = f.csr_a + siteoff;
     A.wp = f.w + siteoff;
     A.pre = half ? tw_z : nullptr;
@@ -905,7 +919,8 @@ struct InvArgs {
     const long long *hoff;       // [MAXH] ring offsets of the stored residuals (shared memory)
     int hist_n, kind, order, anchor, refresh;
     const T *tcur, *wp;
-    T *rcur, *ha;
+    T *rcur, *ycur, *ha;         // residual and Y = t + eta R of the new history pair
+    T eta;
     const typename Cx<T>::type *post;   // half grid: conj of exp(-i pi p / Kz) applies, else null
 };
 
@@ -979,6 +994,12 @@ __device__ __forceinline__ void inv_elements(const Fields<T> &f, const InvArgs<T
             }
         if (A.refresh) *reinterpret_cast<V2 *>(A.ha + oA) = hA;
         *reinterpret_cast<V2 *>(A.rcur + oA) = rA;
+        {
+            V2 yA;
+            yA.x = tA.x + A.eta * rA.x;
+            yA.y = tA.y + A.eta * rA.y;
+            *reinterpret_cast<V2 *>(A.ycur + oA) = yA;
+        }
         if (has1) {
             acc[0].add(rB.x, rB.x);
             acc[0].add(rB.y, rB.y);
@@ -990,6 +1011,10 @@ __device__ __forceinline__ void inv_elements(const Fields<T> &f, const InvArgs<T
                 }
             if (A.refresh) *reinterpret_cast<V2 *>(A.ha + oB) = hB;
             *reinterpret_cast<V2 *>(A.rcur + oB) = rB;
+            V2 yB;
+            yB.x = tB.x + A.eta * rB.x;
+            yB.y = tB.y + A.eta * rB.y;
+            *reinterpret_cast<V2 *>(A.ycur + oB) = yB;
         }
     }
 }
@@ -1035,8 +1060,10 @@ k_plane_inv(Fields<T> f) {
     A.order = ctl->stage_order[stage];
     A.anchor = ctl->anchor_valid;
     A.refresh = ctl->refresh;
-    A.tcur = f.X + (long long)ctl->cur * ring + siteoff;
+    A.tcur = f.Tc + (long long)gam * f.G + (long long)x * Ny * f.Nz;
     A.rcur = f.R + (long long)ctl->cur * ring + siteoff;
+    A.ycur = f.X + (long long)ctl->cur * ring + siteoff;
+    A.eta = (T)ctl->eta;
     A.wp = f.w + siteoff;
     A.ha = f.h_a + siteoff;
     A.post = half ? tw_z : nullptr;
@@ -1131,12 +1158,14 @@ static __device__ void mdiis_pre(Ctrl *ctl, const double *sums, MdiisScratch &sc
     const int hist_n = ctl->hist_n;
     sc.mode = 0;
     ctl->acc_iters += 1;
-    ctl->acc_fwd_units += ctl->do_update ? 2 * ctl->upd_n + 1 : 1;
+    ctl->acc_fwd_units += ctl->do_update ? ctl->upd_n + 1 : 1;
+    ctl->acc_upd_r += ctl->do_update && ctl->upd_r ? ctl->upd_n : 0;
     ctl->acc_hist += hist_n;
     ctl->acc_anchor += ctl->anchor_valid;
     ctl->acc_refresh += ctl->refresh;
     ctl->acc_psi += ctl->anchor_valid == 0;
     const int cur = ctl->cur;
+    ctl->eta_slot[cur] = ctl->eta;    // plane_inv stored Y_cur = t + eta R_cur
     const double rr = sums[0];
     const double rms = sqrt(rr * ctl->inv_count);
     ctl->rms = rms;
@@ -1327,9 +1356,14 @@ static __device__ void mdiis_post(Ctrl *ctl, MdiisScratch &sc) {
     if (ctl->dynamic) eta = fmin(fmax(-0.2 * log10(ctl->rms), 0.1), 1.0);
     ctl->eta = eta;
     ctl->upd_n = n;
+    ctl->upd_r = 0;
     for (int i = 0; i < n; ++i) {
         ctl->upd_slot[i] = H[i];
         ctl->upd_coef[i] = sc.c[i];
+        // sum c_i (t_i + eta R_i) = sum c_i Y_i + sum c_i (eta - eta_i) R_i
+        const double d = sc.c[i] * (eta - ctl->eta_slot[H[i]]);
+        ctl->upd_dcoef[i] = d;
+        if (d != 0.0) ctl->upd_r = 1;
     }
     int next;
     if (n < M) {
@@ -1644,7 +1678,7 @@ __global__ void k_guess_crop_out(Fields<T> f, int mode, int slot, int i0, int j0
         if (mode == 0)
             out[id] = tanhf((float)f.bu[src] * 0.25f);
         else
-            out[id] = (float)f.X[(long long)slot * f.nv * f.G + src];
+            out[id] = (float)f.Tc[src];
     }
 }
 
@@ -1652,7 +1686,7 @@ __global__ void k_guess_crop_out(Fields<T> f, int mode, int slot, int i0, int j0
 template <typename T>
 __global__ void k_guess_crop_in(Fields<T> f, int slot, int i0, int j0, int k0, int n, const float *in) {
     const long long total = (long long)f.nv * f.G;
-    T *dst = f.X + (long long)slot * total;
+    T *dst = f.Tc;
     for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < total;
          id += (long long)gridDim.x * blockDim.x) {
         long long r = id;
@@ -1688,7 +1722,8 @@ __global__ void k_init_guess(Fields<T> f, int slot) {
     const long long base = (long long)slot * n;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        f.X[base + i] = (T)0;
+        f.Tc[i] = (T)0;
+    (void)base;
 }
 
 // tau = t - beta q phi from a caller field t (FP64), into ring slot `slot`.
@@ -1700,7 +1735,8 @@ __global__ void k_guess_from_t(Fields<T> f, int slot, const double *src) {
          i += (long long)gridDim.x * blockDim.x) {
         const int g = (int)(i / f.G);
         const long long p = i - (long long)g * f.G;
-        f.X[base + i] = (T)(src[i] - f.bq[g] * (double)f.phi[p]);
+        f.Tc[i] = (T)(src[i] - f.bq[g] * (double)f.phi[p]);
+        (void)base;
     }
 }
 
@@ -1720,7 +1756,7 @@ __global__ void k_get_field(Fields<T> f, int field, int slot, int kind, int orde
         } else {
             const int g = (int)(i / f.G);
             const long long p = i - (long long)g * f.G;
-            const T tau = f.X[(long long)slot * ring + i];
+            const T tau = f.Tc[i];
             const double fq = f.bq[g] * (double)f.phi[p];
             if (field == 4) {
                 v = (double)tau + fq;
@@ -1755,7 +1791,8 @@ k_sfe(Fields<T> f, int slot, int kind, int order, int sfe_kind, int sfe_order, d
     __shared__ double red[32];
     const int g = blockIdx.y;
     const long long ring = (long long)f.nv * f.G;
-    const T *tt = f.X + (long long)slot * ring + (long long)g * f.G;
+    const T *tt = f.Tc + (long long)g * f.G;
+    (void)ring;
     const T *wp = f.w + (long long)g * f.G;
     const double bq = f.bq[g];
     double acc = 0.0;
@@ -1797,7 +1834,7 @@ __global__ void k_grad_weights(Fields<T> f, int slot, int kind, int order, const
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ring;
          i += (long long)gridDim.x * blockDim.x) {
         const int g = (int)(i / f.G);
-        const T tau = f.X[(long long)slot * ring + i];
+        const T tau = f.Tc[i];
         wg[i] = (T)rho_dV[g] * closure_g(f.w[i] + tau, kind, order);
     }
 }

@@ -359,3 +359,21 @@ def test_globule2000_256_fp32_vs_fp64(water_nacl):
     # over the 1.7e8 site-points
     strunc = abs(out[(64, 5e-6)][2] - out[64][2])
     assert abs(out[32][2] - out[64][2]) <= max(0.05, 1.5 * strunc), (out[32][2], out[64][2], strunc)
+
+
+def test_tune_keeps_results_bitwise(water_nacl):
+    """rism3d_tune picks the pencil tile width by timing; the per-column arithmetic does
+    not depend on it, so a solve after tuning reproduces the one before bit for bit."""
+    grid = GRIDS[1]
+    sol = charged_solute()
+    out = []
+    with solver(water_nacl, grid, 32) as S:
+        for tune in (False, True):
+            S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+            if tune:
+                w, ms = S.tune()
+                assert w >= 1 and ms > 0.0
+            rep = S.solve("kh", tol=1e-6)
+            out.append((rep["iterations"], S.get("g")))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])

@@ -83,3 +83,41 @@ def test_guess_crops(water3):
         assert rep["converged"] and rep2["converged"] and rep2["iterations"] <= 3, (rep, rep2)
         with pytest.raises(capi.RismError):
             S.guess_input((10, 10, 10), 24, x)                       # outside the grid
+
+
+def test_learned_guess_solve_matches_oracle(water_nacl):
+    """solute50_128 (FP32, KH, tol 1e-6) started from the trained network's guess: the
+    solve still ends at the oracle's fixed point (bars of the FP32 form against the oracle
+    converged to 1e-10, at the 1024 stored sample points) in fewer iterations than from
+    the zero guess."""
+    import os
+    from conftest import GOLDEN
+    from paper_2403_01039_gb300 import guess
+    wpath = os.path.join(os.path.dirname(capi.__file__), "data", "guess_unet_solute50_128.npz")
+    ref = np.load(os.path.join(GOLDEN, "solute50_128_reference.npz"))
+    W = np.load(wpath)
+    crop = int(W["crop"])
+    grid = synth.cubic_grid(128, 0.5)
+    sol = synth.workload_solute("solute50_128")
+    pts = ref["points"]
+    net = capi.UNet3D(5, 5, crop, tuple(int(c) for c in W["channels"]))
+    try:
+        net.set_params(W["params"])
+        with capi.Solver(water_nacl, grid, precision=32) as S:
+            S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+            zero = S.solve("kh", tol=1e-6)
+            S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+            x = torch.empty((5, crop, crop, crop), dtype=torch.float32, device="cuda")
+            y = torch.empty_like(x)
+            c = guess.corner(128, crop)
+            S.guess_input(c, crop, x)
+            net.forward(x, y)
+            S.set_guess_crop(c, crop, y)
+            rep = S.solve("kh", tol=1e-6)
+            g = S.get("g")[:, pts[:, 0], pts[:, 1], pts[:, 2]]
+            sfe, _ = S.sfe("kh")
+    finally:
+        net.close()
+    assert rep["converged"] and rep["iterations"] < zero["iterations"], (rep, zero)
+    assert np.max(np.abs(g - ref["kh_1e-10_g"])) <= 1e-3
+    assert abs(sfe - float(ref["kh_1e-10_sfe"])) <= 0.05
