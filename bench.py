@@ -322,7 +322,9 @@ def run_ours(args):
     # launches that did work: every iteration for the iteration kernels, every timed launch
     # for the once-per-solve ones
     per_iter = ("plane_fwd", "pencil", "plane_inv", "mdiis", "ypencil_fwd", "ypencil_inv")
-    worked = {k: (stats["iterations"] if k in per_iter else kern[k]["timed"]) for k in kern}
+    per_iter2 = ("fwd_elem", "fft_fwd", "fft_inv", "inv_elem")          # two launches per iteration
+    worked = {k: (stats["iterations"] if k in per_iter else 2 * stats["iterations"] if k in per_iter2
+                  else kern[k]["timed"]) for k in kern}
     avg_ms = {k: (v["ms"] / v["timed"] if v["timed"] else 0.0) for k, v in kern.items()}
     share_ms = {k: avg_ms[k] * worked[k] for k in kern}       # estimated device time in the region
     dom = max(kern, key=lambda k: share_ms[k])

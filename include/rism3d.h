@@ -110,6 +110,10 @@ typedef struct {
     int slab_rows;            /* 0: whole y-z planes per block when they fit in shared memory,
                                  else row chunks plus a y-pencil pass (automatic); > 0 forces
                                  chunks of this many rows */
+    int split_passes;         /* 1: run the plane passes as streaming element kernels and
+                                 transform kernels on two graph branches (FP32, whole planes,
+                                 Nz/2 of 64 or 128; otherwise ignored); 0 (default): the fused
+                                 plane kernels. Same results within rounding. */
     int kgrid;                /* 0: periodic integer k grid (the convention above); 1:
                                  half-integer grid k_m = 2 pi (m + 1/2) / (N d) on every axis
                                  (the placement of k in the "Numerical procedure" section): no
@@ -135,8 +139,11 @@ typedef struct {
  * 1 pencil (x FFT + Eq. 13 contraction + inverse x FFT), 2 plane_inv (inverse y/z FFT +
  * residual + Gram partials), 3 mdiis (Gram reduction + bordered solve), 4 potential
  * (Eqs. 22, 29), 5 long_range (Eq. 30), 6 sfe, 7 other (guess, conversions, field output),
- * 8 and 9 the forward and inverse y-pencil passes (planes split into row chunks only). */
-#define RISM3D_N_KERNELS 10
+ * 8 and 9 the forward and inverse y-pencil passes (planes split into row chunks only),
+ * 10-13 the split form of the plane passes (FP32, whole planes, Nz/2 of 64 or 128): 10
+ * fwd_elem (update + closure), 11 fft_fwd (forward z/y FFT), 12 fft_inv (inverse y/z FFT),
+ * 13 inv_elem (residual + Gram partials), each launched for two halves of the x planes. */
+#define RISM3D_N_KERNELS 14
 typedef struct {
     long long launches[RISM3D_N_KERNELS];   /* kernels launched (including ones that found the
                                                solve finished and returned at once) */

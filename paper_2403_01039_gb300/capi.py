@@ -41,13 +41,13 @@ class Options(ctypes.Structure):
                 ("max_atoms", ctypes.c_int), ("timing", ctypes.c_int),
                 ("accelerator", ctypes.c_int), ("anderson_s1", ctypes.c_double),
                 ("anderson_s2", ctypes.c_double), ("slab_rows", ctypes.c_int),
-                ("kgrid", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+                ("split_passes", ctypes.c_int), ("kgrid", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
-N_KERNELS = 10
+N_KERNELS = 14
 KERNEL_NAMES = ["plane_fwd", "pencil", "plane_inv", "mdiis", "potential", "long_range", "sfe", "other",
-                "ypencil_fwd", "ypencil_inv"]
+                "ypencil_fwd", "ypencil_inv", "fwd_elem", "fft_fwd", "fft_inv", "inv_elem"]
 
 
 class Stats(ctypes.Structure):
@@ -289,7 +289,7 @@ class Solver:
     def __init__(self, solvent, grid, precision=32, mdiis_nvec=5, mdiis_damp=0.7,
                  dynamic_damp=False, max_iter=10000, check_every=8, max_atoms=100000,
                  timing=False, accelerator="mdiis", anderson_s=(0.2, 0.0), slab_rows=0,
-                 kgrid="integer", stream=None, device=None):
+                 kgrid="integer", split_passes=False, stream=None, device=None):
         import torch
         self._torch = torch
         lib = load()
@@ -313,6 +313,7 @@ class Solver:
         o.anderson_s1, o.anderson_s2 = float(anderson_s[0]), float(anderson_s[1])
         o.slab_rows = int(slab_rows)
         o.kgrid = {"integer": 0, "half": 1}[kgrid]
+        o.split_passes = int(bool(split_passes))
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
             o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)

@@ -27,7 +27,8 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr size_t kMaxSmem = 227 * 1024;
 constexpr size_t kPencilSmemTarget = 64 * 1024;
 constexpr size_t kSlabSmemTarget = 72 * 1024;   // row-chunk size when a plane does not fit
-constexpr int kEventsPerIter = 7;                 // up to six kernels per iteration
+constexpr int kMaxLaunches = 12;                  // launches of one iteration at most
+constexpr int kEventsPerIter = 2 * kMaxLaunches;  // an event pair around each
 
 thread_local std::string g_create_error;
 
@@ -117,6 +118,11 @@ int fft_chunk(const FftPlan &p, int nthreads, int maxc) {
 
 }  // namespace
 
+namespace {
+// element-kernel blocks per site for one half of the planes (as launch_split uses)
+int split_elem_blocks_host(int nv) { return (kSplitBlocks + nv - 1) / nv; }
+}  // namespace
+
 struct rism3d_ctx {
     int device = 0;
     int precision = 32;
@@ -150,6 +156,8 @@ struct rism3d_ctx {
     std::vector<cudaEvent_t> ev;               // [check_every][5] around the iteration kernels
     cudaEvent_t ev_aux[2] = {nullptr, nullptr};
     cudaEvent_t chunk_ev = nullptr;            // end of the last launched iteration chunk
+    cudaStream_t side = nullptr;               // second branch of the split plane passes
+    cudaEvent_t fork[4] = {nullptr, nullptr, nullptr, nullptr};
     // state of the solve in progress (rism3d_solve and the batch scheduler)
     int run_iter_before = 0, run_closure = kKH, run_order = 1;
     std::chrono::steady_clock::time_point run_t0;
@@ -222,7 +230,7 @@ Layout make_layout(const Geometry &g) {
     L.phase = take((size_t)kPhaseChunk * (g.Nx + g.Ny + g.Kz + 1) * c);
     L.table = take((size_t)g.nk * (g.nv + 1) * g.nv * g.s);
     L.tw = take((size_t)(g.Nx + g.Ny + g.Kz + g.Kz + 1 + g.Kz + g.Ny + g.Nx) * c);
-    L.partials = take((size_t)g.nv * g.Nx * g.nyc * (kMaxHist + 1) * sizeof(double));
+    L.partials = take((size_t)std::max(g.nv * g.Nx * g.nyc, kSplitPartials) * (kMaxHist + 1) * sizeof(double));
     L.sfe = take((size_t)g.nv * kSfeBlocksPerSite * sizeof(double));
     L.atoms = take((size_t)g.max_atoms * kAtomStride * sizeof(double));
     L.sites = take((size_t)4 * kMaxSites * sizeof(double));
@@ -256,6 +264,7 @@ rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, cons
         return fail(nullptr, RISM3D_EINVAL, "mdiis_damp must be in (0, 2]");
     if (op->slab_rows < 0) return fail(nullptr, RISM3D_EINVAL, "slab_rows must be >= 0");
     if (op->kgrid != 0 && op->kgrid != 1) return fail(nullptr, RISM3D_EINVAL, "kgrid must be 0 or 1");
+    if (op->split_passes != 0 && op->split_passes != 1) return fail(nullptr, RISM3D_EINVAL, "split_passes must be 0 or 1");
     if (op->timing < 0 || op->timing > 2) return fail(nullptr, RISM3D_EINVAL, "timing must be 0, 1 or 2");
     if (op->accelerator != 0 && op->accelerator != 1)
         return fail(nullptr, RISM3D_EINVAL, "accelerator must be 0 (MDIIS) or 1 (modified Anderson)");
@@ -367,6 +376,7 @@ void fill_fields(rism3d_ctx *ctx, const Geometry &g, const Layout &L, Fields<T> 
     f.tw_ys = f.tw_q + g.Kz;
     f.tw_xs = f.tw_ys + g.Ny;
     f.half = ctx->opt.kgrid == 1;
+    f.split = ctx->opt.split_passes != 0;
     f.px = g.px;
     f.py = g.py;
     f.ph = g.ph;
@@ -399,6 +409,7 @@ void fill_fields(rism3d_ctx *ctx, const Geometry &g, const Layout &L, Fields<T> 
     }
     f.partials = reinterpret_cast<double *>(b + L.partials);
     f.ctrl = reinterpret_cast<Ctrl *>(b + L.ctrl);
+    f.nparts = split_planes(f) ? 2 * split_elem_blocks_host(g.nv) * g.nv : g.nv * g.Nx * g.nyc;
 }
 
 // Interpolation table of Eq. 13 scaled for the unnormalised inverse transform:
@@ -479,48 +490,112 @@ void closure_stages(int kind, int order, double tol, Ctrl &c) {
     for (int i = 0; i < n; ++i) c.stage_tol[i] = (i == n - 1) ? tol : stage_tol;
 }
 
-// The kernels of one iteration in order, with their stats slots: plane_fwd (0),
-// [y pencils forward (8)], pencil (1), [y pencils inverse (9)], plane_inv (2), mdiis (3).
-template <typename T>
-rism3d_status launch_step(rism3d_ctx *ctx, const Fields<T> &f, int slot) {
-    switch (slot) {
-        case 0: CUDA_TRY(ctx, launch_plane_fwd<T>(f, ctx->stream)); break;
-        case 8: CUDA_TRY(ctx, launch_ypencil<T>(f, -1, ctx->stream)); break;
-        case 1: CUDA_TRY(ctx, launch_pencil<T>(f, ctx->stream)); break;
-        case 9: CUDA_TRY(ctx, launch_ypencil<T>(f, +1, ctx->stream)); break;
-        case 2: CUDA_TRY(ctx, launch_plane_inv<T>(f, ctx->stream)); break;
-        case 3: CUDA_TRY(ctx, launch_mdiis<T>(f, ctx->stream)); break;
-        default: break;
+// One iteration as a list of launches. Fused form: plane_fwd (stats slot 0), [y pencils
+// forward (8)], pencil (1), [y pencils inverse (9)], plane_inv (2), mdiis (3), all on the
+// context's stream. Split form (FP32 whole planes, split_planes): the element and
+// transform kernels of the two halves of the x planes on two branches,
+//   main: fwd_elem(A) -> fft_fwd(A) -> [wait B] fft_fwd(B) -> pencil -> fft_inv(A) ->
+//         fft_inv(B) -> inv_elem(B) -> [wait] mdiis
+//   side: [after fwd_elem(A)] fwd_elem(B);   [after fft_inv(A)] inv_elem(A)
+// so that each element kernel runs beside a transform kernel (slots 10-13 for fwd_elem,
+// fft_fwd, fft_inv, inv_elem). tev (timing) receives an event pair around every launch
+// on its stream and tslot the launch's stats slot; returns the number of launches.
+struct Launch {
+    int slot, which, stream, half;
+};
+
+int iteration_plan(const rism3d_ctx *ctx, bool with_mdiis, Launch *L) {
+    const bool fp32 = ctx->fp32();
+    const bool split = fp32 ? split_planes(ctx->f32) : false;
+    const bool ysplit = (fp32 ? ctx->f32.nyc : ctx->f64.nyc) > 1;
+    int n = 0;
+    if (split) {
+        L[n++] = {10, 0, 0, 0};
+        L[n++] = {10, 0, 1, 1};
+        L[n++] = {11, 1, 0, 0};
+        L[n++] = {11, 1, 0, 1};
+        L[n++] = {1, -1, 0, 0};
+        L[n++] = {12, 2, 0, 0};
+        L[n++] = {13, 3, 1, 0};
+        L[n++] = {12, 2, 0, 1};
+        L[n++] = {13, 3, 0, 1};
+    } else {
+        L[n++] = {0, -1, 0, 0};
+        if (ysplit) L[n++] = {8, -1, 0, 0};
+        L[n++] = {1, -1, 0, 0};
+        if (ysplit) L[n++] = {9, -1, 0, 0};
+        L[n++] = {2, -1, 0, 0};
     }
-    return RISM3D_OK;
+    if (with_mdiis) L[n++] = {3, -1, 0, 0};
+    return n;
 }
 
+// launches per iteration and kernel slot (both halves of a split pass count)
 int iteration_slots(const rism3d_ctx *ctx, bool with_mdiis, int *slots) {
-    const bool split = (ctx->fp32() ? ctx->f32.nyc : ctx->f64.nyc) > 1;
-    int n = 0;
-    slots[n++] = 0;
-    if (split) slots[n++] = 8;
-    slots[n++] = 1;
-    if (split) slots[n++] = 9;
-    slots[n++] = 2;
-    if (with_mdiis) slots[n++] = 3;
+    Launch L[kMaxLaunches];
+    const int n = iteration_plan(ctx, with_mdiis, L);
+    for (int i = 0; i < n; ++i) slots[i] = L[i].slot;
     return n;
 }
 
 template <typename T>
-rism3d_status run_iteration_kernels(rism3d_ctx *ctx, const Fields<T> &f, bool with_mdiis) {
-    int slots[8];
-    const int n = iteration_slots(ctx, with_mdiis, slots);
-    for (int i = 0; i < n; ++i) {
-        rism3d_status st = launch_step<T>(ctx, f, slots[i]);
-        if (st != RISM3D_OK) return st;
+rism3d_status launch_one(rism3d_ctx *ctx, const Fields<T> &f, const Launch &l, cudaStream_t s) {
+    const int half_x = f.Nx / 2;
+    const int x0 = l.half ? half_x : 0, x1 = l.half ? f.Nx : half_x;
+    switch (l.slot) {
+        case 0: CUDA_TRY(ctx, launch_plane_fwd<T>(f, s)); break;
+        case 8: CUDA_TRY(ctx, launch_ypencil<T>(f, -1, s)); break;
+        case 1: CUDA_TRY(ctx, launch_pencil<T>(f, s)); break;
+        case 9: CUDA_TRY(ctx, launch_ypencil<T>(f, +1, s)); break;
+        case 2: CUDA_TRY(ctx, launch_plane_inv<T>(f, s)); break;
+        case 3: CUDA_TRY(ctx, launch_mdiis<T>(f, s)); break;
+        default: CUDA_TRY(ctx, launch_split<T>(f, l.which, x0, x1, l.half ? f.nparts / 2 : 0, s)); break;
     }
     return RISM3D_OK;
 }
 
+template <typename T>
+rism3d_status run_iteration(rism3d_ctx *ctx, const Fields<T> &f, bool with_mdiis, cudaEvent_t *tev) {
+    Launch L[kMaxLaunches];
+    const int n = iteration_plan(ctx, with_mdiis, L);
+    const unsigned ext = cudaEventRecordExternal;
+    cudaStream_t st[2] = {ctx->stream, ctx->side};
+    const bool split = n > 0 && L[0].slot == 10;
+    if (split && (!ctx->side || !ctx->fork[0])) return fail(ctx, RISM3D_ESTATE, "split passes without side stream");
+    for (int i = 0; i < n; ++i) {
+        const Launch &l = L[i];
+        if (split) {                                      // fork / join points of the plan
+            if (i == 1 || i == 6) CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->side, ctx->fork[i == 1 ? 0 : 2], 0));
+            if (i == 3) CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->fork[1], 0));
+        }
+        cudaStream_t s = st[l.stream];
+        if (tev) CUDA_TRY(ctx, cudaEventRecordWithFlags(tev[2 * i], s, ext));
+        rism3d_status r = launch_one<T>(ctx, f, l, s);
+        if (r != RISM3D_OK) return r;
+        if (tev) CUDA_TRY(ctx, cudaEventRecordWithFlags(tev[2 * i + 1], s, ext));
+        if (split) {
+            if (i == 0) CUDA_TRY(ctx, cudaEventRecord(ctx->fork[0], ctx->stream));   // fwd_elem(A) done
+            if (i == 1) CUDA_TRY(ctx, cudaEventRecord(ctx->fork[1], ctx->side));     // fwd_elem(B) done
+            if (i == 5) CUDA_TRY(ctx, cudaEventRecord(ctx->fork[2], ctx->stream));   // fft_inv(A) done
+            if (i == 6) CUDA_TRY(ctx, cudaEventRecord(ctx->fork[3], ctx->side));     // inv_elem(A) done
+            if (i == 8) CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->fork[3], 0));   // join
+        }
+    }
+    return RISM3D_OK;
+}
+
+// The split plane passes' second stream and fork/join events (created once).
+rism3d_status ensure_side(rism3d_ctx *ctx) {
+    if (!(ctx->fp32() && split_planes(ctx->f32)) || ctx->side) return RISM3D_OK;
+    CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    for (auto &e : ctx->fork) CUDA_TRY(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return RISM3D_OK;
+}
+
 rism3d_status iteration(rism3d_ctx *ctx, bool with_mdiis) {
-    return ctx->fp32() ? run_iteration_kernels<float>(ctx, ctx->f32, with_mdiis)
-                       : run_iteration_kernels<double>(ctx, ctx->f64, with_mdiis);
+    if (rism3d_status st = ensure_side(ctx)) return st;
+    return ctx->fp32() ? run_iteration<float>(ctx, ctx->f32, with_mdiis, nullptr)
+                       : run_iteration<double>(ctx, ctx->f64, with_mdiis, nullptr);
 }
 
 // Algorithmic HBM bytes of the iterations that ran (from the device counters): per
@@ -537,11 +612,21 @@ void account_iterations(rism3d_ctx *ctx, const Ctrl &c) {
     const double z = ctx->opt.kgrid == 1 ? 1.0 : (double)(ctx->Kz + 1) / (double)ctx->Kz;   // half spectrum per real
     const double it = (double)c.acc_iters;
     ctx->stats.iterations += c.acc_iters;
-    ctx->stats.bytes[0] += P * s * ((double)c.acc_fwd_units + (double)c.acc_upd_r + it * (1.0 + z) +
-                                    (double)c.acc_anchor + (double)c.acc_refresh);
     ctx->stats.bytes[1] += P * s * z * (2.0 * it + (double)c.acc_psi / ctx->nv);
-    ctx->stats.bytes[2] += P * s * (it * (z + 4.0) + (double)c.acc_hist + (double)c.acc_anchor +
-                                    (double)c.acc_refresh);
+    if (ctx->fp32() && split_planes(ctx->f32)) {
+        // split passes: the element kernels also write / read the transform input / output
+        ctx->stats.bytes[10] += P * s * ((double)c.acc_fwd_units + (double)c.acc_upd_r + 2.0 * it +
+                                         (double)c.acc_anchor + (double)c.acc_refresh);
+        ctx->stats.bytes[11] += P * s * it * (1.0 + z);
+        ctx->stats.bytes[12] += P * s * it * (z + 1.0);
+        ctx->stats.bytes[13] += P * s * (it * 5.0 + (double)c.acc_hist + (double)c.acc_anchor +
+                                         (double)c.acc_refresh);
+    } else {
+        ctx->stats.bytes[0] += P * s * ((double)c.acc_fwd_units + (double)c.acc_upd_r + it * (1.0 + z) +
+                                        (double)c.acc_anchor + (double)c.acc_refresh);
+        ctx->stats.bytes[2] += P * s * (it * (z + 4.0) + (double)c.acc_hist + (double)c.acc_anchor +
+                                        (double)c.acc_refresh);
+    }
     const int nyc = ctx->fp32() ? ctx->f32.nyc : ctx->f64.nyc;
     ctx->stats.bytes[3] += 8.0 * ctx->nv * ctx->Nx * nyc * (it + (double)c.acc_hist);
     if (nyc > 1) {                    // y pencils read and write the spectrum
@@ -572,21 +657,6 @@ struct AuxTimer {
     }
 };
 
-template <typename T>
-rism3d_status timed_iteration(rism3d_ctx *ctx, const Fields<T> &f, cudaEvent_t *e) {
-    // external records: captured into the graph as event-record nodes that time each kernel
-    const unsigned x = cudaEventRecordExternal;
-    int slots[8];
-    const int n = iteration_slots(ctx, true, slots);
-    CUDA_TRY(ctx, cudaEventRecordWithFlags(e[0], ctx->stream, x));
-    for (int i = 0; i < n; ++i) {
-        rism3d_status st = launch_step<T>(ctx, f, slots[i]);
-        if (st != RISM3D_OK) return st;
-        CUDA_TRY(ctx, cudaEventRecordWithFlags(e[i + 1], ctx->stream, x));
-    }
-    return RISM3D_OK;
-}
-
 rism3d_status build_graph(rism3d_ctx *ctx) {
     if (ctx->graph) return RISM3D_OK;
     cudaGraph_t g = nullptr;
@@ -595,16 +665,15 @@ rism3d_status build_graph(rism3d_ctx *ctx) {
         ctx->ev.assign((size_t)K * kEventsPerIter, nullptr);
         for (auto &e : ctx->ev) CUDA_TRY(ctx, cudaEventCreate(&e));
     }
+    if (rism3d_status st0 = ensure_side(ctx)) return st0;
     CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     rism3d_status st = RISM3D_OK;
     for (int i = 0; i < K && st == RISM3D_OK; ++i) {
         // timing 1: every iteration of the graph; 2: its first iteration only
         const bool timed = ctx->opt.timing == 1 || (ctx->opt.timing == 2 && i == 0);
-        if (timed)
-            st = ctx->fp32() ? timed_iteration<float>(ctx, ctx->f32, &ctx->ev[(size_t)i * kEventsPerIter])
-                             : timed_iteration<double>(ctx, ctx->f64, &ctx->ev[(size_t)i * kEventsPerIter]);
-        else
-            st = iteration(ctx, true);
+        cudaEvent_t *tev = timed ? &ctx->ev[(size_t)i * kEventsPerIter] : nullptr;
+        st = ctx->fp32() ? run_iteration<float>(ctx, ctx->f32, true, tev)
+                         : run_iteration<double>(ctx, ctx->f64, true, tev);
     }
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
     if (st != RISM3D_OK) {
@@ -924,7 +993,7 @@ static rism3d_status solve_chunk_done(rism3d_ctx *ctx, bool *running) {
     const int K = ctx->opt.check_every;
     const int ran = c.iter - ctx->run_iter_before;
     ctx->run_iter_before = c.iter;
-    int slots[8];
+    int slots[kMaxLaunches];
     const int nk = iteration_slots(ctx, true, slots);
     for (int k = 0; k < nk; ++k) ctx->stats.launches[slots[k]] += K;
     if (ctx->opt.timing) {
@@ -932,7 +1001,7 @@ static rism3d_status solve_chunk_done(rism3d_ctx *ctx, bool *running) {
         for (int i = 0; i < ran && i < timed_its; ++i)
             for (int k = 0; k < nk; ++k) {
                 float ms = 0.f;
-                const size_t e0 = (size_t)i * kEventsPerIter + k;
+                const size_t e0 = (size_t)i * kEventsPerIter + 2 * k;   // pair around launch k
                 CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev[e0], ctx->ev[e0 + 1]));
                 ctx->stats.ms[slots[k]] += ms;
                 ctx->stats.timed[slots[k]] += 1;
@@ -1089,7 +1158,7 @@ rism3d_status rism3d_residual(rism3d_ctx *ctx, int closure, int pse_order, const
     st = iteration(ctx, false);
     if (st != RISM3D_OK) return st;
     {
-        int slots[8];
+        int slots[kMaxLaunches];
         const int nk = iteration_slots(ctx, false, slots);
         for (int kk = 0; kk < nk; ++kk) ctx->stats.launches[slots[kk]] += 1;
     }
@@ -1340,6 +1409,9 @@ void rism3d_destroy(rism3d_ctx *ctx) {
         for (auto e : ctx->ev_aux)
             if (e) cudaEventDestroy(e);
         if (ctx->chunk_ev) cudaEventDestroy(ctx->chunk_ev);
+        for (auto e : ctx->fork)
+            if (e) cudaEventDestroy(e);
+        if (ctx->side) cudaStreamDestroy(ctx->side);
         if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
         if (ctx->ctrl_host) cudaFreeHost(ctx->ctrl_host);
         if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

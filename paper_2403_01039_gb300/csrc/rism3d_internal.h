@@ -13,6 +13,8 @@ constexpr int kMaxClosureStages = 12;
 constexpr int kThreadsPlane = 256;
 constexpr int kThreadsPencil = 256;
 constexpr int kThreadsMdiis = 32 * (kMaxHist + 1);   // at least one warp per Gram value
+constexpr int kSplitBlocks = 608;                     // element-kernel blocks per half (split passes)
+constexpr int kSplitPartials = 2 * (kSplitBlocks + kMaxSites);   // Gram partial slots they need
 
 // Solver status words written by the device (Ctrl::status).
 enum { kRunning = 0, kConverged = 1, kDiverged = 2, kMaxIter = 3, kStopped = 4 };
@@ -122,6 +124,7 @@ struct Fields {
     double inv_dk;
     C *tw_x, *tw_y, *tw_h, *tw_z;   // exp(-2 pi i m / L) for L = Nx, Ny, Kz, Nz
     int half;                       // 1: half-integer k grid
+    int split;                      // 1: split plane passes requested
     C *tw_q;                        // half grid: exp(-i pi (2m + 1) / Nz), m < Kz
     C *tw_ys, *tw_xs;               // half grid: exp(-i pi n / N) for N = Ny, Nx
     FftPlan px, py, ph;
@@ -135,7 +138,8 @@ struct Fields {
     FastDiv dKz, dKz1h, dKzp, dW, dNx, dWy, dNy;   // Kz, Kz/2 + 1, (Kz + 1)/2, W, Nx, Wy, Ny
     double bq[kMaxSites];           // beta * q_gamma
     double ks[3];                   // 2 pi / (N d) per axis
-    double *partials;               // [kMaxHist + 1][nv * Nx * nyc] (value-major)
+    double *partials;               // [kMaxHist + 1][nparts] (value-major)
+    int nparts;                     // Gram partial sums per value (blocks that write them)
     Ctrl *ctrl;
 };
 
@@ -180,6 +184,11 @@ void set_global_error(const char *msg);
 template <typename T>
 cudaError_t launch_guess_crop(const Fields<T> &f, int mode, int slot, const int *corner, int n, float *out,
                               const float *in, cudaStream_t s);
+// Split plane passes: which = 0 fwd_elem, 1 fft_fwd, 2 fft_inv, 3 inv_elem over x planes
+// [x0, x1); inv_elem writes its Gram partials from slot part0.
+template <typename T> bool split_planes(const Fields<T> &f);
+template <typename T>
+cudaError_t launch_split(const Fields<T> &f, int which, int x0, int x1, int part0, cudaStream_t s);
 template <typename T>
 cudaError_t launch_sfe_gradient(const Fields<T> &f, int slot, int kind, int order, const double *rho_dV,
                                 const double *atoms, int n_atoms, const double *site_sig,

@@ -1949,6 +1949,262 @@ cudaError_t launch_sfe_gradient(const Fields<T> &f, int slot, int kind, int orde
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ split plane passes
+// The plane passes in two kernels each, for x planes [x0, x1), so that the streaming
+// element work of one half of the planes can run beside the transforms of the other:
+//   fwd_elem : MDIIS update, closure, c^sr - c^sr_a  -> the spectrum buffer (real layout)
+//   fft_fwd  : z and y transforms of those planes, in place (spectrum layout)
+//   fft_inv  : inverse y and z transforms, in place back to the real layout
+//   inv_elem : residual, Y, Gram-row partial sums
+// The spectrum buffer holds n_v * Nx * Ny * Nz reals, so plane (site, x) occupies the same
+// bytes in both layouts and each transform block works in place on its own plane. FP32,
+// whole planes, integer grid and Nz/2 = LZ in {64, 128}.
+
+// Four consecutive reals (two packed complex elements) per thread and step.
+__device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+
+template <int MAXH>
+__global__ void __launch_bounds__(256) k_fwd_elem(Fields<float> f, int x0, int x1) {
+    const Ctrl *ctl = f.ctrl;
+    if (ctl->status != kRunning) return;
+    __shared__ float coef[MAXH], dcoef[MAXH];
+    __shared__ long long slot_off[MAXH];
+    const long long ring = (long long)f.nv * f.G;
+    const int upd_n = ctl->upd_n;
+    if (threadIdx.x < MAXH) {
+        const int i = threadIdx.x;
+        coef[i] = i < upd_n ? (float)ctl->upd_coef[i] : 0.f;
+        dcoef[i] = i < upd_n ? (float)ctl->upd_dcoef[i] : 0.f;
+        slot_off[i] = i < upd_n ? (long long)ctl->upd_slot[i] * ring : 0;
+    }
+    const int do_update = ctl->do_update, upd_r = ctl->upd_r;
+    const int stage = ctl->stage, kind = ctl->stage_kind[stage], order = ctl->stage_order[stage];
+    const int anchor = ctl->anchor_valid, refresh = ctl->refresh;
+    __syncthreads();
+    const int g = blockIdx.y;
+    const long long plane = (long long)f.Ny * f.Nz;
+    const long long base = (long long)g * f.G + (long long)x0 * plane;
+    const long long nq = (long long)(x1 - x0) * plane / 4;
+    float *cs = reinterpret_cast<float *>(f.spec);
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long o = base + 4 * q;
+        float4 t;
+        if (do_update) {
+            t = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < MAXH; ++i) {
+                if (i < upd_n) {
+                    const float4 y = ld4(f.X + slot_off[i] + o);
+                    const float c = coef[i];
+                    t.x += c * y.x;
+                    t.y += c * y.y;
+                    t.z += c * y.z;
+                    t.w += c * y.w;
+                }
+            }
+            if (upd_r)
+                for (int i = 0; i < upd_n; ++i) {
+                    const float4 r = ld4(f.R + slot_off[i] + o);
+                    const float d = dcoef[i];
+                    t.x += d * r.x;
+                    t.y += d * r.y;
+                    t.z += d * r.z;
+                    t.w += d * r.w;
+                }
+        } else {
+            t = ld4(f.Tc + o);
+        }
+        const float4 w = ld4(f.w + o);
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (anchor) a = ld4(f.csr_a + o);
+        float4 c;
+        c.x = closure_g(w.x + t.x, kind, order) - 1.f - t.x;
+        c.y = closure_g(w.y + t.y, kind, order) - 1.f - t.y;
+        c.z = closure_g(w.z + t.z, kind, order) - 1.f - t.z;
+        c.w = closure_g(w.w + t.w, kind, order) - 1.f - t.w;
+        if (do_update) *reinterpret_cast<float4 *>(f.Tc + o) = t;
+        if (refresh) *reinterpret_cast<float4 *>(f.csr_a + o) = c;
+        *reinterpret_cast<float4 *>(cs + o) = make_float4(c.x - a.x, c.y - a.y, c.z - a.z, c.w - a.w);
+    }
+}
+
+template <int MAXH>
+__global__ void __launch_bounds__(256) k_inv_elem(Fields<float> f, int x0, int x1, int part0, int nparts) {
+    const Ctrl *ctl = f.ctrl;
+    if (ctl->status != kRunning) return;
+    __shared__ long long hoff[MAXH];
+    __shared__ double red[(MAXH + 1) * 8];
+    const long long ring = (long long)f.nv * f.G;
+    const int hist_n = ctl->hist_n;
+    if (threadIdx.x < MAXH) hoff[threadIdx.x] = threadIdx.x < hist_n ? (long long)ctl->hist_slot[threadIdx.x] * ring : 0;
+    const int stage = ctl->stage, kind = ctl->stage_kind[stage], order = ctl->stage_order[stage];
+    const int anchor = ctl->anchor_valid, refresh = ctl->refresh;
+    const float eta = (float)ctl->eta;
+    const long long cur = (long long)ctl->cur * ring;
+    __syncthreads();
+    const int g = blockIdx.y;
+    const long long plane = (long long)f.Ny * f.Nz;
+    const long long base = (long long)g * f.G + (long long)x0 * plane;
+    const long long nq = (long long)(x1 - x0) * plane / 4;
+    const float *dh = reinterpret_cast<const float *>(f.spec);
+    GramAcc<float> acc[MAXH + 1];
+#pragma unroll
+    for (int i = 0; i <= MAXH; ++i) acc[i].zero();
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long o = base + 4 * q;
+        const float4 t = ld4(f.Tc + o), w = ld4(f.w + o), hc = ld4(dh + o);
+        float4 ha = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (anchor) ha = ld4(f.h_a + o);
+        float4 qv[MAXH];
+#pragma unroll
+        for (int i = 0; i < MAXH; ++i)
+            if (i < hist_n) qv[i] = ld4(f.R + hoff[i] + o);
+        const float g0 = closure_g(w.x + t.x, kind, order), g1 = closure_g(w.y + t.y, kind, order);
+        const float g2 = closure_g(w.z + t.z, kind, order), g3 = closure_g(w.w + t.w, kind, order);
+        // R = h + 1 - g (Eq. 33) with h = h_a + dh, (h_a - g) first as in plane_inv
+        float4 r;
+        if (anchor) {
+            r.x = ((ha.x - g0) + 1.f) + hc.x;
+            r.y = ((ha.y - g1) + 1.f) + hc.y;
+            r.z = ((ha.z - g2) + 1.f) + hc.z;
+            r.w = ((ha.w - g3) + 1.f) + hc.w;
+        } else {
+            r.x = (hc.x - g0) + 1.f;
+            r.y = (hc.y - g1) + 1.f;
+            r.z = (hc.z - g2) + 1.f;
+            r.w = (hc.w - g3) + 1.f;
+        }
+        acc[0].add(r.x, r.x);
+        acc[0].add(r.y, r.y);
+        acc[0].add(r.z, r.z);
+        acc[0].add(r.w, r.w);
+#pragma unroll
+        for (int i = 0; i < MAXH; ++i)
+            if (i < hist_n) {
+                acc[i + 1].add(r.x, qv[i].x);
+                acc[i + 1].add(r.y, qv[i].y);
+                acc[i + 1].add(r.z, qv[i].z);
+                acc[i + 1].add(r.w, qv[i].w);
+            }
+        if (refresh)
+            *reinterpret_cast<float4 *>(f.h_a + o) =
+                make_float4(ha.x + hc.x, ha.y + hc.y, ha.z + hc.z, ha.w + hc.w);
+        *reinterpret_cast<float4 *>(f.R + cur + o) = r;
+        *reinterpret_cast<float4 *>(f.X + cur + o) =
+            make_float4(t.x + eta * r.x, t.y + eta * r.y, t.z + eta * r.z, t.w + eta * r.w);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i <= MAXH; ++i)
+        if (i <= hist_n) {
+            acc[i].warp_reduce();
+            if (lane == 0) red[i * 8 + warp] = acc[i].value();
+        }
+    __syncthreads();
+    if (threadIdx.x <= hist_n) {
+        double s = 0.0;
+        for (int k = 0; k < nw; ++k) s += red[threadIdx.x * 8 + k];
+        const int blk = part0 + blockIdx.y * gridDim.x + blockIdx.x;
+        f.partials[(long long)threadIdx.x * nparts + blk] = s;
+    }
+}
+
+// z and y transforms of planes [x0, x1) in place: the block's plane is read as packed rows
+// (real layout), transformed, and written back in the spectrum layout.
+template <int LZ>
+__global__ void __launch_bounds__(kThreadsPlane, RISM_MINBLOCKS_F32) k_fft_fwd(Fields<float> f, int x0) {
+    typedef float2 C;
+    if (f.ctrl->status != kRunning) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *buf = reinterpret_cast<C *>(smraw);
+    const int Ny = f.Ny, Kz = LZ, pitch = f.pitch;
+    C *tw_h = buf + (long)Ny * pitch;
+    C *tw_y = tw_h + Kz;
+    C *tw_z = tw_y + Ny;
+    for (int i = threadIdx.x; i < Kz; i += blockDim.x) tw_h[i] = f.tw_h[i];
+    for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw_y[i] = f.tw_y[i];
+    for (int i = threadIdx.x; i <= Kz; i += blockDim.x) tw_z[i] = f.tw_z[i];
+    const int x = x0 + blockIdx.x, gam = blockIdx.y;
+    C *plane = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz;     // same bytes in both layouts
+    __syncthreads();
+    constexpr int RW = 256 / LZ;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r0 = warp * RW; r0 < Ny; r0 += nw * RW) {
+        const int nr = min(RW, Ny - r0);
+        for (int e = lane; e < nr * Kz; e += 32) {            // packed row element m of row r0 + e / Kz
+            const int y = e / Kz, m = e - y * Kz;
+            buf[(r0 + y) * pitch + m] = plane[(long long)(r0 + y) * Kz + m];
+        }
+        __syncwarp();
+        fft_rows_warp<C, LZ>(buf + (long)r0 * pitch, nr, pitch, tw_h, -1, lane);
+        r2c_rows(buf + (long)r0 * pitch, nr, Kz, pitch, tw_z, f.dKz1h, lane, 32, true);
+        __syncwarp();
+    }
+    __syncthreads();
+    fft_smem<C, MaxC<float>::v>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, -1);
+    for (int k = threadIdx.x; k <= Ny / 2; k += blockDim.x) {     // split the real columns
+        const int k2 = k == 0 ? 0 : Ny - k;
+        const C P = buf[k * pitch], Q = buf[k2 * pitch];
+        buf[k * pitch] = cscale(cadd(P, cconj(Q)), 0.5f);
+        buf[k * pitch + Kz] = cscale(cmuli(csub(P, cconj(Q)), -1), 0.5f);
+        if (k2 != k) {
+            buf[k2 * pitch] = cscale(cadd(Q, cconj(P)), 0.5f);
+            buf[k2 * pitch + Kz] = cscale(cmuli(csub(Q, cconj(P)), -1), 0.5f);
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < Ny * Kz; idx += blockDim.x) {
+        const int y = idx / Kz, k = idx - y * Kz;
+        plane[idx] = buf[y * pitch + k];
+    }
+    C *dn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny;
+    for (int y = threadIdx.x; y < Ny; y += blockDim.x) dn[y] = buf[y * pitch + Kz];
+}
+
+template <int LZ>
+__global__ void __launch_bounds__(kThreadsPlane, RISM_MINBLOCKS_F32) k_fft_inv(Fields<float> f, int x0) {
+    typedef float2 C;
+    if (f.ctrl->status != kRunning) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *buf = reinterpret_cast<C *>(smraw);
+    const int Ny = f.Ny, Kz = LZ, pitch = f.pitch;
+    C *tw_h = buf + (long)Ny * pitch;
+    C *tw_y = tw_h + Kz;
+    C *tw_z = tw_y + Ny;
+    for (int i = threadIdx.x; i < Kz; i += blockDim.x) tw_h[i] = f.tw_h[i];
+    for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw_y[i] = f.tw_y[i];
+    for (int i = threadIdx.x; i <= Kz; i += blockDim.x) tw_z[i] = f.tw_z[i];
+    const int x = x0 + blockIdx.x, gam = blockIdx.y;
+    C *plane = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz;
+    for (int idx = threadIdx.x; idx < Ny * Kz; idx += blockDim.x) {
+        const int y = idx / Kz, k = idx - y * Kz;
+        buf[y * pitch + k] = plane[idx];
+    }
+    const C *sn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny;
+    for (int y = threadIdx.x; y < Ny; y += blockDim.x) buf[y * pitch + Kz] = sn[y];
+    __syncthreads();
+    for (int y = threadIdx.x; y < Ny; y += blockDim.x) {           // real columns as one
+        const C A0 = buf[y * pitch], B0 = buf[y * pitch + Kz];
+        buf[y * pitch] = cmk(A0.x - B0.y, A0.y + B0.x);
+    }
+    __syncthreads();
+    fft_smem<C, MaxC<float>::v>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, +1);
+    constexpr int RW = 256 / LZ;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r0 = warp * RW; r0 < Ny; r0 += nw * RW) {
+        const int nr = min(RW, Ny - r0);
+        c2r_rows(buf + (long)r0 * pitch, nr, Kz, pitch, tw_z, f.dKz1h, lane, 32, true);
+        __syncwarp();
+        fft_rows_warp<C, LZ>(buf + (long)r0 * pitch, nr, pitch, tw_h, +1, lane);
+        for (int e = lane; e < nr * Kz; e += 32) {
+            const int y = e / Kz, m = e - y * Kz;
+            plane[(long long)(r0 + y) * Kz + m] = buf[(r0 + y) * pitch + m];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 template <typename T> size_t plane_smem_bytes(const Fields<T> &f) {
     typedef typename Cx<T>::type C;
@@ -2007,6 +2263,15 @@ template <typename T> cudaError_t prepare_kernels(const Fields<T> &f) {
         default: e = prepare_planes<T, 0>(pl); break;
     }
     if (e == cudaSuccess) e = set_smem(k_ypencil<T>, f.nyc > 1 ? ypencil_smem_bytes(f) : 0);
+    if (e == cudaSuccess && split_planes(f)) {
+        if (f.Kz == 64) {
+            e = set_smem(k_fft_fwd<64>, pl);
+            if (e == cudaSuccess) e = set_smem(k_fft_inv<64>, pl);
+        } else {
+            e = set_smem(k_fft_fwd<128>, pl);
+            if (e == cudaSuccess) e = set_smem(k_fft_inv<128>, pl);
+        }
+    }
     if (e != cudaSuccess) return e;
     switch (f.nv) {
         case 1: return set_smem(k_pencil<T, 1>, pe);
@@ -2018,6 +2283,45 @@ template <typename T> cudaError_t prepare_kernels(const Fields<T> &f) {
         case 7: return set_smem(k_pencil<T, 7>, pe);
         case 8: return set_smem(k_pencil<T, 8>, pe);
         default: return cudaErrorInvalidValue;
+    }
+}
+
+// Split plane passes (see above): FP32, whole planes, integer grid, Nz/2 in {64, 128}.
+template <typename T> bool split_planes(const Fields<T> &f) {
+    return f.split && sizeof(T) == 4 && f.nyc == 1 && !f.half && (f.Kz == 64 || f.Kz == 128) && f.Nx >= 2;
+}
+
+// Element-kernel blocks per site for one half of the planes (about 4 blocks per SM).
+inline int split_elem_blocks(int nv) { return (kSplitBlocks + nv - 1) / nv; }
+
+template <typename T>
+cudaError_t launch_split(const Fields<T> &f, int which, int x0, int x1, int part0, cudaStream_t s) {
+    if constexpr (sizeof(T) != 4) {
+        return cudaErrorInvalidValue;
+    } else {
+        const dim3 eg(split_elem_blocks(f.nv), f.nv), pg(x1 - x0, f.nv);
+        const size_t sm = plane_smem_bytes(f);
+        switch (which) {
+            case 0:
+                if (f.M <= 5) k_fwd_elem<5><<<eg, 256, 0, s>>>(f, x0, x1);
+                else if (f.M <= 8) k_fwd_elem<8><<<eg, 256, 0, s>>>(f, x0, x1);
+                else k_fwd_elem<kMaxHist><<<eg, 256, 0, s>>>(f, x0, x1);
+                break;
+            case 1:
+                if (f.Kz == 64) k_fft_fwd<64><<<pg, kThreadsPlane, sm, s>>>(f, x0);
+                else k_fft_fwd<128><<<pg, kThreadsPlane, sm, s>>>(f, x0);
+                break;
+            case 2:
+                if (f.Kz == 64) k_fft_inv<64><<<pg, kThreadsPlane, sm, s>>>(f, x0);
+                else k_fft_inv<128><<<pg, kThreadsPlane, sm, s>>>(f, x0);
+                break;
+            default:
+                if (f.M <= 5) k_inv_elem<4><<<eg, 256, 0, s>>>(f, x0, x1, part0, f.nparts);
+                else if (f.M <= 8) k_inv_elem<8><<<eg, 256, 0, s>>>(f, x0, x1, part0, f.nparts);
+                else k_inv_elem<kMaxHist><<<eg, 256, 0, s>>>(f, x0, x1, part0, f.nparts);
+                break;
+        }
+        return cudaGetLastError();
     }
 }
 
@@ -2080,7 +2384,7 @@ template <typename T> cudaError_t launch_pencil(const Fields<T> &f, cudaStream_t
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_mdiis(const Fields<T> &f, cudaStream_t s) {
-    k_mdiis<<<1, kThreadsMdiis, 0, s>>>(f.ctrl, f.partials, f.nv * f.Nx * f.nyc);
+    k_mdiis<<<1, kThreadsMdiis, 0, s>>>(f.ctrl, f.partials, f.nparts);
     return cudaGetLastError();
 }
 template <typename T>
@@ -2155,6 +2459,8 @@ cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sf
                                                 const double *, const double *, const double *, \
                                                 const double *, double *, double *, cudaStream_t);    \
     template cudaError_t launch_guess_crop<T>(const Fields<T> &, int, int, const int *, int, float *,  \
-                                              const float *, cudaStream_t);
+                                              const float *, cudaStream_t);                        \
+    template bool split_planes<T>(const Fields<T> &);                                            \
+    template cudaError_t launch_split<T>(const Fields<T> &, int, int, int, int, cudaStream_t);
 
 }  // namespace rism
