@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--cpu-sample-iters", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--inflight", type=int, default=8, help="batch64: jobs in flight")
+    p.add_argument("--split-passes", action="store_true",
+                   help="run the plane passes as split element/transform kernels")
     p.add_argument("--no-kernel-events", action="store_true",
                    help="time the solves without per-kernel CUDA events (no roofline)")
     return p.parse_args()
@@ -263,7 +265,7 @@ def run_ours(args):
     # per-kernel CUDA events on the first iteration of every 8-iteration graph (a sample
     # spread over the whole timed region; every-iteration events cost ~5 % of the time)
     S = capi.Solver(solv, grid, precision=args.precision, mdiis_nvec=w["mdiis_nvec"],
-                    timing=False if args.no_kernel_events else "sampled")
+                    timing=False if args.no_kernel_events else "sampled", split_passes=args.split_passes)
 
     def step():
         S.set_solute(solute["xyz"], solute["q"], solute["sigma"], solute["eps"])

@@ -545,6 +545,14 @@ __device__ __forceinline__ void c2r_rows_half(C *rows, int nr, int yg, int Kz, i
     }
 }
 
+// Asynchronous 8-byte global -> shared copy (no register staging: every copy of a loop is
+// in flight at once); cp_async_wait() waits for the calling thread's copies.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // ------------------------------------------------------------------ pass 1: plane_fwd
 // Per-launch values of the update and closure, shared by the element loops.
 template <typename T, int MAXH>
@@ -800,8 +808,13 @@ k_pencil(Fields<T> f) {
     for (int idx = threadIdx.x; idx < nload; idx += blockDim.x) {
         const int rest = fdiv(idx, f.dW), c = idx - rest * W;
         const int a = fdiv(rest, f.dNx), xx = rest - a * Nx;
-        if (c < ncol) buf[(a * W + c) * pp + xx] = src_base[a * site_stride + xx * xstride + col_base + c];
+        if (c < ncol) {
+            const C *g = &src_base[a * site_stride + xx * xstride + col_base + c];
+            if (sizeof(T) == 4) cp_async8(&buf[(a * W + c) * pp + xx], g);   // in flight together
+            else buf[(a * W + c) * pp + xx] = *g;
+        }
     }
+    if (sizeof(T) == 4) cp_async_wait();
     __syncthreads();
     fft_smem<C, MaxC<T>::v>(buf, f.px, 1, NV * W, pp, f.chunk_x, tw_x, -1);
     // contraction (Eq. 13 with Eq. 32): E_g = sum_a D_a A_ag(|k|) [+ Psi A_{nv,g} before the
@@ -1070,13 +1083,25 @@ k_plane_inv(Fields<T> f) {
     const C phx = half ? f.tw_xs[x] : cmk((T)1, (T)0);
 
     const C *src = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz + (long long)y0 * Kz;
-    for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
-        const int y = fdiv(idx, f.dKz), k = idx - y * Kz;
-        buf[y * pitch + k] = src[idx];
-    }
-    if (!half) {
-        const C *sn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny + y0;
-        for (int y = threadIdx.x; y < nyb; y += blockDim.x) buf[y * pitch + Kz] = sn[y];
+    if (sizeof(T) == 4) {                     // 8-byte elements: asynchronous copies
+        for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
+            const int y = fdiv(idx, f.dKz), k = idx - y * Kz;
+            cp_async8(&buf[y * pitch + k], &src[idx]);
+        }
+        if (!half) {
+            const C *sn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny + y0;
+            for (int y = threadIdx.x; y < nyb; y += blockDim.x) cp_async8(&buf[y * pitch + Kz], &sn[y]);
+        }
+        cp_async_wait();
+    } else {
+        for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
+            const int y = fdiv(idx, f.dKz), k = idx - y * Kz;
+            buf[y * pitch + k] = src[idx];
+        }
+        if (!half) {
+            const C *sn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny + y0;
+            for (int y = threadIdx.x; y < nyb; y += blockDim.x) buf[y * pitch + Kz] = sn[y];
+        }
     }
     __syncthreads();
     if (nyc == 1 && half) {
@@ -2135,8 +2160,9 @@ __global__ void __launch_bounds__(kThreadsPlane, RISM_MINBLOCKS_F32) k_fft_fwd(F
         const int nr = min(RW, Ny - r0);
         for (int e = lane; e < nr * Kz; e += 32) {            // packed row element m of row r0 + e / Kz
             const int y = e / Kz, m = e - y * Kz;
-            buf[(r0 + y) * pitch + m] = plane[(long long)(r0 + y) * Kz + m];
+            cp_async8(&buf[(r0 + y) * pitch + m], &plane[(long long)(r0 + y) * Kz + m]);
         }
+        cp_async_wait();
         __syncwarp();
         fft_rows_warp<C, LZ>(buf + (long)r0 * pitch, nr, pitch, tw_h, -1, lane);
         r2c_rows(buf + (long)r0 * pitch, nr, Kz, pitch, tw_z, f.dKz1h, lane, 32, true);
@@ -2180,10 +2206,11 @@ __global__ void __launch_bounds__(kThreadsPlane, RISM_MINBLOCKS_F32) k_fft_inv(F
     C *plane = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz;
     for (int idx = threadIdx.x; idx < Ny * Kz; idx += blockDim.x) {
         const int y = idx / Kz, k = idx - y * Kz;
-        buf[y * pitch + k] = plane[idx];
+        cp_async8(&buf[y * pitch + k], &plane[idx]);
     }
     const C *sn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny;
-    for (int y = threadIdx.x; y < Ny; y += blockDim.x) buf[y * pitch + Kz] = sn[y];
+    for (int y = threadIdx.x; y < Ny; y += blockDim.x) cp_async8(&buf[y * pitch + Kz], &sn[y]);
+    cp_async_wait();
     __syncthreads();
     for (int y = threadIdx.x; y < Ny; y += blockDim.x) {           // real columns as one
         const C A0 = buf[y * pitch], B0 = buf[y * pitch + Kz];
