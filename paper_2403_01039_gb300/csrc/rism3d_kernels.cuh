@@ -2281,24 +2281,33 @@ template <typename T, int LZ> cudaError_t prepare_planes(size_t pl) {
     return e;
 }
 
-template <typename T> cudaError_t prepare_kernels(const Fields<T> &f) {
-    const size_t pl = plane_smem_bytes(f), pe = pencil_smem_bytes(f);
+// The plane kernels (fused and split) are compiled in their own translation units.
+template <typename T> cudaError_t prepare_plane_kernels(const Fields<T> &f) {
+    const size_t pl = plane_smem_bytes(f);
     cudaError_t e;
     switch (plane_lz(f)) {
         case 64: e = prepare_planes<T, sizeof(T) == 4 ? 64 : 0>(pl); break;
         case 128: e = prepare_planes<T, sizeof(T) == 4 ? 128 : 0>(pl); break;
         default: e = prepare_planes<T, 0>(pl); break;
     }
-    if (e == cudaSuccess) e = set_smem(k_ypencil<T>, f.nyc > 1 ? ypencil_smem_bytes(f) : 0);
     if (e == cudaSuccess && split_planes(f)) {
-        if (f.Kz == 64) {
-            e = set_smem(k_fft_fwd<64>, pl);
-            if (e == cudaSuccess) e = set_smem(k_fft_inv<64>, pl);
-        } else {
-            e = set_smem(k_fft_fwd<128>, pl);
-            if (e == cudaSuccess) e = set_smem(k_fft_inv<128>, pl);
+        if constexpr (sizeof(T) == 4) {
+            if (f.Kz == 64) {
+                e = set_smem(k_fft_fwd<64>, pl);
+                if (e == cudaSuccess) e = set_smem(k_fft_inv<64>, pl);
+            } else {
+                e = set_smem(k_fft_fwd<128>, pl);
+                if (e == cudaSuccess) e = set_smem(k_fft_inv<128>, pl);
+            }
         }
     }
+    return e;
+}
+
+template <typename T> cudaError_t prepare_kernels(const Fields<T> &f) {
+    const size_t pe = pencil_smem_bytes(f);
+    cudaError_t e = prepare_plane_kernels(f);
+    if (e == cudaSuccess) e = set_smem(k_ypencil<T>, f.nyc > 1 ? ypencil_smem_bytes(f) : 0);
     if (e != cudaSuccess) return e;
     switch (f.nv) {
         case 1: return set_smem(k_pencil<T, 1>, pe);
@@ -2460,12 +2469,24 @@ cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sf
     return cudaGetLastError();
 }
 
-#define RISM_INSTANTIATE(T)                                                                     \
+// Explicit instantiations, in two groups compiled in separate translation units: the plane
+// kernels (fused and split) and everything else.
+#define RISM_INSTANTIATE_PLANES(T)                                                              \
     template size_t plane_smem_bytes<T>(const Fields<T> &);                                      \
-    template cudaError_t prepare_kernels<T>(const Fields<T> &);                                  \
-    template size_t pencil_smem_bytes<T>(const Fields<T> &);                                     \
+    template cudaError_t prepare_plane_kernels<T>(const Fields<T> &);                            \
     template cudaError_t launch_plane_fwd<T>(const Fields<T> &, cudaStream_t);                   \
     template cudaError_t launch_plane_inv<T>(const Fields<T> &, cudaStream_t);                   \
+    template bool split_planes<T>(const Fields<T> &);                                            \
+    template cudaError_t launch_split<T>(const Fields<T> &, int, int, int, int, cudaStream_t);
+
+#define RISM_EXTERN_PLANES(T)                                                                   \
+    extern template size_t plane_smem_bytes<T>(const Fields<T> &);                               \
+    extern template cudaError_t prepare_plane_kernels<T>(const Fields<T> &);                     \
+    extern template bool split_planes<T>(const Fields<T> &);
+
+#define RISM_INSTANTIATE_REST(T)                                                                \
+    template cudaError_t prepare_kernels<T>(const Fields<T> &);                                  \
+    template size_t pencil_smem_bytes<T>(const Fields<T> &);                                     \
     template cudaError_t launch_ypencil<T>(const Fields<T> &, int, cudaStream_t);                \
     template cudaError_t launch_pencil<T>(const Fields<T> &, cudaStream_t);                      \
     template cudaError_t launch_mdiis<T>(const Fields<T> &, cudaStream_t);                       \
@@ -2486,8 +2507,6 @@ cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sf
                                                 const double *, const double *, const double *, \
                                                 const double *, double *, double *, cudaStream_t);    \
     template cudaError_t launch_guess_crop<T>(const Fields<T> &, int, int, const int *, int, float *,  \
-                                              const float *, cudaStream_t);                        \
-    template bool split_planes<T>(const Fields<T> &);                                            \
-    template cudaError_t launch_split<T>(const Fields<T> &, int, int, int, int, cudaStream_t);
+                                              const float *, cudaStream_t);
 
 }  // namespace rism
