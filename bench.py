@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -91,7 +92,7 @@ class ClockSampler:
 
     def start(self):
         try:
-            out_dir = os.path.join(ROOT, "gpurun_out")
+            out_dir = os.environ.get("RISM_BENCH_OUT", tempfile.gettempdir())
             os.makedirs(out_dir, exist_ok=True)
             self.path = os.path.join(out_dir, "bench_clocks_rank%d.csv" % self.index)
             self.fh = open(self.path, "w")
