@@ -24,13 +24,13 @@ def _declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names.update(re.findall(r"\b((?:rism3d|rism1d)_[a-z0-9_]+)\s*\(", src))
+        names.update(re.findall(r"\b((?:rism3d|rism1d|unet3d)_[a-z0-9_]+)\s*\(", src))
     return sorted(names)
 
 
 def test_exports_every_declared_symbol(lib):
     names = _declared()
-    assert "rism3d_solve" in names and len(names) >= 12
+    assert "rism3d_solve" in names and "unet3d_forward" in names and len(names) >= 30
     for n in names:
         assert hasattr(lib, n), n
 
@@ -118,3 +118,42 @@ def test_product_xrism_thermo_matches_oracle(lib):
     assert abs(th["pressure"] - float(ref["pressure"])) <= 1e-7 * abs(float(ref["pressure"]))
     assert abs(th["kT_chi_T"] - float(ref["kT_chi_T"])) <= 1e-6 * float(ref["kT_chi_T"])
     assert np.max(np.abs(th["c"][:, :, ::8] - ref["c_every8"])) <= 1e-6
+
+
+def test_new_entry_points_validate_without_a_device(lib):
+    """Batch, tuning, learned-guess and network entry points reject bad arguments before
+    any CUDA call."""
+    from paper_2403_01039_gb300 import capi
+    P = ctypes.POINTER
+    # batch: null list with jobs, bad max_inflight; an empty list is fine
+    assert lib.rism3d_solve_batch(None, 2, 4, 0.0) == 1
+    jobs = (capi.BatchJob * 1)()
+    assert lib.rism3d_solve_batch(jobs, 1, 0, 0.0) == 1
+    assert lib.rism3d_solve_batch(jobs, 1, 4, 0.0) == 1          # job without a context
+    assert jobs[0].status == 4                                     # ESTATE: never started
+    assert lib.rism3d_solve_batch(jobs, 0, 4, 0.0) == 0
+    # null contexts
+    w, ms = ctypes.c_int(), ctypes.c_double()
+    assert lib.rism3d_tune(None, ctypes.byref(w), ctypes.byref(ms)) == 1
+    corner = (ctypes.c_int * 3)(0, 0, 0)
+    assert lib.rism3d_guess_input(None, corner, 8, None) == 1
+    assert lib.rism3d_set_guess_crop(None, corner, 8, None) == 1
+    assert lib.rism3d_get_pmv(None, 1.0, ctypes.byref(ms), None) == 1
+    assert lib.rism3d_get_sfe_gradient(None, None) == 1
+    # network: sizes are checked before any allocation
+    net = ctypes.c_void_p()
+    assert lib.unet3d_create(5, 5, 30, 16, 32, 64, None, ctypes.byref(net)) == 1     # crop % 4
+    assert lib.unet3d_create(0, 5, 32, 16, 32, 64, None, ctypes.byref(net)) == 1
+    assert not net.value
+    assert lib.unet3d_param_count(None) == 0
+
+
+def test_option_validation(lib):
+    """kgrid, split_passes and timing outside their ranges are rejected by the size query."""
+    sv, grid, opt = _inputs()
+    for field, bad in (("kgrid", 2), ("split_passes", 3), ("timing", 5)):
+        o = type(opt)()
+        ctypes.memmove(ctypes.byref(o), ctypes.byref(opt), ctypes.sizeof(opt))
+        setattr(o, field, bad)
+        st, _ = _ws(lib, sv, grid, o)
+        assert st == 1, field
