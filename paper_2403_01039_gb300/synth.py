@@ -90,12 +90,17 @@ def cubic_grid(n, spacing):
 #               128^3 at 0.5 A, KH and PSE-3, FP32 and FP64, MDIIS 5.
 # globule2000_256: 2000-atom globule (radius 16 A, seed 3001, net +8) in water + NaCl,
 #               256^3 at 0.375 A, KH, MDIIS 10.
+# globule12877_512: 12877 atoms (radius 32 A, seed 5001, net 0) in water + NaCl, 512^3 at
+#               0.5 A, KH, MDIIS 10.
 WORKLOADS = {
     "sphere_32": dict(n=32, spacing=0.5, solvent="water3", mdiis_nvec=5),
     "solute50_128": dict(n=128, spacing=0.5, solvent="water_nacl", mdiis_nvec=5,
                          atoms=50, radius=10.0, seed=2001, net_charge=0.0),
     "globule2000_256": dict(n=256, spacing=0.375, solvent="water_nacl", mdiis_nvec=10,
                             atoms=2000, radius=16.0, seed=3001, net_charge=8.0),
+    # the paper's grid (512^3 over a 256 A box) and atom count (12 877), net charge 0
+    "globule12877_512": dict(n=512, spacing=0.5, solvent="water_nacl", mdiis_nvec=10,
+                             atoms=12877, radius=32.0, seed=5001, net_charge=0.0),
 }
 
 
