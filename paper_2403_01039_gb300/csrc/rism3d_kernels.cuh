@@ -1740,28 +1740,25 @@ cudaError_t launch_guess_crop(const Fields<T> &f, int mode, int slot, const int 
 }
 
 // ------------------------------------------------------------------ small helpers
-// Step 1: t = f, i.e. tau = 0.
+// Step 1: t = f, i.e. tau = 0 in the current-iterate field (the ring slot argument of the
+// launcher only names where the next residual goes).
 template <typename T>
-__global__ void k_init_guess(Fields<T> f, int slot) {
+__global__ void k_init_guess(Fields<T> f) {
     const long long n = (long long)f.nv * f.G;
-    const long long base = (long long)slot * n;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         f.Tc[i] = (T)0;
-    (void)base;
 }
 
 // tau = t - beta q phi from a caller field t (FP64), into ring slot `slot`.
 template <typename T>
-__global__ void k_guess_from_t(Fields<T> f, int slot, const double *src) {
+__global__ void k_guess_from_t(Fields<T> f, const double *src) {
     const long long n = (long long)f.nv * f.G;
-    const long long base = (long long)slot * n;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int g = (int)(i / f.G);
         const long long p = i - (long long)g * f.G;
         f.Tc[i] = (T)(src[i] - f.bq[g] * (double)f.phi[p]);
-        (void)base;
     }
 }
 
@@ -1815,9 +1812,7 @@ __global__ void __launch_bounds__(256)
 k_sfe(Fields<T> f, int slot, int kind, int order, int sfe_kind, int sfe_order, double *partials) {
     __shared__ double red[32];
     const int g = blockIdx.y;
-    const long long ring = (long long)f.nv * f.G;
     const T *tt = f.Tc + (long long)g * f.G;
-    (void)ring;
     const T *wp = f.w + (long long)g * f.G;
     const double bq = f.bq[g];
     double acc = 0.0;
@@ -2446,13 +2441,13 @@ cudaError_t launch_longrange(const Fields<T> &f, const double *atoms, int n_atom
     }
     return cudaGetLastError();
 }
-template <typename T> cudaError_t launch_init_guess(const Fields<T> &f, int slot, cudaStream_t s) {
-    k_init_guess<T><<<152 * 8, 256, 0, s>>>(f, slot);
+template <typename T> cudaError_t launch_init_guess(const Fields<T> &f, int, cudaStream_t s) {
+    k_init_guess<T><<<152 * 8, 256, 0, s>>>(f);
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_guess_from_t(const Fields<T> &f, int slot, const double *src, cudaStream_t s) {
-    k_guess_from_t<T><<<152 * 8, 256, 0, s>>>(f, slot, src);
+cudaError_t launch_guess_from_t(const Fields<T> &f, int, const double *src, cudaStream_t s) {
+    k_guess_from_t<T><<<152 * 8, 256, 0, s>>>(f, src);
     return cudaGetLastError();
 }
 template <typename T>
