@@ -6,12 +6,17 @@
 //   pencil     : FFT along x -> 3D-RISM contraction h~_g = sum_a c~_a X_ag(|k|) with
 //                c~ = c~^sr - f~ (Eqs. 13, 32) -> inverse FFT along x
 //   plane_inv  : inverse FFT along y and complex-to-real along z -> residual
-//                R = h + 1 - g (Eq. 33) -> FP64 Gram-row partials <R, R_i> and sum R^2
+//                R = h + 1 - g (Eq. 33) -> stored pair (Y = tau + eta R, R) -> Gram-row
+//                partials <R, R_i> and sum R^2 (Dot2 in FP32, FP64 across threads)
 //   mdiis      : reduce the partials, update the Gram matrix, solve the bordered MDIIS
 //                system (Eq. 40), convergence test on the RMS residual (Eq. 41 read as RMS)
 //
-// Every field stays in HBM between launches; the solver state lives in a device struct
-// (Ctrl) so that one captured CUDA graph replays any number of iterations.
+// Planes too large for shared memory take row chunks plus y-pencil passes (k_ypencil); the
+// split option runs each plane pass as a streaming element kernel and a transform kernel
+// on two graph branches. Every field stays in HBM between launches; the solver state lives
+// in a device struct (Ctrl) so that one captured CUDA graph replays any number of
+// iterations. The shared-memory transforms are compile-time radix-8 passes for power-of-two
+// lengths 16-256 and mixed-radix (2, 3, 4, 5, 8) Stockham stages otherwise.
 //
 // The iterate is stored as tau = t - f (f = beta q phi of Eq. 29) and the potential as
 // w = f - beta*u, so that d = -beta*u + t = w + tau and c^sr = g - 1 - t + f = g - 1 - tau
