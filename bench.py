@@ -157,6 +157,27 @@ def ncu_traffic(kernel, workload):
     return e.get("dram_bytes_per_launch")
 
 
+class _HostClock:
+    """Wall and process CPU time (all threads) of a host region: their ratio is the number
+    of host cores the oracle kept busy, which numpy's BLAS may make more than one."""
+
+    def __enter__(self):
+        self.w0, self.c0 = time.perf_counter(), time.process_time()
+        return self
+
+    def __exit__(self, *exc):
+        self.wall = time.perf_counter() - self.w0
+        self.cpu = time.process_time() - self.c0
+        return False
+
+
+def _cores_used(*clocks):
+    wall = sum(c.wall for c in clocks)
+    cpu = sum(c.cpu for c in clocks)
+    ratio = cpu / wall if wall > 0 else 1.0
+    return max(1, int(round(ratio))), ratio
+
+
 def cpu_baseline(args, w, solv, grid, solute, n_iter_gpu):
     """The FP64 oracle as it stands, timed on a bounded sample of the same workload: the
     once-per-solute setup (direct potential sums, long-range fields, X on the grid) plus
@@ -165,14 +186,15 @@ def cpu_baseline(args, w, solv, grid, solute, n_iter_gpu):
     import numpy as np
     from oracle import rism3d as orc, closure as cl
     kinds = {"kh": cl.KH, "pse": cl.PSE, "hnc": cl.HNC}
-    t0 = time.perf_counter()
-    P = orc.Problem(solv, grid, solute)
-    t_setup = time.perf_counter() - t0
+    with _HostClock() as cs:
+        P = orc.Problem(solv, grid, solute)
+    t_setup = cs.wall
     n = args.cpu_sample_iters
-    t0 = time.perf_counter()
-    orc.solve(P, kinds[args.closure], args.pse_order, tol=1e-300, max_iter=n,
-              mdiis_nvec=w["mdiis_nvec"])
-    t_iter = (time.perf_counter() - t0) / n
+    with _HostClock() as ci:
+        orc.solve(P, kinds[args.closure], args.pse_order, tol=1e-300, max_iter=n,
+                  mdiis_nvec=w["mdiis_nvec"])
+    t_iter = ci.wall / n
+    cores, ratio = _cores_used(cs, ci)
     ref = os.path.join(ROOT, "tests", "golden", "%s_reference.npz" % args.workload)
     key = "%s_%g_iterations" % ({"kh": "kh", "pse": "pse3"}.get(args.closure, args.closure), args.tol)
     n_full, src = n_iter_gpu, "the GPU solve's iteration count"
@@ -181,10 +203,11 @@ def cpu_baseline(args, w, solv, grid, solute, n_iter_gpu):
         if key in d:
             n_full, src = int(d[key]), "the oracle's own iteration count (stored reference)"
     t_solve = t_setup + n_full * t_iter
-    return dict(value=1.0 / t_solve, unit="solves/s", cores=1, kind="oracle",
-                sample="oracle setup (%.1f s) + %d iterations (%.2f s each) of %s on 1 host "
-                       "thread, extrapolated to %d iterations (%s)"
-                       % (t_setup, n, t_iter, args.workload, n_full, src),
+    return dict(value=1.0 / t_solve, unit="solves/s", cores=cores, kind="oracle",
+                sample="oracle setup (%.1f s) + %d iterations (%.2f s each) of %s, host CPU "
+                       "time / wall time %.2f (%d cores available), extrapolated to %d "
+                       "iterations (%s)"
+                       % (t_setup, n, t_iter, args.workload, ratio, os.cpu_count() or 0, n_full, src),
                 site_gridpoint_iters_per_s=len(solv["q"]) * float(np.prod(grid["n"])) / t_iter)
 
 
@@ -206,22 +229,24 @@ def run_reference(args):
     grid = synth.cubic_grid(w["n"], w["spacing"])
     solute = synth.workload_solute(args.workload)
     kinds = {"kh": cl.KH, "pse": cl.PSE, "hnc": cl.HNC}
-    t0 = time.perf_counter()
-    P = orc.Problem(solv, grid, solute)
-    t_setup = time.perf_counter() - t0
+    with _HostClock() as cs:
+        P = orc.Problem(solv, grid, solute)
+    t_setup = cs.wall
     # one step = one iteration of steps 2-6 (a bounded sample of the solve)
     orc.solve(P, kinds[args.closure], args.pse_order, tol=1e-300, max_iter=args.warmup,
               mdiis_nvec=w["mdiis_nvec"])
-    t0 = time.perf_counter()
-    orc.solve(P, kinds[args.closure], args.pse_order, tol=1e-300, max_iter=args.steps,
-              mdiis_nvec=w["mdiis_nvec"])
-    t_iter = (time.perf_counter() - t0) / args.steps
+    with _HostClock() as ci:
+        orc.solve(P, kinds[args.closure], args.pse_order, tol=1e-300, max_iter=args.steps,
+                  mdiis_nvec=w["mdiis_nvec"])
+    t_iter = ci.wall / args.steps
+    cores, ratio = _cores_used(cs, ci)
     ref = os.path.join(ROOT, "tests", "golden", "%s_reference.npz" % args.workload)
     key = "%s_%g_iterations" % ({"kh": "kh", "pse": "pse3"}.get(args.closure, args.closure), args.tol)
     n_full = int(np.load(ref)[key]) if os.path.exists(ref) and key in np.load(ref) else 127
     value = 1.0 / (t_setup + n_full * t_iter)
-    sample = ("oracle setup %.1f s + %d timed iterations (%.2f s each) on 1 host thread, "
-              "extrapolated to the %d iterations of a converged solve" % (t_setup, args.steps, t_iter, n_full))
+    sample = ("oracle setup %.1f s + %d timed iterations (%.2f s each), host CPU time / wall "
+              "time %.2f (%d cores available), extrapolated to the %d iterations of a converged "
+              "solve" % (t_setup, args.steps, t_iter, ratio, os.cpu_count() or 0, n_full))
     line = dict(impl="reference", metric=METRIC, value=value, unit="solves/s", n_gpus=args.gpus,
                 steps=args.steps, warmup=args.warmup, ms_per_step=t_iter * 1e3, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
@@ -229,7 +254,7 @@ def run_reference(args):
                             sites=len(sites["q"]), atoms=len(solute["q"]), closure=args.closure,
                             tol=args.tol, mdiis=w["mdiis_nvec"]),
                 site_gridpoint_iters_per_s=len(sites["q"]) * float(np.prod(grid["n"])) / t_iter,
-                cpu_baseline=dict(value=value, unit="solves/s", cores=1, kind="oracle", sample=sample),
+                cpu_baseline=dict(value=value, unit="solves/s", cores=cores, kind="oracle", sample=sample),
                 e2e=dict(value=value, unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
