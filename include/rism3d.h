@@ -178,7 +178,10 @@ rism3d_status rism3d_create(const rism3d_solvent *solvent, const rism3d_grid *gr
  * mixing, r^2 floored at 1e-8 A^2, beta*u capped above at 1e4), the long-range field phi
  * (Eq. 29) and its analytic transform (Eq. 30, zero at k = 0 and on Nyquist planes), and
  * sets the initial guess t = f (step 1). xyz is [n_atoms][3], q/sigma/eps are [n_atoms],
- * all host arrays. 1 <= n_atoms <= max_atoms. */
+ * all host arrays. 1 <= n_atoms <= max_atoms. EINVAL (a bad count, a null array, a
+ * non-finite position or charge, a negative sigma or eps) leaves the previous solute in
+ * place; a CUDA error after the checks leaves the context without a solute (ESTATE from
+ * the calls that need one until a later rism3d_set_solute succeeds). */
 rism3d_status rism3d_set_solute(rism3d_ctx *ctx, int n_atoms, const double *xyz,
                                 const double *q, const double *sigma, const double *eps);
 

@@ -892,9 +892,11 @@ rism3d_status rism3d_set_solute(rism3d_ctx *ctx, int n_atoms, const double *xyz,
     if (!xyz || !q || !sigma || !eps) return fail(ctx, RISM3D_EINVAL, "null solute array");
     DeviceGuard dg(ctx->device);
     const double L[3] = {ctx->Nx * ctx->spacing[0], ctx->Ny * ctx->spacing[1], ctx->Nz * ctx->spacing[2]};
-    ctx->atom_host.assign((size_t)n_atoms * kAtomStride, 0.0);
+    // every atom is checked before anything of the context changes: bad arguments leave the
+    // previous solute in place
+    std::vector<double> atoms((size_t)n_atoms * kAtomStride, 0.0);
     for (int a = 0; a < n_atoms; ++a) {
-        double *at = &ctx->atom_host[(size_t)a * kAtomStride];
+        double *at = &atoms[(size_t)a * kAtomStride];
         for (int d = 0; d < 3; ++d) {
             at[d] = xyz[3 * a + d];
             at[6 + d] = (xyz[3 * a + d] - ctx->origin[d]) / L[d];
@@ -906,6 +908,9 @@ rism3d_status rism3d_set_solute(rism3d_ctx *ctx, int n_atoms, const double *xyz,
         if (!(sigma[a] >= 0.0) || !(eps[a] >= 0.0) || !std::isfinite(q[a]))
             return fail(ctx, RISM3D_EINVAL, "atom %d: sigma, eps must be >= 0 and q finite", a);
     }
+    // from here on the device fields are rewritten: a CUDA error part-way leaves no solute
+    ctx->has_solute = false;
+    ctx->atom_host.swap(atoms);
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->atoms, ctx->atom_host.data(), ctx->atom_host.size() * sizeof(double),
                                   cudaMemcpyHostToDevice, ctx->stream));
     const double amp0 = 4.0 * kPi * kCoulomb * ctx->beta / ctx->dV;
@@ -1221,7 +1226,7 @@ static rism3d_status guess_crop(rism3d_ctx *ctx, int mode, const int *corner, in
     if (!corner || crop < 1 || (mode == 2 ? !in : !out)) return fail(ctx, RISM3D_EINVAL, "bad crop arguments");
     const int N[3] = {ctx->Nx, ctx->Ny, ctx->Nz};
     for (int d = 0; d < 3; ++d)
-        if (corner[d] < 0 || corner[d] + crop > N[d])
+        if (corner[d] < 0 || (long long)corner[d] + crop > N[d])
             return fail(ctx, RISM3D_EINVAL, "crop [%d, %d) outside the grid on axis %d", corner[d], corner[d] + crop, d);
     DeviceGuard dg(ctx->device);
     const int slot = mode == 2 ? 0 : ctx->cur_slot;
