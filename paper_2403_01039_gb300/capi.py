@@ -186,6 +186,17 @@ def default_options():
     return o
 
 
+def _f32_cuda(t, count, name):
+    """Device pointer of a contiguous float32 CUDA tensor of exactly ``count`` values: the
+    kernels behind it read and write that many values, so anything else is refused here."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous float32 CUDA tensor" % name)
+    if t.numel() != count:
+        raise ValueError("%s has %d values, expected %d" % (name, t.numel(), count))
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _check(lib, ctx, st):
     if st != OK:
         raise RismError(st, lib.rism3d_last_error(ctx).decode())
@@ -428,22 +439,25 @@ class Solver:
     def _corner(self, corner):
         return (ctypes.c_int * 3)(*[int(v) for v in corner])
 
+    def _crop_arg(self, t, crop, name):
+        return _f32_cuda(t, self.n_sites * int(crop) ** 3, name)
+
     def guess_input(self, corner, crop, out):
         """Network input tanh(beta u / 4) on the crop into ``out`` (float32 CUDA tensor
         [n_sites, crop, crop, crop])."""
-        _check(self.lib, self.ctx, self.lib.rism3d_guess_input(self.ctx, self._corner(corner), int(crop),
-                                                               ctypes.c_void_p(out.data_ptr())))
+        p = self._crop_arg(out, crop, "out")
+        _check(self.lib, self.ctx, self.lib.rism3d_guess_input(self.ctx, self._corner(corner), int(crop), p))
 
     def guess_target(self, corner, crop, out):
         """The current iterate tau = t - f on the crop into ``out`` (float32 CUDA tensor)."""
-        _check(self.lib, self.ctx, self.lib.rism3d_guess_target(self.ctx, self._corner(corner), int(crop),
-                                                                ctypes.c_void_p(out.data_ptr())))
+        p = self._crop_arg(out, crop, "out")
+        _check(self.lib, self.ctx, self.lib.rism3d_guess_target(self.ctx, self._corner(corner), int(crop), p))
 
     def set_guess_crop(self, corner, crop, tau):
         """Start the next solve from tau on the crop (float32 CUDA tensor) and 0 elsewhere."""
+        p = self._crop_arg(tau, crop, "tau")
         self._sync_torch()
-        _check(self.lib, self.ctx, self.lib.rism3d_set_guess_crop(self.ctx, self._corner(corner), int(crop),
-                                                                  ctypes.c_void_p(tau.data_ptr())))
+        _check(self.lib, self.ctx, self.lib.rism3d_set_guess_crop(self.ctx, self._corner(corner), int(crop), p))
 
     def pmv(self, kT_chi_T):
         """Partial molar volume (Eq. 19, A^3) and the per-site c integrals of the current
@@ -514,7 +528,8 @@ class UNet3D:
 
     def set_params(self, flat):
         a = np.ascontiguousarray(flat, dtype=np.float32)
-        assert a.size == self.n_params
+        if a.size != self.n_params:
+            raise ValueError("parameter vector has %d values, expected %d" % (a.size, self.n_params))
         self._ok(self.lib.unet3d_set_params(self.net, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
 
     def get_params(self):
@@ -528,15 +543,20 @@ class UNet3D:
         return a
 
     def forward(self, x, y):
-        self._ok(self.lib.unet3d_forward(self.net, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr())))
+        px = _f32_cuda(x, self.n_in * self.crop ** 3, "x")
+        py = _f32_cuda(y, self.n_out * self.crop ** 3, "y")
+        self._ok(self.lib.unet3d_forward(self.net, px, py))
 
     def backward(self, gy):
-        self._ok(self.lib.unet3d_backward(self.net, ctypes.c_void_p(gy.data_ptr())))
+        self._ok(self.lib.unet3d_backward(self.net, _f32_cuda(gy, self.n_out * self.crop ** 3, "gy")))
 
     def mse(self, y, target, gy):
+        n = y.numel() if hasattr(y, "numel") else 0
+        py = _f32_cuda(y, n, "y")
+        pt = _f32_cuda(target, n, "target")
+        pg = _f32_cuda(gy, n, "gy")
         loss = ctypes.c_double()
-        self._ok(self.lib.unet3d_mse(self.net, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(target.data_ptr()),
-                                     y.numel(), ctypes.byref(loss), ctypes.c_void_p(gy.data_ptr())))
+        self._ok(self.lib.unet3d_mse(self.net, py, pt, n, ctypes.byref(loss), pg))
         return loss.value
 
     def adam(self, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):

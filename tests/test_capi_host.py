@@ -157,3 +157,13 @@ def test_option_validation(lib):
         setattr(o, field, bad)
         st, _ = _ws(lib, sv, grid, o)
         assert st == 1, field
+
+
+def test_device_tensor_arguments_are_checked_before_the_call():
+    """Crop and network entry points take raw device pointers: the binding refuses host
+    tensors, other dtypes and non-tensors before anything reaches the library."""
+    torch = pytest.importorskip("torch")
+    from paper_2403_01039_gb300 import capi
+    for bad in (torch.zeros(8), torch.zeros(8, dtype=torch.float64), np.zeros(8, dtype=np.float32), None):
+        with pytest.raises(ValueError):
+            capi._f32_cuda(bad, 8, "x")
