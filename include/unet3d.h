@@ -21,7 +21,8 @@
  *
  * Arithmetic: FP32 with FP32 accumulation (direct convolutions over shared-memory tiles).
  * Every array argument is device memory of the current CUDA device unless stated; every
- * call returns 0 on success, else a nonzero code with a message in unet3d_last_error().
+ * call returns 0 on success, else a nonzero code with a message in unet3d_last_error():
+ * 1 bad arguments, 2 allocation failure, 3 a CUDA error, 4 a call out of order.
  * Calls enqueue on the network's stream and return without synchronising unless stated.
  */
 #ifndef UNET3D_PUBLIC_API_H_
@@ -51,7 +52,8 @@ int unet3d_get_params(const unet3d *net, float *host_params);
 int unet3d_forward(unet3d *net, const float *x, float *y);
 
 /* Parameter gradient of a loss with dL/dy = gy [n_out][crop^3] at the last forward's
- * input, written into the network's gradient vector (overwritten, not accumulated). */
+ * input, written into the network's gradient vector (overwritten, not accumulated).
+ * Returns 4 when no forward pass has completed since creation (or the last one failed). */
 int unet3d_backward(unet3d *net, const float *gy);
 
 /* Copy the gradient vector to host memory (synchronous). */

@@ -377,6 +377,7 @@ struct unet3d {
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
     std::vector<float *> bufs;               // every device allocation but the above
     float *x = nullptr;                      // copy of the last input
+    bool have_forward = false;               // activations of a forward pass are stored
     float *cat1 = nullptr, *e1a = nullptr, *p1 = nullptr, *cat2 = nullptr, *e2a = nullptr, *p2 = nullptr;
     float *ma = nullptr, *mid = nullptr, *d2a = nullptr, *dec2 = nullptr, *d1a = nullptr, *dec1 = nullptr;
     // gradients of activations
@@ -545,6 +546,7 @@ int unet3d_get_grads(const unet3d *net, float *host) {
 
 int unet3d_forward(unet3d *net, const float *x, float *y) {
     if (!net || !x || !y) return fail(1, "null argument");
+    net->have_forward = false;
     const int n = net->n, h = n / 2, q = n / 4;
     const long long V = cube(n), V2 = cube(h), V4 = cube(q);
     const int c0 = net->c0, c1 = net->c1, c2 = net->c2;
@@ -569,11 +571,13 @@ int unet3d_forward(unet3d *net, const float *x, float *y) {
     k_conv1<<<grid_for(V), 256, 0, s>>>(net->dec1, c0, V, net->params + net->woff[10], net->params + net->boff[10],
                                          net->n_out, y);
     UNET_TRY(cudaGetLastError());
+    net->have_forward = true;
     return 0;
 }
 
 int unet3d_backward(unet3d *net, const float *gy) {
     if (!net || !gy) return fail(1, "null argument");
+    if (!net->have_forward) return fail(4, "backward before a successful forward");
     const int n = net->n, h = n / 2, q = n / 4;
     const long long V = cube(n), V2 = cube(h), V4 = cube(q);
     const int c0 = net->c0, c1 = net->c1, c2 = net->c2;
