@@ -161,8 +161,22 @@ rism1d_status rism1d_xrism_ex(const rism1d_solvent *sv, const rism1d_options *op
         return fail(RISM1D_EINVAL, "bad MDIIS / charge-step options");
     if (!sv->q || !sv->sigma || !sv->eps || !sv->rho || !sv->species || !sv->coords)
         return fail(RISM1D_EINVAL, "null solvent array");
-    for (int a = 0; a < n; ++a)
+    for (int a = 0; a < n; ++a) {
         if (!(sv->rho[a] > 0.0)) return fail(RISM1D_EINVAL, "rho must be positive");
+        if (!(sv->sigma[a] >= 0.0) || !(sv->eps[a] >= 0.0) || !std::isfinite(sv->q[a]) ||
+            !std::isfinite(sv->sigma[a]) || !std::isfinite(sv->eps[a]))
+            return fail(RISM1D_EINVAL, "site sigma and eps must be finite and >= 0, q finite");
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(sv->coords[3 * a + d])) return fail(RISM1D_EINVAL, "non-finite site position");
+        for (int b = 0; b < a; ++b) {
+            if (sv->species[a] != sv->species[b]) continue;
+            const double dx = sv->coords[3 * a] - sv->coords[3 * b];
+            const double dy = sv->coords[3 * a + 1] - sv->coords[3 * b + 1];
+            const double dz = sv->coords[3 * a + 2] - sv->coords[3 * b + 2];
+            if (!(dx * dx + dy * dy + dz * dz > 0.0))        // omega = sin(kl)/(kl) needs l > 0
+                return fail(RISM1D_EINVAL, "two sites of one molecule at the same position");
+        }
+    }
 
     const int P = N - 1;                     // radial points i = 1..N-1
     const double dr = op->dr, dk = kPi / (N * dr);

@@ -120,6 +120,24 @@ def test_product_xrism_thermo_matches_oracle(lib):
     assert np.max(np.abs(th["c"][:, :, ::8] - ref["c_every8"])) <= 1e-6
 
 
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda s: s["coords"].__setitem__((2, slice(None)), s["coords"][1]), "same position"),
+    (lambda s: s["sigma"].__setitem__(0, -1.0), "sigma"),
+    (lambda s: s["q"].__setitem__(1, np.nan), "q finite"),
+    (lambda s: s["coords"].__setitem__((0, 0), np.inf), "position"),
+])
+def test_product_xrism_validates_sites(lib, mutate, msg):
+    """The host 1D solver refuses sites it cannot represent (coincident sites of one
+    molecule make omega = sin(kl)/(kl) undefined) before it iterates."""
+    from paper_2403_01039_gb300 import capi, synth
+    sv = synth.water_3site()
+    sv = {k: (np.array(v, dtype=np.float64) if k in ("q", "sigma", "eps", "rho", "coords") else v)
+          for k, v in sv.items()}
+    mutate(sv)
+    with pytest.raises(RuntimeError, match=msg):
+        capi.xrism(sv)
+
+
 def test_new_entry_points_validate_without_a_device(lib):
     """Batch, tuning, learned-guess and network entry points reject bad arguments before
     any CUDA call."""
