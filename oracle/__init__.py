@@ -21,6 +21,11 @@ rism3d     the solve procedure (steps 1-7 of the Numerical procedure section,
            Eqs. 13, 31-33, 41) and the SFE sums
 rism1d     Eq. 4 (XRISM for the pure solvent -> susceptibility X of Eq. 8) and the
            single-site solute-solvent RISM of Eq. 8 used to cross-check 3D
+anderson   Eqs. 34-39 (the modified Anderson coefficients with two histories)
+thermo     Eq. 19 (partial molar volume), Eq. 20 (pressure), the second Eq. 21
+           (solvation force as the SFE gradient)
+unet       the learned-guess network (no counterpart in the paper): 3x3x3
+           convolutions, pooling, upsampling, MSE and the chain rule, in FP64
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 except the 1D solvent susceptibility values themselves ("parity unpinned"
