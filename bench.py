@@ -478,6 +478,10 @@ def run_batch(args):
 def main():
     args = parse()
     if args.impl == "reference":
+        from paper_2403_01039_gb300 import synth
+        if args.workload not in synth.WORKLOADS:
+            sys.exit("--impl reference times the oracle on one solve of a single-solute workload "
+                     "(%s); %s has no such form" % (", ".join(sorted(synth.WORKLOADS)), args.workload))
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)
