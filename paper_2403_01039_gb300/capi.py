@@ -157,6 +157,19 @@ def _arr(a):
     return a, a.ctypes.data_as(_dp)
 
 
+def _solute_arrays(xyz, q, sigma, eps):
+    """Contiguous float64 copies of a solute and their pointers; the library reads n_atoms
+    values from each, so the lengths must agree (checked here: it cannot check a pointer)."""
+    xyz, pxyz = _arr(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+    q, pq = _arr(np.ravel(q))
+    s, ps = _arr(np.ravel(sigma))
+    e, pe = _arr(np.ravel(eps))
+    if not (len(xyz) == len(q) == len(s) == len(e)):
+        raise ValueError("solute arrays disagree: %d positions, %d charges, %d sigma, %d eps"
+                         % (len(xyz), len(q), len(s), len(e)))
+    return (xyz, q, s, e), (pxyz, pq, ps, pe)
+
+
 def make_solvent(sites):
     """Marshal a solvent dict (q, sigma, eps, rho, temperature, chi [n,n,nk], dk)."""
     keep = {}
@@ -271,13 +284,10 @@ def solve_batch(jobs, max_inflight=8, time_limit=0.0):
         J.ctx = S.ctx
         sol = d.get("solute")
         if sol is not None:
-            xyz, pxyz = _arr(np.asarray(sol["xyz"], dtype=np.float64).reshape(-1, 3))
-            q, pq = _arr(sol["q"])
-            sg, ps = _arr(sol["sigma"])
-            ep, pe = _arr(sol["eps"])
-            keep += [xyz, q, sg, ep]
-            J.n_atoms, J.xyz, J.q, J.sigma, J.eps = len(q), pxyz, pq, ps, pe
-            S.n_atoms = len(q)
+            arrays, (pxyz, pq, ps, pe) = _solute_arrays(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+            keep += list(arrays)
+            J.n_atoms, J.xyz, J.q, J.sigma, J.eps = len(arrays[1]), pxyz, pq, ps, pe
+            S.n_atoms = len(arrays[1])
         else:
             J.n_atoms = 0
         J.closure = CLOSURES[d.get("closure", "kh")]
@@ -368,12 +378,10 @@ class Solver:
 
     # -- API
     def set_solute(self, xyz, q, sigma, eps):
-        xyz, pxyz = _arr(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
-        q, pq = _arr(q)
-        s, ps = _arr(sigma)
-        e, pe = _arr(eps)
-        _check(self.lib, self.ctx, self.lib.rism3d_set_solute(self.ctx, len(q), pxyz, pq, ps, pe))
-        self.n_atoms = len(q)
+        arrays, (pxyz, pq, ps, pe) = _solute_arrays(xyz, q, sigma, eps)
+        n = len(arrays[1])
+        _check(self.lib, self.ctx, self.lib.rism3d_set_solute(self.ctx, n, pxyz, pq, ps, pe))
+        self.n_atoms = n
 
     def set_guess(self, t):
         p, dev, keep = self._field_arg(t)

@@ -185,3 +185,15 @@ def test_device_tensor_arguments_are_checked_before_the_call():
     for bad in (torch.zeros(8), torch.zeros(8, dtype=torch.float64), np.zeros(8, dtype=np.float32), None):
         with pytest.raises(ValueError):
             capi._f32_cuda(bad, 8, "x")
+
+
+def test_solute_arrays_must_agree_in_length():
+    """The binding refuses a solute whose arrays disagree in length: the library reads
+    n_atoms values from each pointer."""
+    from paper_2403_01039_gb300 import capi
+    (xyz, q, s, e), _ = capi._solute_arrays(np.zeros((4, 3)), np.zeros(4), np.ones(4), np.ones(4))
+    assert xyz.shape == (4, 3) and q.shape == s.shape == e.shape == (4,)
+    with pytest.raises(ValueError):
+        capi._solute_arrays(np.zeros((3, 3)), np.zeros(4), np.ones(4), np.ones(4))
+    with pytest.raises(ValueError):
+        capi._solute_arrays(np.zeros((4, 3)), np.zeros(4), np.ones(5), np.ones(4))
