@@ -38,6 +38,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="solute50_128")
+    p.add_argument("--no-cufft", action="store_true",
+                   help="skip the cuFFT comparison (torch.fft transforms of the same fields)")
     p.add_argument("--precision", type=int, default=32, choices=[32, 64])
     p.add_argument("--closure", default="kh", choices=["kh", "pse", "hnc"])
     p.add_argument("--pse-order", type=int, default=3)
@@ -273,6 +275,42 @@ def replica_totals(secs, iters, device):
     return float(t[0]), float(n[0])
 
 
+def cufft_comparison(nv, n, precision, iteration_ms, pairs=20, warmup=3):
+    """cuFFT (through torch.fft) timed as a comparison only: the forward R2C and inverse C2R
+    3D transforms of all solvent sites on the same grid and precision, which is the FFT part
+    of one iteration; the solver's iteration also does the closure, the contraction, the
+    residual, the Gram products and the update. The L2 is flushed (a 256 MB write) before
+    each timed pair, as the solver's fields do not fit in L2 either. Never fails the bench:
+    an error is reported in the result instead."""
+    try:
+        import torch
+        dt = torch.float32 if precision == 32 else torch.float64
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(7)
+        x = torch.randn((nv,) + tuple(n), dtype=dt, device="cuda", generator=gen)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        dims = (1, 2, 3)
+        for _ in range(warmup):
+            y = torch.fft.irfftn(torch.fft.rfftn(x, dim=dims), s=tuple(n), dim=dims)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(pairs)]
+        for e0, e1 in evs:
+            flush.fill_(1.0)
+            e0.record()
+            y = torch.fft.irfftn(torch.fft.rfftn(x, dim=dims), s=tuple(n), dim=dims)
+            e1.record()
+        torch.cuda.synchronize()
+        ms = statistics.median(e0.elapsed_time(e1) for e0, e1 in evs)
+        err = float((y - x).abs().max())
+        del x, y, flush
+        return dict(what="torch.fft.rfftn + irfftn over all %d sites (cuFFT), %s, L2 flushed before "
+                         "each pair; comparison only, not on the solve path" % (nv, "FP32" if precision == 32 else "FP64"),
+                    ms_per_pair=ms, iteration_ms=iteration_ms,
+                    iteration_over_pair=(iteration_ms / ms) if (iteration_ms and ms) else None,
+                    roundtrip_max_err=err, pairs=pairs)
+    except Exception as exc:          # the comparison is optional context for the line
+        return dict(error="%s: %s" % (type(exc).__name__, exc))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -373,6 +411,12 @@ def run_ours(args):
                            share=(share_ms[k] / total_ms) if total_ms else None)
                    for k, v in kern.items() if v["launches"]}
 
+    cufft = None
+    if rank == 0 and not args.no_cufft:
+        it_keys = [k for k in per_iter + per_iter2 if k in kern]
+        it_ms = sum(share_ms[k] for k in it_keys) / stats["iterations"] if stats["iterations"] else None
+        cufft = cufft_comparison(nv, grid["n"], args.precision, it_ms)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, w, solv, grid, solute, reps[-1]["iterations"])
@@ -389,7 +433,7 @@ def run_ours(args):
                     site_gridpoint_iters_per_s=sgi, iterations_per_solve=iters_all / (world * args.steps),
                     roofline=roofline, cpu_baseline=cpu,
                     e2e=dict(value=e2e_val, unit="solves/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
-                    gpu_launches=launches, clocks=clk, kernels=kernels_out)
+                    gpu_launches=launches, clocks=clk, kernels=kernels_out, cufft_comparison=cufft)
         print(json.dumps(line), flush=True)
     S.close()
     if world > 1:
