@@ -112,8 +112,9 @@ typedef struct {
                                  chunks of this many rows */
     int split_passes;         /* 1: run the plane passes as streaming element kernels and
                                  transform kernels on two graph branches (FP32, whole planes,
-                                 Nz/2 of 64 or 128; otherwise ignored); 0 (default): the fused
-                                 plane kernels. Same results within rounding. */
+                                 Nz/2 of 64 or 128, integer k grid; otherwise ignored);
+                                 0 (default): the fused plane kernels. Same results within
+                                 rounding. */
     int kgrid;                /* 0: periodic integer k grid (the convention above); 1:
                                  half-integer grid k_m = 2 pi (m + 1/2) / (N d) on every axis
                                  (the placement of k in the "Numerical procedure" section): no
