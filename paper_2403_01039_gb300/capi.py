@@ -583,12 +583,13 @@ class UNet3D:
 
 
 def flatten_params(params):
-    """Oracle-layout parameters [[w, b], ...] to the library's flat float32 vector."""
+    """Per-layer parameters [[w, b], ...] (w [out][in][3][3][3] or [out][in]) to the
+    library's flat float32 vector, layer by layer, weights before biases."""
     return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in params]).astype(np.float32)
 
 
 def unflatten(flat, like):
-    """Flat vector back to the oracle layout of ``like``."""
+    """Flat vector back to per-layer [[w, b], ...] with the shapes of ``like``."""
     out, o = [], 0
     for w, b in like:
         gw = flat[o:o + w.size].reshape(w.shape)
