@@ -18,7 +18,18 @@
  *    0 between molecules;
  *  - X_ab(0) = omega_ab(0) + rho_a 4 pi dr sum_i r_i^2 h_ab(r_i);
  *  - MDIIS (Eq. 40 read as the bordered DIIS system) with the charges switched on in
- *    charge_steps equal steps, each solve starting from the previous tau.
+ *    charge_steps equal steps, each solve starting from the previous tau;
+ *  - DRISM (option dielectric > 0; the dielectrically consistent RISM of Perkyns and
+ *    Pettitt): the equation above is solved with omega' = omega + rho zeta in place of
+ *    omega for h' = h - zeta, the physical h being h' + zeta, so X = omega' + rho h'.
+ *    zeta_ab(k) = d_a d_b h_c(k) couples the sites of molecules with a dipole:
+ *    d_a = j0(k x_a) j0(k y_a) j1(k z_a), (x, y, z) the site in its molecule's frame
+ *    (origin at the centroid of the molecule's sites, z along the dipole, x along the
+ *    component normal to z of the site farthest from the z axis, the first on a tie,
+ *    y = z cross x), h_c(k) = h_c0 exp(-a^2 k^2 / 4) with a = drism_damping and
+ *    h_c0 = (dielectric - 1 - 3 y) / sum_s rho_s y_s, y_s = 4 pi beta 332.0637 rho_s mu_s^2 / 9
+ *    per polar species s and y = sum_s y_s. This amplitude makes the k -> 0 limit of
+ *    4 pi beta S_qq(k) / k^2 equal 1 - 1/dielectric (XRISM gives 3y / (1 + 3y)).
  * Errors: every call returns a status (0 = OK, see rism1d_status); rism1d_last_error() gives
  * a one-line message for the calling thread. All arrays are host memory owned by the caller.
  */
@@ -57,6 +68,10 @@ typedef struct {
     int mdiis_nvec;          /* default 5 */
     double mdiis_damp;       /* default 0.3 */
     int charge_steps;        /* default 10 */
+    double dielectric;       /* 0 (default): XRISM; > 0: DRISM with this dielectric constant,
+                                which must exceed 1 + 3y (the XRISM value); needs a solvent
+                                molecule with a dipole */
+    double drism_damping;    /* DRISM damping length a (A), > 0 (default 1.0) */
 } rism1d_options;
 
 void rism1d_options_default(rism1d_options *opt);

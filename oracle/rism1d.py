@@ -23,8 +23,21 @@ Readings (the paper defers the 1D method to Kinoshita and is silent on details):
 * MDIIS as in ``oracle.mdiis``; the charges are switched on in ten steps (0.1, 0.2, ... 1.0 of
   their values, each solve starting from the previous tau), without which XRISM-KH for
   the 3-site water above diverges from tau = 0;
-DRISM (the dielectrically consistent variant) is not implemented: X is a shared input
-of both the oracle and the CUDA path, so the choice cannot affect their parity.
+* DRISM (the dielectrically consistent RISM of Perkyns and Pettitt, which the paper names
+  through Kinoshita's 1D method without detail), as an option: the RISM equation above is
+  solved with omega' = omega + rho zeta in place of omega for h' = h - zeta, and the
+  physical h = h' + zeta; then X = omega + rho h = omega' + rho h'. zeta couples the sites
+  of the polar molecules: zeta_ab(k) = d_a(k) d_b(k) h_c(k), d_a = j0(k x_a) j0(k y_a)
+  j1(k z_a) with (x, y, z) the site position in its molecule's frame (origin at the
+  centroid of its sites, z along the dipole mu, x along the component normal to z of the
+  site farthest from the z axis, the first such site on a tie; y = z cross x), h_c(k) =
+  h_c0 exp(-a^2 k^2 / 4). The amplitude follows from
+  the small-k limit: with j1(x) -> x/3 the polar species' dipole strength
+  y = sum_s 4 pi beta COULOMB rho_s mu_s^2 / 9 grows to y + sum_s rho_s y_s h_c0 / 3, and
+  the RISM dielectric constant 1 + 3y (the XRISM value) becomes the prescribed eps when
+  h_c0 = (eps - 1 - 3y) / sum_s rho_s y_s. The damping length a is a parameter (1 A by
+  default; the paper is silent). X is a shared input of both the oracle and the CUDA path,
+  so this choice cannot affect their parity.
 """
 import numpy as np
 
@@ -65,6 +78,56 @@ def omega_matrix(grid, species, coords):
     return W
 
 
+def _sph_j0(x):
+    xs = np.where(x == 0.0, 1.0, x)
+    return np.where(x == 0.0, 1.0, np.sin(xs) / xs)
+
+
+def _sph_j1(x):
+    xs = np.where(x == 0.0, 1.0, x)
+    return np.where(x == 0.0, 0.0, np.sin(xs) / (xs * xs) - np.cos(xs) / xs)
+
+
+def drism_zeta(grid, q, rho, species, coords, temperature, dielectric, a=1.0):
+    """zeta_ab(k_j) of DRISM, shape [n, n, N-1] (zero outside the polar molecules), and the
+    amplitude h_c0 (module docstring). Raises ValueError when no molecule has a dipole."""
+    q = np.asarray(q, dtype=np.float64)
+    coords = np.asarray(coords, dtype=np.float64)
+    species = np.asarray(species)
+    n = len(q)
+    b = beta_of(temperature)
+    k = grid.k
+    d = np.zeros((n, grid.N - 1))
+    y_tot, rho_y = 0.0, 0.0
+    for s_ in np.unique(species):
+        idx = np.flatnonzero(species == s_)
+        pos = coords[idx] - coords[idx].mean(axis=0)
+        mu = q[idx] @ pos
+        m = float(np.linalg.norm(mu))
+        if m < 1e-12:
+            continue
+        z = mu / m
+        perp = pos - np.outer(pos @ z, z)                # components normal to z
+        pn = np.linalg.norm(perp, axis=1)
+        far = int(np.argmax(pn))
+        if pn[far] > 1e-12:
+            x = perp[far] / pn[far]
+        else:                                            # all sites on the dipole axis
+            x = np.cross(z, [1.0, 0.0, 0.0] if abs(z[0]) < 0.9 else [0.0, 1.0, 0.0])
+            x /= np.linalg.norm(x)
+        yax = np.cross(z, x)
+        ys = 4.0 * np.pi * b * COULOMB * rho[idx[0]] * m * m / 9.0
+        y_tot += ys
+        rho_y += rho[idx[0]] * ys
+        for i, site in enumerate(idx):
+            d[site] = _sph_j0(k * (pos[i] @ x)) * _sph_j0(k * (pos[i] @ yax)) * _sph_j1(k * (pos[i] @ z))
+    if rho_y == 0.0:
+        raise ValueError("DRISM needs a solvent molecule with a dipole")
+    hc0 = (dielectric - 1.0 - 3.0 * y_tot) / rho_y
+    hc = hc0 * np.exp(-(a * k) ** 2 / 4.0)
+    return d[:, None, :] * d[None, :, :] * hc, hc0
+
+
 def _pair_params(q, sig, eps):
     s = 0.5 * (sig[:, None] + sig[None, :])
     e = np.sqrt(eps[:, None] * eps[None, :])
@@ -73,9 +136,11 @@ def _pair_params(q, sig, eps):
 
 def xrism_solvent(q, sig, eps, rho, species, coords, temperature, n=2048, dr=0.05,
                   closure=cl.KH, tol=1e-10, max_iter=5000, mdiis_nvec=5, mdiis_damp=0.3,
-                  charge_steps=tuple(0.1 * i for i in range(1, 11)), verbose=False):
-    """Solve Eq. 4 for the pure solvent. Returns dict(chi [n,n,N] at k_j = j dk for
-    j = 0..N-1, dk, h, c, grid, iterations, rms)."""
+                  charge_steps=tuple(0.1 * i for i in range(1, 11)), verbose=False,
+                  dielectric=None, drism_a=1.0):
+    """Solve Eq. 4 for the pure solvent (XRISM; DRISM with the given dielectric constant
+    when ``dielectric`` is set). Returns dict(chi [n,n,N] at k_j = j dk for j = 0..N-1, dk,
+    h, c, grid, iterations, rms)."""
     q, sig, eps, rho = (np.asarray(v, dtype=np.float64) for v in (q, sig, eps, rho))
     grid = RadialGrid(n, dr)
     b = beta_of(temperature)
@@ -87,6 +152,11 @@ def xrism_solvent(q, sig, eps, rho, species, coords, temperature, n=2048, dr=0.0
     Wk = np.moveaxis(W, -1, 0)                           # [N-1, n, n]
     P = np.diag(rho)
     I = np.eye(ns)
+    Zk = np.zeros((grid.N - 1, ns, ns))
+    if dielectric is not None:
+        zeta, _ = drism_zeta(grid, q, rho, species, coords, temperature, dielectric, drism_a)
+        Zk = np.moveaxis(zeta, -1, 0)                   # [N-1, n, n]
+    Wp = Wk + P[None] @ Zk                               # omega' = omega + rho zeta
     tau = np.zeros((ns, ns, grid.N - 1))
     total_it = 0
     for scale in charge_steps:
@@ -103,8 +173,8 @@ def xrism_solvent(q, sig, eps, rho, species, coords, temperature, n=2048, dr=0.0
             cs = h - tau
             Cs = grid.forward(cs)
             C = np.moveaxis(Cs - bU_L, -1, 0)            # full c = c_s - beta u_L
-            WC = Wk @ C
-            H = np.linalg.solve(I[None] - WC @ P[None], WC @ Wk)   # Eq. 4 in k space
+            WC = Wp @ C
+            H = np.linalg.solve(I[None] - WC @ P[None], WC @ Wp) + Zk   # Eq. 4 in k space
             tau_new = grid.inverse(np.moveaxis(H, 0, -1) - Cs)
             return tau_new - tau, h, cs, np.moveaxis(H, 0, -1)
 

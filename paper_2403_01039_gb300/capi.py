@@ -142,7 +142,8 @@ class Rism1dSolvent(ctypes.Structure):
 class Rism1dOptions(ctypes.Structure):
     _fields_ = [("n_r", ctypes.c_int), ("dr", ctypes.c_double), ("closure", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mdiis_nvec", ctypes.c_int),
-                ("mdiis_damp", ctypes.c_double), ("charge_steps", ctypes.c_int)]
+                ("mdiis_damp", ctypes.c_double), ("charge_steps", ctypes.c_int),
+                ("dielectric", ctypes.c_double), ("drism_damping", ctypes.c_double)]
 
 
 class RismError(RuntimeError):
@@ -238,9 +239,11 @@ def sfe_noalloc(h, c, rho, temperature, dV, kind="kh", pse_order=3, d=None, stre
     return tot.value, per
 
 
-def xrism(sites, n_r=2048, dr=0.05, closure="kh", tol=1e-10, charge_steps=10, thermo=False):
+def xrism(sites, n_r=2048, dr=0.05, closure="kh", tol=1e-10, charge_steps=10, thermo=False,
+          dielectric=None, drism_damping=1.0):
     """Solvent susceptibility X_ag(k_j), k_j = j dk, of a pure solvent (Eq. 4) from the
-    library's host 1D-RISM solver. Returns (chi [n][n][n_r], dk, iterations, rms); with
+    library's host 1D-RISM solver (XRISM, or DRISM with the given dielectric constant).
+    Returns (chi [n][n][n_r], dk, iterations, rms); with
     thermo=True also a dict with the full direct correlation c [n][n][n_r - 1] at r_i = i dr,
     the bulk pressure of Eq. 20 (kcal/mol/A^3) and k_B T chi_T (A^3)."""
     lib = load()
@@ -255,6 +258,8 @@ def xrism(sites, n_r=2048, dr=0.05, closure="kh", tol=1e-10, charge_steps=10, th
     lib.rism1d_options_default(ctypes.byref(o))
     o.n_r, o.dr, o.tol, o.charge_steps = int(n_r), float(dr), float(tol), int(charge_steps)
     o.closure = {"kh": 1, "hnc": 2}[closure]
+    o.dielectric = 0.0 if dielectric is None else float(dielectric)
+    o.drism_damping = float(drism_damping)
     chi = np.zeros((n, n, n_r))
     c_r = np.zeros((n, n, n_r - 1))
     dk, pres, ktchi = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -121,6 +121,87 @@ bool gauss_multi(std::vector<double> &A, std::vector<double> &B, int n, int m) {
     return true;
 }
 
+double sph_j0(double x) { return x == 0.0 ? 1.0 : std::sin(x) / x; }
+double sph_j1(double x) { return x == 0.0 ? 0.0 : std::sin(x) / (x * x) - std::cos(x) / x; }
+
+// DRISM zeta_ab(k_j) (header), written into Z [n][n][P]; false when no molecule has a
+// dipole or the dielectric constant is not above the XRISM value 1 + 3y.
+bool drism_zeta(const rism1d_solvent *sv, double beta, double dielectric, double a, const std::vector<double> &k,
+                std::vector<double> &Z, std::string &why) {
+    const int n = sv->n_sites, P = (int)k.size();
+    std::vector<double> d((size_t)n * P, 0.0);
+    double y_tot = 0.0, rho_y = 0.0;
+    std::vector<int> done;
+    for (int s0 = 0; s0 < n; ++s0) {
+        const int sp = sv->species[s0];
+        if (std::find(done.begin(), done.end(), sp) != done.end()) continue;
+        done.push_back(sp);
+        std::vector<int> idx;
+        for (int b = 0; b < n; ++b)
+            if (sv->species[b] == sp) idx.push_back(b);
+        double cen[3] = {0.0, 0.0, 0.0};
+        for (int b : idx)
+            for (int c = 0; c < 3; ++c) cen[c] += sv->coords[3 * b + c] / (double)idx.size();
+        std::vector<double> pos(3 * idx.size());
+        double mu[3] = {0.0, 0.0, 0.0};
+        for (size_t i = 0; i < idx.size(); ++i)
+            for (int c = 0; c < 3; ++c) {
+                pos[3 * i + c] = sv->coords[3 * idx[i] + c] - cen[c];
+                mu[c] += sv->q[idx[i]] * pos[3 * i + c];
+            }
+        const double m = std::sqrt(mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]);
+        if (m < 1e-12) continue;
+        const double z[3] = {mu[0] / m, mu[1] / m, mu[2] / m};
+        // x along the normal-to-z part of the site farthest from the z axis
+        double x[3] = {0.0, 0.0, 0.0}, best = -1.0;
+        for (size_t i = 0; i < idx.size(); ++i) {
+            const double *p = &pos[3 * i];
+            const double pz = p[0] * z[0] + p[1] * z[1] + p[2] * z[2];
+            const double v[3] = {p[0] - pz * z[0], p[1] - pz * z[1], p[2] - pz * z[2]};
+            const double nv = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            if (nv > best) {
+                best = nv;
+                for (int c = 0; c < 3; ++c) x[c] = nv > 0.0 ? v[c] / nv : 0.0;
+            }
+        }
+        if (!(best > 1e-12)) {        // all sites on the dipole axis: any x normal to z
+            const double e[3] = {std::fabs(z[0]) < 0.9 ? 1.0 : 0.0, std::fabs(z[0]) < 0.9 ? 0.0 : 1.0, 0.0};
+            double c3[3] = {z[1] * e[2] - z[2] * e[1], z[2] * e[0] - z[0] * e[2], z[0] * e[1] - z[1] * e[0]};
+            const double nc = std::sqrt(c3[0] * c3[0] + c3[1] * c3[1] + c3[2] * c3[2]);
+            for (int c = 0; c < 3; ++c) x[c] = c3[c] / nc;
+        }
+        const double yv[3] = {z[1] * x[2] - z[2] * x[1], z[2] * x[0] - z[0] * x[2], z[0] * x[1] - z[1] * x[0]};
+        const double rho_s = sv->rho[idx[0]];
+        const double ys = 4.0 * kPi * beta * kCoulomb * rho_s * m * m / 9.0;
+        y_tot += ys;
+        rho_y += rho_s * ys;
+        for (size_t i = 0; i < idx.size(); ++i) {
+            const double *p = &pos[3 * i];
+            const double px = p[0] * x[0] + p[1] * x[1] + p[2] * x[2];
+            const double py = p[0] * yv[0] + p[1] * yv[1] + p[2] * yv[2];
+            const double pz = p[0] * z[0] + p[1] * z[1] + p[2] * z[2];
+            for (int j = 0; j < P; ++j)
+                d[(size_t)idx[i] * P + j] = sph_j0(k[j] * px) * sph_j0(k[j] * py) * sph_j1(k[j] * pz);
+        }
+    }
+    if (rho_y == 0.0) {
+        why = "DRISM needs a solvent molecule with a dipole";
+        return false;
+    }
+    if (!(dielectric > 1.0 + 3.0 * y_tot)) {
+        why = "DRISM dielectric constant must exceed the XRISM value 1 + 3y = " + std::to_string(1.0 + 3.0 * y_tot);
+        return false;
+    }
+    const double hc0 = (dielectric - 1.0 - 3.0 * y_tot) / rho_y;
+    Z.assign((size_t)n * n * P, 0.0);
+    for (int a0 = 0; a0 < n; ++a0)
+        for (int b = 0; b < n; ++b)
+            for (int j = 0; j < P; ++j)
+                Z[((size_t)a0 * n + b) * P + j] =
+                    d[(size_t)a0 * P + j] * d[(size_t)b * P + j] * hc0 * std::exp(-(a * k[j]) * (a * k[j]) / 4.0);
+    return true;
+}
+
 // HNC (closure 2): exp(d); KH (closure 1): exp(d) for d <= 0, 1 + d otherwise.
 double closure_g(double d, int closure) {
     if (closure == 2 || d <= 0.0) return std::exp(d);
@@ -141,6 +222,8 @@ void rism1d_options_default(rism1d_options *o) {
     o->mdiis_nvec = 5;
     o->mdiis_damp = 0.3;
     o->charge_steps = 10;
+    o->dielectric = 0.0;
+    o->drism_damping = 1.0;
 }
 
 rism1d_status rism1d_xrism(const rism1d_solvent *sv, const rism1d_options *op, double *chi, double *dk_out,
@@ -157,6 +240,8 @@ rism1d_status rism1d_xrism_ex(const rism1d_solvent *sv, const rism1d_options *op
     if (N < 8 || (N & (N - 1))) return fail(RISM1D_EINVAL, "n_r must be a power of two >= 8");
     if (!(op->dr > 0.0) || !(sv->temperature > 0.0)) return fail(RISM1D_EINVAL, "dr and T must be positive");
     if (op->closure != 1 && op->closure != 2) return fail(RISM1D_EINVAL, "closure must be 1 (KH) or 2 (HNC)");
+    if (!(op->dielectric >= 0.0) || !(op->drism_damping > 0.0) || !std::isfinite(op->dielectric))
+        return fail(RISM1D_EINVAL, "dielectric must be >= 0 (0: XRISM) and drism_damping > 0");
     if (op->mdiis_nvec < 1 || op->mdiis_nvec > 32 || op->charge_steps < 1 || op->max_iter < 1 || !(op->tol > 0))
         return fail(RISM1D_EINVAL, "bad MDIIS / charge-step options");
     if (!sv->q || !sv->sigma || !sv->eps || !sv->rho || !sv->species || !sv->coords)
@@ -202,6 +287,15 @@ rism1d_status rism1d_xrism_ex(const rism1d_solvent *sv, const rism1d_options *op
                 for (int j = 0; j < P; ++j) W[at(a, b) + j] = std::sin(k[j] * l) / (k[j] * l);
             }
         }
+    // DRISM: omega' = omega + rho_a zeta_ab replaces omega in the RISM equation (Z = 0: XRISM)
+    std::vector<double> Z(F, 0.0), Wp(W);
+    if (op->dielectric > 0.0) {
+        std::string why;
+        if (!drism_zeta(sv, beta, op->dielectric, op->drism_damping, k, Z, why)) return fail(RISM1D_EINVAL, why);
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b)
+                for (int j = 0; j < P; ++j) Wp[at(a, b) + j] += sv->rho[a] * Z[at(a, b) + j];
+    }
     SineTransform dst(N);
     std::vector<double> tmp(P), out(P);
     auto forward = [&](const double *f, double *Fk) {
@@ -250,25 +344,26 @@ rism1d_status rism1d_xrism_ex(const rism1d_solvent *sv, const rism1d_options *op
             }
             for (int a = 0; a < n; ++a)
                 for (int b = 0; b < n; ++b) forward(&cs[at(a, b)], &Cs[at(a, b)]);
-            // RISM equation per k: (I - W C rho) H = W C W with C = C_s - beta U_L
+            // RISM equation per k: (I - W' C rho) H' = W' C W' with C = C_s - beta U_L, and
+            // H = H' + zeta (W' = W and zeta = 0 for XRISM)
             for (int j = 0; j < P; ++j) {
                 for (int a = 0; a < n; ++a)
                     for (int b = 0; b < n; ++b) {
                         double s = 0.0;
                         for (int c = 0; c < n; ++c)
-                            s += W[at(a, c) + j] * (Cs[at(c, b) + j] - bUL[at(c, b) + j]);
+                            s += Wp[at(a, c) + j] * (Cs[at(c, b) + j] - bUL[at(c, b) + j]);
                         WC[a * n + b] = s;
                     }
                 for (int a = 0; a < n; ++a)
                     for (int b = 0; b < n; ++b) {
                         A[a * n + b] = (a == b ? 1.0 : 0.0) - WC[a * n + b] * sv->rho[b];
                         double s = 0.0;
-                        for (int c = 0; c < n; ++c) s += WC[a * n + c] * W[at(c, b) + j];
+                        for (int c = 0; c < n; ++c) s += WC[a * n + c] * Wp[at(c, b) + j];
                         Bm[a * n + b] = s;
                     }
                 if (!gauss_multi(A, Bm, n, n)) return fail(RISM1D_EDIVERGED, "singular RISM matrix");
                 for (int a = 0; a < n; ++a)
-                    for (int b = 0; b < n; ++b) H[at(a, b) + j] = Bm[a * n + b];
+                    for (int b = 0; b < n; ++b) H[at(a, b) + j] = Bm[a * n + b] + Z[at(a, b) + j];
             }
             for (int a = 0; a < n; ++a)
                 for (int b = 0; b < n; ++b) {

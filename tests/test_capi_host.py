@@ -108,6 +108,26 @@ def test_product_xrism_matches_oracle_table(lib):
     assert np.max(np.abs(chi - ref)) < 1e-7
 
 
+def test_product_drism_matches_oracle(lib):
+    """The library's host DRISM (dielectric 78.44) against the oracle's (both to RMS 1e-10;
+    measured max|dX| 1.6e-9), and its refusals: a dielectric constant at or below the XRISM
+    value, a solvent without a dipole."""
+    from paper_2403_01039_gb300 import capi, synth
+    from oracle import rism1d
+    s = synth.water_3site()
+    ref = rism1d.xrism_solvent(s["q"], s["sigma"], s["eps"], s["rho"], s["species"], s["coords"],
+                               s["temperature"], dielectric=78.44)
+    chi, dk, its, rms = capi.xrism(s, dielectric=78.44)
+    assert dk == ref["dk"] and rms < 1e-10
+    assert np.max(np.abs(chi - ref["chi"])) < 1e-7
+    with pytest.raises(RuntimeError, match="XRISM value"):
+        capi.xrism(s, dielectric=5.0)
+    lj = dict(q=np.zeros(1), sigma=np.array([3.4]), eps=np.array([0.2]), rho=np.array([0.02]),
+              species=np.zeros(1, dtype=np.int32), coords=np.zeros((1, 3)), temperature=120.0)
+    with pytest.raises(RuntimeError, match="dipole"):
+        capi.xrism(lj, dielectric=2.0)
+
+
 def test_product_xrism_thermo_matches_oracle(lib):
     """Bulk pressure (Eq. 20), k_B T chi_T and the full direct correlation of 3-site water
     from the library's host 1D solver against the oracle's stored values."""

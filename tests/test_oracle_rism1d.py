@@ -61,6 +61,38 @@ def test_water_dielectric_limit(water_xrism):
     assert abs(lim - 3 * y / (1 + 3 * y)) < 2e-3
 
 
+def _dielectric_limit(s, chi, dk):
+    """k -> 0 limit of 4 pi beta S_qq(k) / k^2 for a one-molecule solvent, Richardson-
+    extrapolated from k = dk and 2 dk (the leading correction is O(k^2))."""
+    q, rho, b = s["q"], s["rho"][0], beta(s["temperature"])
+    n = len(q)
+    S = sum(rho * q[a] * q[c] * chi[a, c] for a in range(n) for c in range(n))
+    lim = [4 * np.pi * b * COULOMB * S[j] / (j * dk) ** 2 for j in (1, 2)]
+    return (4 * lim[0] - lim[1]) / 3
+
+
+@pytest.mark.parametrize("eps_r", [78.44, 40.0])
+def test_drism_dielectric_limit(eps_r):
+    """DRISM (Perkyns-Pettitt) exists to give the solvent a prescribed dielectric constant:
+    4 pi beta S_qq(k) / k^2 -> 1 - 1/eps as k -> 0, where XRISM gives 3y / (1 + 3y)
+    (measured: 0.987253 for eps 78.44, 0.975000 for eps 40). A wrong amplitude (eps in
+    place of eps - 1 moves it by 1.6e-4), a dropped zeta in omega' or in h, j0 in place of
+    j1, or a dipole frame off the dipole each move the limit by more than the bar."""
+    s = synth.water_3site()
+    r = rism1d.xrism_solvent(s["q"], s["sigma"], s["eps"], s["rho"], s["species"], s["coords"],
+                             s["temperature"], dielectric=eps_r)
+    assert r["rms"] < 1e-10
+    assert abs(_dielectric_limit(s, r["chi"], r["dk"]) - (1.0 - 1.0 / eps_r)) < 3e-5
+
+
+def test_xrism_dielectric_limit_extrapolated(water_xrism):
+    s, r = water_xrism
+    rho, b = s["rho"][0], beta(s["temperature"])
+    mu = np.linalg.norm(sum(s["q"][a] * s["coords"][a] for a in range(3)))
+    y = 4 * np.pi * b * COULOMB * rho * mu * mu / 9.0
+    assert abs(_dielectric_limit(s, r["chi"], r["dk"]) - 3 * y / (1 + 3 * y)) < 3e-5
+
+
 def test_stored_tables_match_live_solve(water_xrism):
     _, r = water_xrism
     chi, dk = load_chi("water3")
