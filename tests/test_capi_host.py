@@ -217,3 +217,21 @@ def test_solute_arrays_must_agree_in_length():
         capi._solute_arrays(np.zeros((3, 3)), np.zeros(4), np.ones(4), np.ones(4))
     with pytest.raises(ValueError):
         capi._solute_arrays(np.zeros((4, 3)), np.zeros(4), np.ones(5), np.ones(4))
+
+
+def test_workloads_fit_one_gb300(lib):
+    """The device workspace of every named workload, in both precisions, fits one GB300
+    (284,208 MiB of HBM) with room to spare for the CUDA context and the caller."""
+    from paper_2403_01039_gb300 import capi, synth
+    hbm = 284208 * 2 ** 20
+    for name, w in synth.WORKLOADS.items():
+        sites = synth.solvent_sites(w["solvent"])
+        nv = len(sites["q"])
+        s, keep = capi.make_solvent(dict(sites, chi=np.zeros((nv, nv, 64)), dk=0.05))
+        g = capi.make_grid(synth.cubic_grid(w["n"], w["spacing"]))
+        for prec in (32, 64):
+            o = capi.default_options()
+            o.precision, o.mdiis_nvec = prec, w["mdiis_nvec"]
+            nb = ctypes.c_size_t()
+            st = lib.rism3d_workspace_bytes(ctypes.byref(s), ctypes.byref(g), ctypes.byref(o), ctypes.byref(nb))
+            assert st == capi.OK and 0 < nb.value < 0.6 * hbm, (name, prec, nb.value)
