@@ -19,6 +19,8 @@ SOURCES = ["rism3d_planes_f32.cu", "rism3d_kernels_f32.cu", "rism3d_planes_f64.c
            "rism1d.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+# RISM_MINBLOCKS_F32: minimum resident blocks per SM that the FP32 plane, pencil and
+# transform kernels are compiled for (their launch bounds; 3 when unset), for occupancy sweeps
 if os.environ.get("RISM_MINBLOCKS_F32"):
     FLAGS.append("-DRISM_MINBLOCKS_F32=%d" % int(os.environ["RISM_MINBLOCKS_F32"]))
 
