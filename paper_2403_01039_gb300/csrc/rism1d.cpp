@@ -332,18 +332,22 @@ rism1d_status rism1d_xrism_ex(const rism1d_solvent *sv, const rism1d_options *op
                 for (int j = 0; j < P; ++j)
                     bUL[at(a, b) + j] = beta * 4.0 * kPi * kCoulomb * qq / (k[j] * k[j] * (k[j] * k[j] + 1.0));
             }
-        std::vector<std::vector<double>> hist_t, hist_R;
+        std::vector<std::vector<double>> hist_t, hist_R, gram;
         bool converged = false;
         for (int it = 1; it <= op->max_iter; ++it) {
             ++total;
-            // closure on d = -beta u_s + tau
+            // closure on d = -beta u_s + tau; pair functions are symmetric (ab = ba), so the
+            // upper triangle is computed and mirrored
             for (size_t x = 0; x < F; ++x) {
                 const double g = closure_g(-bus[x] + tau[x], op->closure);
                 h[x] = g - 1.0;
                 cs[x] = h[x] - tau[x];
             }
             for (int a = 0; a < n; ++a)
-                for (int b = 0; b < n; ++b) forward(&cs[at(a, b)], &Cs[at(a, b)]);
+                for (int b = a; b < n; ++b) {
+                    forward(&cs[at(a, b)], &Cs[at(a, b)]);
+                    if (b != a) std::copy(&Cs[at(a, b)], &Cs[at(a, b)] + P, &Cs[at(b, a)]);
+                }
             // RISM equation per k: (I - W' C rho) H' = W' C W' with C = C_s - beta U_L, and
             // H = H' + zeta (W' = W and zeta = 0 for XRISM)
             for (int j = 0; j < P; ++j) {
@@ -362,14 +366,21 @@ rism1d_status rism1d_xrism_ex(const rism1d_solvent *sv, const rism1d_options *op
                         Bm[a * n + b] = s;
                     }
                 if (!gauss_multi(A, Bm, n, n)) return fail(RISM1D_EDIVERGED, "singular RISM matrix");
+                // H is symmetric (omega rho = rho omega within a molecule): keep its upper
+                // triangle, mirrored, so that tau stays exactly symmetric
                 for (int a = 0; a < n; ++a)
-                    for (int b = 0; b < n; ++b) H[at(a, b) + j] = Bm[a * n + b] + Z[at(a, b) + j];
+                    for (int b = a; b < n; ++b) {
+                        const double v = Bm[a * n + b] + Z[at(a, b) + j];
+                        H[at(a, b) + j] = v;
+                        H[at(b, a) + j] = v;
+                    }
             }
+            std::vector<double> tk(P);
             for (int a = 0; a < n; ++a)
-                for (int b = 0; b < n; ++b) {
-                    for (int j = 0; j < P; ++j) tmp[j] = H[at(a, b) + j] - Cs[at(a, b) + j];
-                    std::vector<double> tk(tmp);
+                for (int b = a; b < n; ++b) {
+                    for (int j = 0; j < P; ++j) tk[j] = H[at(a, b) + j] - Cs[at(a, b) + j];
                     inverse(tk.data(), &tnew[at(a, b)]);
+                    if (b != a) std::copy(&tnew[at(a, b)], &tnew[at(a, b)] + P, &tnew[at(b, a)]);
                 }
             double ss = 0.0;
             for (size_t x = 0; x < F; ++x) {
@@ -382,13 +393,28 @@ rism1d_status rism1d_xrism_ex(const rism1d_solvent *sv, const rism1d_options *op
                 converged = true;
                 break;
             }
-            // MDIIS: minimise |sum c_i R_i| with sum c_i = 1 (bordered Gram system)
+            // MDIIS: minimise |sum c_i R_i| with sum c_i = 1 (bordered Gram system). The Gram
+            // entries of stored pairs do not change, so only the new row is computed.
             hist_t.push_back(tau);
             hist_R.push_back(R);
-            if ((int)hist_R.size() > M) {
+            {
+                const int m0 = (int)hist_R.size();
+                std::vector<double> row(m0);
+                for (int p = 0; p < m0; ++p) {
+                    double s = 0.0;
+                    for (size_t x = 0; x < F; ++x) s += hist_R[p][x] * hist_R[m0 - 1][x];
+                    row[p] = s;
+                }
+                for (int p = 0; p < m0 - 1; ++p) gram[p].push_back(row[p]);
+                gram.push_back(row);
+            }
+            auto drop_oldest = [&]() {
                 hist_t.erase(hist_t.begin());
                 hist_R.erase(hist_R.begin());
-            }
+                gram.erase(gram.begin());
+                for (auto &g : gram) g.erase(g.begin());
+            };
+            if ((int)hist_R.size() > M) drop_oldest();
             std::vector<double> coef;
             for (;;) {
                 const int m = (int)hist_R.size();
@@ -399,11 +425,7 @@ rism1d_status rism1d_xrism_ex(const rism1d_solvent *sv, const rism1d_options *op
                 std::vector<double> Gm((size_t)m * m);
                 double dmax = 0.0;
                 for (int p = 0; p < m; ++p)
-                    for (int q = 0; q < m; ++q) {
-                        double s = 0.0;
-                        for (size_t x = 0; x < F; ++x) s += hist_R[p][x] * hist_R[q][x];
-                        Gm[p * m + q] = s;
-                    }
+                    for (int q = 0; q < m; ++q) Gm[p * m + q] = gram[p][q];
                 for (int p = 0; p < m; ++p) dmax = std::max(dmax, Gm[p * m + p]);
                 const int dim = m + 1;
                 std::vector<double> Ab((size_t)dim * dim, 0.0), rhs(dim, 0.0);
@@ -417,8 +439,7 @@ rism1d_status rism1d_xrism_ex(const rism1d_solvent *sv, const rism1d_options *op
                     coef.assign(rhs.begin(), rhs.begin() + m);
                     break;
                 }
-                hist_t.erase(hist_t.begin());
-                hist_R.erase(hist_R.begin());
+                drop_oldest();
             }
             std::fill(tau.begin(), tau.end(), 0.0);
             for (size_t p = 0; p < coef.size(); ++p)
