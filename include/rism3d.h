@@ -22,6 +22,11 @@
  * Errors: every call returns a status; nothing throws across the ABI. After a failure
  *   rism3d_last_error(ctx) (or rism3d_last_error(NULL) when no context exists) gives a
  *   one-line message. RISM3D_ENOTCONV and RISM3D_EDIVERGED leave the last iterate readable.
+ *   Common to every call: RISM3D_EINVAL for a NULL context or required pointer, an
+ *   argument out of its stated range, or an output buffer smaller than stated;
+ *   RISM3D_ESTATE for a call that needs a solute before rism3d_set_solute has succeeded;
+ *   RISM3D_ECUDA when a CUDA runtime call fails (the message names it). Nothing is
+ *   written to outputs when a call fails before its device work.
  * Threads: one context per host thread; every kernel of a context runs on its stream.
  * Pointers: "host" arrays are ordinary host memory; "device" arrays are device memory of
  *   the current CUDA device (for example a torch CUDA tensor's data_ptr()).
@@ -171,7 +176,10 @@ rism3d_status rism3d_workspace_bytes(const rism3d_solvent *solvent, const rism3d
 
 /* Create a context for one solvent and one grid (the solvent's 1D part is computed once
  * per solvent and reused, Package Features section). Copies the susceptibility table to
- * the device as the interpolation table of Eq. 13. On success *out is a new context. */
+ * the device as the interpolation table of Eq. 13. On success *out is a new context, else
+ * *out is NULL: EINVAL (bad solvent, grid or options), EUNSUPPORTED (a grid the kernels do
+ * not implement), ENOMEM (a caller workspace smaller than rism3d_workspace_bytes, or the
+ * device allocation failed). */
 rism3d_status rism3d_create(const rism3d_solvent *solvent, const rism3d_grid *grid,
                             const rism3d_options *opt, rism3d_ctx **out);
 
@@ -186,7 +194,9 @@ rism3d_status rism3d_create(const rism3d_solvent *solvent, const rism3d_grid *gr
 rism3d_status rism3d_set_solute(rism3d_ctx *ctx, int n_atoms, const double *xyz,
                                 const double *q, const double *sigma, const double *eps);
 
-/* Replace the initial guess t by a caller field [n_sites][Nx][Ny][Nz] (warm start). */
+/* Replace the initial guess of step 1 (t = f) by a caller field t [n_sites][Nx][Ny][Nz]
+ * of FP64, host memory (on_device = 0) or device memory (on_device = 1), for a warm start.
+ * The next rism3d_solve starts from it with an empty MDIIS history. */
 rism3d_status rism3d_set_guess(rism3d_ctx *ctx, const double *t, int on_device);
 
 /* Run steps 2-7 from the current guess until RMS(R) < tol (read of Eq. 41), max_iter, or a
@@ -203,8 +213,9 @@ rism3d_status rism3d_residual(rism3d_ctx *ctx, int closure, int pse_order, const
                               double *R, int on_device);
 
 /* Copy one field (see RISM3D_G ...) of every site, converted to FP64, into dst
- * ([n_sites][Nx][Ny][Nz], or [Nx][Ny][Nz] for PHI). count is the capacity of dst in
- * elements. G, H and C use the closure of the last solve (KH before any solve). */
+ * ([n_sites][Nx][Ny][Nz], or [Nx][Ny][Nz] for PHI; host or device memory by on_device).
+ * count is the capacity of dst in elements (EINVAL when smaller than the field). G, H and
+ * C use the closure of the last solve (KH before any solve), Eqs. 14-16 and 31. */
 rism3d_status rism3d_get(rism3d_ctx *ctx, int field, double *dst, size_t count, int on_device);
 
 /* Solvation free energy in kcal/mol of the current iterate: k_B T sum_g rho_g dV
@@ -214,8 +225,9 @@ rism3d_status rism3d_get_sfe(rism3d_ctx *ctx, int kind, int pse_order, double *t
                              double *per_site);
 
 /* Learned initial guess (next row of the method; the paper starts every solve from t = f):
- * crops of side `crop` at grid index corner[3] (inside the grid), FP32 device arrays
- * [n_sites][crop][crop][crop], for the network of unet3d.h. */
+ * crops of side `crop` at grid index corner[3] (inside the grid, else EINVAL), FP32 device
+ * arrays of exactly n_sites * crop^3 values [n_sites][crop][crop][crop], for the network
+ * of unet3d.h. */
 /* Network input: tanh(beta u_g / 4) on the crop (after rism3d_set_solute). */
 rism3d_status rism3d_guess_input(rism3d_ctx *ctx, const int *corner, int crop, float *x);
 /* Training target: the current iterate tau = t - f on the crop (after a solve). */
@@ -268,7 +280,8 @@ rism3d_status rism3d_get_pmv(rism3d_ctx *ctx, double kT_chi_T, double *pmv, doub
  * in kcal/mol/A, with du/dR the analytic derivative of Eq. 22's pair terms (Lorentz-Berthelot
  * mixing, r^2 floored at 1e-8 A^2). grad is host [n_atoms][3]. For a neutral solute this is the
  * exact derivative of the KH/HNC SFE on the grid; for a charged one it omits the dependence of
- * the long-range split (Eqs. 29-30) on the atom positions. */
+ * the long-range split (Eqs. 29-30) on the atom positions. EUNSUPPORTED when the grid is too
+ * small to hold the FP64 partial sums of one atom (n_sites * Nx * Ny * Nz below 915). */
 rism3d_status rism3d_get_sfe_gradient(rism3d_ctx *ctx, double *grad);
 
 /* Autotune the transform tiles of this context by measurement: the x-pencil pass (x
