@@ -66,7 +66,7 @@ def workload_inputs(name, chi_source):
     from paper_2403_01039_gb300 import synth
     w = synth.WORKLOADS[name]
     sites = synth.solvent_sites(w["solvent"])
-    chi, dk = chi_source(sites)
+    chi, dk = chi_source(sites, w.get("dielectric"))
     solv = dict(sites)
     solv.update(chi=chi, dk=dk)
     grid = synth.cubic_grid(w["n"], w["spacing"])
@@ -74,9 +74,11 @@ def workload_inputs(name, chi_source):
     return w, solv, grid, solute
 
 
-def product_chi(sites):
+def product_chi(sites, dielectric=None):
+    """X of the solvent from the library's host 1D solver (XRISM; DRISM when the workload
+    names a dielectric constant)."""
     from paper_2403_01039_gb300 import capi
-    chi, dk, _, _ = capi.xrism(sites)
+    chi, dk, _, _ = capi.xrism(sites, dielectric=dielectric)
     return chi, dk
 
 
@@ -225,7 +227,7 @@ def run_reference(args):
     # the oracle's own 1D solver provides its susceptibility
     from oracle import rism1d
     r1 = rism1d.xrism_solvent(sites["q"], sites["sigma"], sites["eps"], sites["rho"], sites["species"],
-                              sites["coords"], sites["temperature"])
+                              sites["coords"], sites["temperature"], dielectric=w.get("dielectric"))
     solv = dict(sites)
     solv.update(chi=r1["chi"], dk=r1["dk"])
     grid = synth.cubic_grid(w["n"], w["spacing"])

@@ -84,8 +84,13 @@ def cubic_grid(n, spacing):
     return dict(n=(n, n, n), spacing=(spacing,) * 3, origin=(-(n // 2) * spacing,) * 3)
 
 
+# dielectric constant of water for the DRISM solvent (298 K)
+WATER_DIELECTRIC = 78.44
+
+
 # Workloads ------------------------------------------------------------------
-# sphere_32: one neutral LJ sphere in 3-site water, 32^3 at 0.5 A, KH, MDIIS 5, FP64.
+# sphere_32: one neutral LJ sphere in 3-site water (X from 1D DRISM, dielectric constant
+#            78.44), 32^3 at 0.5 A, KH, MDIIS 5, FP64.
 # solute50_128: 50-atom solute (10 A sphere, seed 2001) in water + 0.1 M NaCl,
 #               128^3 at 0.5 A, KH and PSE-3, FP32 and FP64, MDIIS 5.
 # globule2000_256: 2000-atom globule (radius 16 A, seed 3001, net +8) in water + NaCl,
@@ -93,7 +98,7 @@ def cubic_grid(n, spacing):
 # globule12877_512: 12877 atoms (radius 32 A, seed 5001, net 0) in water + NaCl, 512^3 at
 #               0.5 A, KH, MDIIS 10.
 WORKLOADS = {
-    "sphere_32": dict(n=32, spacing=0.5, solvent="water3", mdiis_nvec=5),
+    "sphere_32": dict(n=32, spacing=0.5, solvent="water3", mdiis_nvec=5, dielectric=WATER_DIELECTRIC),
     "solute50_128": dict(n=128, spacing=0.5, solvent="water_nacl", mdiis_nvec=5,
                          atoms=50, radius=10.0, seed=2001, net_charge=0.0),
     "globule2000_256": dict(n=256, spacing=0.375, solvent="water_nacl", mdiis_nvec=10,

@@ -32,6 +32,16 @@ def water3():
 
 
 @pytest.fixture(scope="session")
+def water3_drism():
+    """3-site water with X from the oracle's DRISM (the sphere_32 workload's solvent)."""
+    from paper_2403_01039_gb300 import synth
+    s = synth.water_3site()
+    chi, dk = load_chi("water3_drism")
+    s.update(chi=chi, dk=dk)
+    return s
+
+
+@pytest.fixture(scope="session")
 def water_nacl():
     from paper_2403_01039_gb300 import synth
     s = synth.water_nacl_5site()

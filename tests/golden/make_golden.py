@@ -3,7 +3,8 @@
 Calls only the FP64 oracle (``oracle/``) and the seeded input generators; nothing here
 touches the CUDA path. Run from the repository root:
 
-    python tests/golden/make_golden.py chi          # solvent susceptibility tables
+    python tests/golden/make_golden.py chi          # solvent susceptibility tables (XRISM)
+    python tests/golden/make_golden.py drism        # 3-site water from DRISM (eps 78.44)
     python tests/golden/make_golden.py thermo       # bulk pressure, kT chi_T, c(r) of water
     python tests/golden/make_golden.py solute50_128 # full-size reference (slow, ~minutes)
 """
@@ -30,6 +31,19 @@ def make_chi():
         np.savez_compressed(os.path.join(HERE, "chi_%s.npz" % name), chi=r["chi"], dk=r["dk"], h=r["h"],
                             n=2048, dr=0.05, iterations=r["iterations"], rms=r["rms"])
         print(name, "iterations", r["iterations"], "rms %.2e" % r["rms"], "%.1f s" % (time.time() - t0))
+
+
+def make_drism():
+    """X of 3-site water from the oracle's DRISM with the dielectric constant of the
+    sphere_32 workload."""
+    s = synth.solvent_sites("water3")
+    eps_r = synth.WORKLOADS["sphere_32"]["dielectric"]
+    t0 = time.time()
+    r = rism1d.xrism_solvent(s["q"], s["sigma"], s["eps"], s["rho"], s["species"], s["coords"],
+                             s["temperature"], dielectric=eps_r)
+    np.savez_compressed(os.path.join(HERE, "chi_water3_drism.npz"), chi=r["chi"], dk=r["dk"], n=2048,
+                        dr=0.05, dielectric=eps_r, iterations=r["iterations"], rms=r["rms"])
+    print("water3 DRISM iterations", r["iterations"], "rms %.2e" % r["rms"], "%.1f s" % (time.time() - t0))
 
 
 def make_thermo():
@@ -91,5 +105,7 @@ if __name__ == "__main__":
         make_chi()
     elif what == "thermo":
         make_thermo()
+    elif what == "drism":
+        make_drism()
     else:
         make_full(what)

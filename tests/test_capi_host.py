@@ -109,17 +109,16 @@ def test_product_xrism_matches_oracle_table(lib):
 
 
 def test_product_drism_matches_oracle(lib):
-    """The library's host DRISM (dielectric 78.44) against the oracle's (both to RMS 1e-10;
-    measured max|dX| 1.6e-9), and its refusals: a dielectric constant at or below the XRISM
-    value, a solvent without a dipole."""
+    """The library's host DRISM (dielectric 78.44) against the oracle's stored table (both to
+    RMS 1e-10; measured max|dX| 1.6e-9), and its refusals: a dielectric constant at or below
+    the XRISM value, a solvent without a dipole."""
     from paper_2403_01039_gb300 import capi, synth
-    from oracle import rism1d
+    from conftest import load_chi
     s = synth.water_3site()
-    ref = rism1d.xrism_solvent(s["q"], s["sigma"], s["eps"], s["rho"], s["species"], s["coords"],
-                               s["temperature"], dielectric=78.44)
-    chi, dk, its, rms = capi.xrism(s, dielectric=78.44)
-    assert dk == ref["dk"] and rms < 1e-10
-    assert np.max(np.abs(chi - ref["chi"])) < 1e-7
+    ref, rdk = load_chi("water3_drism")
+    chi, dk, its, rms = capi.xrism(s, dielectric=synth.WORKLOADS["sphere_32"]["dielectric"])
+    assert dk == rdk and rms < 1e-10
+    assert np.max(np.abs(chi - ref)) < 1e-7
     with pytest.raises(RuntimeError, match="XRISM value"):
         capi.xrism(s, dielectric=5.0)
     lj = dict(q=np.zeros(1), sigma=np.array([3.4]), eps=np.array([0.2]), rho=np.array([0.02]),

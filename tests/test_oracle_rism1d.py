@@ -83,6 +83,9 @@ def test_drism_dielectric_limit(eps_r):
                              s["temperature"], dielectric=eps_r)
     assert r["rms"] < 1e-10
     assert abs(_dielectric_limit(s, r["chi"], r["dk"]) - (1.0 - 1.0 / eps_r)) < 3e-5
+    if eps_r == synth.WORKLOADS["sphere_32"]["dielectric"]:       # the stored table is this solve
+        chi, dk = load_chi("water3_drism")
+        assert np.isclose(dk, r["dk"]) and np.max(np.abs(chi - r["chi"])) < 1e-8
 
 
 def test_xrism_dielectric_limit_extrapolated(water_xrism):
