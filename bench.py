@@ -136,13 +136,16 @@ class ClockSampler:
                     reasons=sorted(reasons))
 
 
+NOMINAL_HBM_GBS = 7900.0        # GB300 HBM3e nominal bandwidth, for context beside the measured peak
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback (6.8 TB/s, one earlier GB300 copy measurement; MEASURED_PEAKS.json absent)"
 
 
 def ncu_traffic(kernel, workload):
@@ -409,7 +412,8 @@ def run_ours(args):
     achieved = bytes_per_launch / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
     total_ms = sum(share_ms.values())
     roofline = dict(bound="hbm", kernel=dom, achieved=achieved, peak=peak, unit="GB/s",
-                    frac=achieved / peak, peak_source=peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+                    frac=achieved / peak, peak_source=peak_src,
+                    frac_of_nominal=achieved / NOMINAL_HBM_GBS, nominal_peak=NOMINAL_HBM_GBS,
                     traffic=ncu_traffic(dom, args.workload),
                     algorithmic_bytes_per_launch=bytes_per_launch, avg_launch_ms=per_launch_s * 1e3,
                     timed_launches=kd["timed"], share=share_ms[dom] / total_ms if total_ms else None)
