@@ -29,6 +29,7 @@ unet       the learned-guess network (no counterpart in the paper): 3x3x3
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 except the 1D solvent susceptibility values themselves ("parity unpinned"
-beyond the low-density limit, the RISM-equation identity and chi -> omega as
-rho -> 0); chi is a shared input of both sides, so it cannot break parity.
+beyond the low-density limit, the k -> 0 dielectric limits of XRISM and DRISM,
+and a single-site solute reproducing the solvent's own ion correlations); chi is
+a shared input of both sides, so it cannot break parity.
 """
