@@ -55,14 +55,22 @@ class SineTransform {
             j ^= bit;
             if (i < j) std::swap(buf_[i], buf_[j]);
         }
+        // butterflies in real arithmetic: the same products as the complex operator for
+        // finite values, without its inf/nan recovery path
+        double *z = reinterpret_cast<double *>(buf_.data());
+        const double *w = reinterpret_cast<const double *>(tw_.data());
         for (int len = 2; len <= n; len <<= 1) {
             const int half = len / 2, stride = n / len;
             for (int i = 0; i < n; i += len)
                 for (int k = 0; k < half; ++k) {
-                    const cd u = buf_[i + k];
-                    const cd v = buf_[i + k + half] * tw_[k * stride];
-                    buf_[i + k] = u + v;
-                    buf_[i + k + half] = u - v;
+                    double *pu = z + 2 * (i + k), *pv = z + 2 * (i + k + half);
+                    const double wr = w[2 * k * stride], wi = w[2 * k * stride + 1];
+                    const double vr = pv[0] * wr - pv[1] * wi, vi = pv[0] * wi + pv[1] * wr;
+                    const double ur = pu[0], ui = pu[1];
+                    pu[0] = ur + vr;
+                    pu[1] = ui + vi;
+                    pv[0] = ur - vr;
+                    pv[1] = ui - vi;
                 }
         }
     }
