@@ -63,10 +63,13 @@ def test_sfe_difference_equals_coupling_integral(setup, closure, sfe_kind, order
     assert abs(ti - closed) < 5e-6, (ti, closed)
 
 
-@pytest.mark.parametrize("closure,sfe_kind,nodes", [(cl.HNC, cl.SFE_HNC, 8), (cl.KH, cl.SFE_KH, 16)])
-def test_3d_sfe_difference_equals_coupling_integral(closure, sfe_kind, nodes):
+@pytest.mark.parametrize("closure,sfe_kind,nodes,kgrid", [(cl.HNC, cl.SFE_HNC, 8, "integer"),
+                                                          (cl.KH, cl.SFE_KH, 16, "integer"),
+                                                          (cl.HNC, cl.SFE_HNC, 8, "half")])
+def test_3d_sfe_difference_equals_coupling_integral(closure, sfe_kind, nodes, kgrid):
     """The same identity for the 3D solve and its grid sums dV sum_grid (a sphere at the
-    centre of a 32^3 box at 0.5 A; measured agreement 3e-7 for HNC, 3e-6 for KH)."""
+    centre of a 32^3 box at 0.5 A; measured agreement 3e-7 for HNC, 3e-6 for KH), on the
+    integer and on the half-integer k grid."""
     from oracle import rism3d as orc, potential as pot
     s = synth.water_3site()
     chi, dk = load_chi("water3")
@@ -87,7 +90,7 @@ def test_3d_sfe_difference_equals_coupling_integral(closure, sfe_kind, nodes):
         return out
 
     def solve(e):
-        P = orc.Problem(s, grid, synth.lj_sphere(sigma=SIGMA_U, eps=e))
+        P = orc.Problem(s, grid, synth.lj_sphere(sigma=SIGMA_U, eps=e), kgrid=kgrid)
         return P, orc.solve(P, closure, 1, tol=1e-11, mdiis_nvec=5)
 
     x, w = np.polynomial.legendre.leggauss(nodes)
