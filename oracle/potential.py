@@ -24,11 +24,14 @@ import numpy as np
 from .units import COULOMB, R2_FLOOR, BETA_U_CAP, beta as beta_of
 
 
-def grid_points(n, spacing, origin):
+def grid_points(n, spacing, origin, x_range=None):
     """Cartesian coordinates of every grid point, shape (Nx, Ny, Nz, 3).
 
-    Grid index (i, j, k) sits at origin + (i dx, j dy, k dz)."""
+    Grid index (i, j, k) sits at origin + (i dx, j dy, k dz). ``x_range`` = (x0, x1) keeps
+    only the planes x0 <= i < x1 (same coordinates as in the whole grid)."""
     axes = [origin[d] + spacing[d] * np.arange(n[d], dtype=np.float64) for d in range(3)]
+    if x_range is not None:
+        axes[0] = axes[0][x_range[0]:x_range[1]]
     X, Y, Z = np.meshgrid(*axes, indexing="ij")
     return np.stack([X, Y, Z], axis=-1)
 
@@ -46,15 +49,16 @@ def _pair_r2(points, R, box=None):
 
 
 def beta_u(n, spacing, origin, xyz, q, sig, eps, site_q, site_sig, site_eps, temperature,
-           minimum_image=False):
+           minimum_image=False, x_range=None):
     """Reduced solute-solvent potential beta*u_gamma(r) of Eq. 22 on the grid.
 
     Direct sum over every solute atom at every grid point, no cutoff.
-    Returns an array [n_sites, Nx, Ny, Nz]; beta*u is capped above at BETA_U_CAP."""
+    Returns an array [n_sites, Nx, Ny, Nz] (only the planes of ``x_range`` if given);
+    beta*u is capped above at BETA_U_CAP."""
     b = beta_of(temperature)
-    pts = grid_points(n, spacing, origin)
+    pts = grid_points(n, spacing, origin, x_range)
     box = np.asarray(spacing, dtype=np.float64) * np.asarray(n) if minimum_image else None
-    out = np.zeros((len(site_q),) + tuple(n), dtype=np.float64)
+    out = np.zeros((len(site_q),) + pts.shape[:3], dtype=np.float64)
     for a in range(len(q)):
         r2 = _pair_r2(pts, np.asarray(xyz[a], dtype=np.float64), box)
         r = np.sqrt(r2)
@@ -67,12 +71,12 @@ def beta_u(n, spacing, origin, xyz, q, sig, eps, site_q, site_sig, site_eps, tem
     return np.minimum(out, BETA_U_CAP)
 
 
-def phi_long_range(n, spacing, origin, xyz, q, minimum_image=False):
+def phi_long_range(n, spacing, origin, xyz, q, minimum_image=False, x_range=None):
     """Shared long-range field phi(r) = COULOMB sum_a q_a (1 - e^{-r_a}) / r_a (Eq. 29 without
     the factor beta q_gamma). 1 - e^{-r} is evaluated as -expm1(-r)."""
-    pts = grid_points(n, spacing, origin)
+    pts = grid_points(n, spacing, origin, x_range)
     box = np.asarray(spacing, dtype=np.float64) * np.asarray(n) if minimum_image else None
-    out = np.zeros(tuple(n), dtype=np.float64)
+    out = np.zeros(pts.shape[:3], dtype=np.float64)
     for a in range(len(q)):
         r = np.sqrt(_pair_r2(pts, np.asarray(xyz[a], dtype=np.float64), box))
         out += COULOMB * q[a] * (-np.expm1(-r)) / r

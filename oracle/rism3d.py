@@ -53,9 +53,11 @@ class Problem:
 
     ``minimum_image`` evaluates the real-space potentials with the minimum-image
     convention; it exists only for the whole-cell shift test. ``kgrid`` = "integer" (the
-    periodic grid) or "half" (half-integer k on every axis)."""
+    periodic grid) or "half" (half-integer k on every axis). ``workers`` > 1 evaluates the
+    direct potential sums of Eqs. 22 and 29 over slabs of x planes in that many processes
+    (each grid point's sum is the same as in one process)."""
 
-    def __init__(self, solvent, grid, solute, minimum_image=False, kgrid="integer"):
+    def __init__(self, solvent, grid, solute, minimum_image=False, kgrid="integer", workers=1):
         self.n = tuple(int(v) for v in grid["n"])
         self.spacing = tuple(float(v) for v in grid["spacing"])
         self.origin = tuple(float(v) for v in grid["origin"])
@@ -73,13 +75,14 @@ class Problem:
         q = np.asarray(solute["q"], dtype=np.float64)
         sig = np.asarray(solute["sigma"], dtype=np.float64)
         eps = np.asarray(solute["eps"], dtype=np.float64)
-        # Eq. 22 on the grid
-        self.bu = beta_u(self.n, self.spacing, self.origin, xyz, q, sig, eps,
-                         self.site_q, self.site_sig, self.site_eps, self.temperature,
-                         minimum_image=minimum_image)
-        # Eq. 29 / Eq. 30: f_gamma = beta q_gamma phi, f~_gamma = beta q_gamma Phi~
-        self.phi = phi_long_range(self.n, self.spacing, self.origin, xyz, q,
-                                  minimum_image=minimum_image)
+        # Eq. 22 and Eq. 29 on the grid
+        args = (self.n, self.spacing, self.origin, xyz, q, sig, eps, self.site_q, self.site_sig,
+                self.site_eps, self.temperature, minimum_image)
+        if workers > 1:
+            self.bu, self.phi = _potentials_parallel(args, int(workers))
+        else:
+            self.bu, self.phi = _potentials_slab(args + (None,))
+        # Eq. 30: f_gamma = beta q_gamma phi, f~_gamma = beta q_gamma Phi~
         if kgrid not in ("integer", "half"):
             raise ValueError("kgrid must be 'integer' or 'half'")
         self.kgrid = kgrid
@@ -123,6 +126,24 @@ class Problem:
         return h + 1.0 - g, g, d                                             # Eq. 33
 
 
+def _potentials_slab(args):
+    """beta*u (Eq. 22) and phi (Eq. 29) on the x planes args[-1] = (x0, x1) (None: all)."""
+    n, spacing, origin, xyz, q, sig, eps, sq, ss, se, temp, mi, xr = args
+    bu = beta_u(n, spacing, origin, xyz, q, sig, eps, sq, ss, se, temp, minimum_image=mi, x_range=xr)
+    phi = phi_long_range(n, spacing, origin, xyz, q, minimum_image=mi, x_range=xr)
+    return bu, phi
+
+
+def _potentials_parallel(args, workers):
+    import multiprocessing as mp
+    nx = args[0][0]
+    edges = np.linspace(0, nx, min(workers, nx) + 1).astype(int)
+    jobs = [args + ((int(a), int(b)),) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        parts = pool.map(_potentials_slab, jobs)
+    return (np.concatenate([p[0] for p in parts], axis=1), np.concatenate([p[1] for p in parts], axis=0))
+
+
 def closure_stages(kind, pse_order):
     """Closure continuation (the paper is silent): an exponential closure started from
     t = f overflows for charged solutes, so PSE-n is reached through PSE-1 (= KH), PSE-2, ...,
@@ -141,22 +162,35 @@ STAGE_TOL = 1.0e-4   # tolerance of every stage but the last one (the last uses 
 
 def solve(problem, kind=cl.KH, pse_order=3, tol=1e-6, max_iter=10000, mdiis_nvec=5,
           mdiis_damp=0.7, dynamic_damp=False, t_guess=None, verbose=False, accel="mdiis",
-          anderson_s=(0.2, 0.0)):
+          anderson_s=(0.2, 0.0), snapshots=()):
     """Run steps 1-7 (per closure stage) and return a dict with t, g, h, c, d, the total
     iteration count and the RMS history. ``accel`` is "mdiis" (Eq. 40) or "anderson" (the
     modified Anderson method of Eqs. 34-39 with two histories, shifts ``anderson_s`` and
-    mixing b = ``mdiis_damp``)."""
+    mixing b = ``mdiis_damp``).
+
+    ``snapshots``: tolerances above ``tol``; for each, the result also holds (under
+    ``"snapshots"``, keyed by the tolerance) the input t of the first iteration of the last
+    closure stage whose RMS residual fell below it, with its iteration count: the solution a
+    solve stopped at that tolerance returns, taken from the same run.
+
+    The Gram entries <R_i, R_j> of the stored residuals do not change while the pair stays
+    in the history, so each iteration computes only the new residual's row (the same sums
+    a full recomputation gives)."""
     if accel == "anderson":
         mdiis_nvec = 3
     P = problem
     t = P.f.copy() if t_guess is None else np.array(t_guess, dtype=np.float64, copy=True)  # step 1
     stages = closure_stages(kind, pse_order)
     rms_log, mad_log = [], []
+    snaps = {}
+    pending = sorted((float(s) for s in snapshots if s > tol), reverse=True)
     converged = False
     total = 0
     for si, (skind, sorder) in enumerate(stages):
-        stol = tol if si == len(stages) - 1 else max(tol, STAGE_TOL)
+        last = si == len(stages) - 1
+        stol = tol if last else max(tol, STAGE_TOL)
         hist_t, hist_R = [], []
+        gram = np.zeros((0, 0))
         converged = False
         while total < max_iter:
             total += 1
@@ -165,25 +199,31 @@ def solve(problem, kind=cl.KH, pse_order=3, tol=1e-6, max_iter=10000, mdiis_nvec
             rms_log.append(rms)
             mad_log.append(float(np.mean(np.abs(R))))
             if verbose and (total % 20 == 0 or total < 5):
-                print("iter %d stage %d rms %.3e" % (total, si, rms))
+                print("iter %d stage %d rms %.3e" % (total, si, rms), flush=True)
             if not np.isfinite(rms):
                 break
+            while last and pending and rms < pending[0]:
+                snaps[pending.pop(0)] = dict(t=t.copy(), iterations=total, rms=rms)
             if rms < stol:
                 converged = True
                 break
             if total >= max_iter:
                 break
             # step 6: MDIIS
+            row = np.array([float(np.sum(Ri * R)) for Ri in hist_R] + [float(np.sum(R * R))])
             hist_t.append(t)
             hist_R.append(R)
-            if len(hist_R) > mdiis_nvec:
+            k = len(hist_R)
+            grown = np.empty((k, k))
+            grown[:k - 1, :k - 1] = gram
+            grown[k - 1, :] = row
+            grown[:, k - 1] = row
+            gram = grown
+            if k > mdiis_nvec:
                 hist_t.pop(0)
                 hist_R.pop(0)
-            k = len(hist_R)
-            B = np.empty((k, k))
-            for i in range(k):
-                for j in range(i, k):
-                    B[i, j] = B[j, i] = float(np.sum(hist_R[i] * hist_R[j]))
+                gram = gram[1:, 1:]
+            B = gram.copy()
             if accel == "anderson":
                 c, dropped = anderson.coefficients(B, *anderson_s), 0
             else:
@@ -191,6 +231,7 @@ def solve(problem, kind=cl.KH, pse_order=3, tol=1e-6, max_iter=10000, mdiis_nvec
             for _ in range(dropped):
                 hist_t.pop(0)
                 hist_R.pop(0)
+            gram = gram[dropped:, dropped:]
             eta = mdiis.damping(rms, mdiis_damp, dynamic_damp)
             t = sum(ci * (ti + eta * Ri) for ci, ti, Ri in zip(c, hist_t, hist_R))
         if not converged:
@@ -199,7 +240,16 @@ def solve(problem, kind=cl.KH, pse_order=3, tol=1e-6, max_iter=10000, mdiis_nvec
     h = g - 1.0
     c = h - t
     return dict(t=t, g=g, h=h, c=c, d=d, iterations=total, converged=converged,
-                rms=rms_log[-1] if rms_log else float("nan"), rms_log=rms_log, mad_log=mad_log)
+                rms=rms_log[-1] if rms_log else float("nan"), rms_log=rms_log, mad_log=mad_log,
+                snapshots=snaps)
+
+
+def solution_from_t(problem, t, kind, pse_order=3):
+    """The returned fields of a solve stopped at input t: g, d from its closure, h = g - 1,
+    c = h - t (the returned-solution reading)."""
+    d, g = problem.closure(t, kind, pse_order)
+    h = g - 1.0
+    return dict(t=t, g=g, h=h, c=h - t, d=d)
 
 
 def sfe(problem, sol, kind, pse_order=3):

@@ -7,6 +7,7 @@ touches the CUDA path. Run from the repository root:
     python tests/golden/make_golden.py drism        # 3-site water from DRISM (eps 78.44)
     python tests/golden/make_golden.py thermo       # bulk pressure, kT chi_T, c(r) of water
     python tests/golden/make_golden.py solute50_128 # full-size reference (slow, ~minutes)
+    python tests/golden/make_golden.py globule2000_256  # protein-scale reference (hours)
 """
 import os
 import sys
@@ -99,6 +100,52 @@ def make_full(workload, closures=((cl.KH, 3, "kh"), (cl.PSE, 3, "pse3")), tols=(
             np.savez_compressed(os.path.join(HERE, "%s_reference.npz" % workload), **out)
 
 
+def make_globule(workload="globule2000_256", tol=1e-10, snapshots=(1e-6, 1e-8), workers=6):
+    """One KH oracle solve of the protein-scale workload to ``tol``, with the solutions a
+    solve stopped at each of ``snapshots`` returns (the same run). Stores, for each
+    tolerance, g, c and t at 4096 seeded grid points (all sites), the whole x = N/2 plane
+    of g (all sites; float64 at the loosest tolerance, float32 otherwise), the KH and GF
+    SFE (total and per site) and the iteration count, in tests/golden/<workload>_reference.npz."""
+    w = synth.WORKLOADS[workload]
+    s = synth.solvent_sites(w["solvent"])
+    chi = np.load(os.path.join(HERE, "chi_%s.npz" % w["solvent"]))
+    solv = dict(q=s["q"], sigma=s["sigma"], eps=s["eps"], rho=s["rho"],
+                temperature=s["temperature"], chi=chi["chi"], dk=float(chi["dk"]))
+    grid = synth.cubic_grid(w["n"], w["spacing"])
+    t0 = time.time()
+    P = rism3d.Problem(solv, grid, synth.workload_solute(workload), workers=workers)
+    print("setup %.0f s" % (time.time() - t0), flush=True)
+    pts = sample_points(w["n"], 4096, 7)
+    idx = (slice(None), pts[:, 0], pts[:, 1], pts[:, 2])
+    xp = w["n"] // 2
+    sol = rism3d.solve(P, cl.KH, 1, tol=tol, mdiis_nvec=w["mdiis_nvec"], verbose=True,
+                       snapshots=snapshots)
+    print("solve %.0f s, %d iterations, converged %s" % (time.time() - t0, sol["iterations"], sol["converged"]),
+          flush=True)
+    out = dict(points=pts, plane_x=xp)
+    loosest = max(snapshots) if snapshots else tol
+    runs = [(tol, sol["t"], sol["iterations"], sol["rms"])]
+    runs += [(k, v["t"], v["iterations"], v["rms"]) for k, v in sol["snapshots"].items()]
+    for tl, t, iters, rms in runs:
+        r = rism3d.solution_from_t(P, t, cl.KH, 1)
+        tot, per = rism3d.sfe(P, r, cl.SFE_KH, 1)
+        gf, gf_per = rism3d.sfe(P, r, cl.SFE_GF, 1)
+        key = "kh_%g" % tl
+        out[key + "_iterations"] = iters
+        out[key + "_rms"] = rms
+        out[key + "_sfe"] = tot
+        out[key + "_sfe_per_site"] = per
+        out[key + "_sfe_gf"] = gf
+        out[key + "_g"] = r["g"][idx]
+        out[key + "_c"] = r["c"][idx]
+        out[key + "_t"] = r["t"][idx]
+        out[key + "_g_max"] = float(r["g"].max())
+        plane = r["g"][:, xp]
+        out[key + "_g_plane"] = plane if tl == loosest else plane.astype(np.float32)
+        print(workload, tl, iters, tot, gf, flush=True)
+    np.savez_compressed(os.path.join(HERE, "%s_reference.npz" % workload), **out)
+
+
 if __name__ == "__main__":
     what = sys.argv[1] if len(sys.argv) > 1 else "chi"
     if what == "chi":
@@ -107,5 +154,7 @@ if __name__ == "__main__":
         make_thermo()
     elif what == "drism":
         make_drism()
+    elif what.startswith("globule"):
+        make_globule(what)
     else:
         make_full(what)
