@@ -301,16 +301,19 @@ rism3d_status rism3d_reset_stats(rism3d_ctx *ctx);
 
 /* Solvation free energy (same integrands as rism3d_get_sfe) from caller fields, without
  * allocating device memory. The paper has no counterpart: this entry point exists for
- * callers that cannot allocate - for example code running while a CUDA stream is being
- * captured into a graph, or a host framework that owns every device allocation - and needs
- * no context. h, c and (for RISM3D_SFE_PSE only, else may be NULL) d = -beta u + t are
- * device arrays [n_sites][n_points] of FP64; rho is host [n_sites]; per_site (host
- * [n_sites]) may be NULL. Runs on cuda_stream (NULL = default stream) and returns after it
- * has finished. Its scratch is a static device array of 8 x 152 + 8 doubles that every GPU
+ * callers that cannot allocate - a host framework that owns every device allocation (a
+ * memory pool holding the whole device), or a latency-critical loop in which cudaMalloc
+ * or cudaFree would synchronise the device - and needs no context. h, c and (for
+ * RISM3D_SFE_PSE only, else may be NULL) d = -beta u + t are arrays [n_sites][n_points] of
+ * FP64 in device (or managed) memory of the current device, checked before any launch:
+ * other pointers give RISM3D_EINVAL. rho is host [n_sites]; per_site (host [n_sites]) may
+ * be NULL. Runs on cuda_stream (NULL = default stream) and synchronises that stream before
+ * it returns. Its scratch is a static device array of 8 x 152 + 8 doubles that every GPU
  * that loads the library keeps until the process exits: n_sites above 8 is rejected with
  * RISM3D_EINVAL. The first call on each device looks up that array's device address, so
  * make it before any stream capture. Every call shares the array (each call rewrites all it
- * reads, so nothing needs clearing); calls that overlap on the GPU race on it. */
+ * reads, so nothing needs clearing); calls that overlap on the GPU race on it. Launch
+ * failures give RISM3D_ECUDA before anything is copied back. */
 rism3d_status rism3d_sfe_noalloc(int n_sites, long long n_points, const double *h, const double *c,
                                  const double *d, const double *rho, double temperature, double dV,
                                  int kind, int pse_order, double *total, double *per_site,

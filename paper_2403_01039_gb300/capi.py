@@ -220,20 +220,25 @@ def sfe_noalloc(h, c, rho, temperature, dV, kind="kh", pse_order=3, d=None, stre
     """rism3d_sfe_noalloc on CUDA float64 tensors h, c (and d for PSE) of shape
     [n_sites, ...]: the SFE with the library's static scratch, no device allocation.
     Returns (total, per_site)."""
+    import torch
     lib = load()
     n_sites = h.shape[0]
     n_points = h.numel() // n_sites
     for x in (h, c) + ((d,) if d is not None else ()):
         if x.dtype.itemsize != 8 or not x.is_cuda or not x.is_contiguous() or x.numel() != h.numel():
             raise ValueError("h, c, d must be contiguous float64 CUDA tensors of one shape")
+        if x.device != h.device:
+            raise ValueError("h, c, d must be on one device")
     rho_a, prho = _arr(rho)
     tot = ctypes.c_double()
     per = np.zeros(n_sites)
-    st = lib.rism3d_sfe_noalloc(n_sites, n_points, ctypes.c_void_p(h.data_ptr()), ctypes.c_void_p(c.data_ptr()),
-                                ctypes.c_void_p(d.data_ptr() if d is not None else 0), prho,
-                                float(temperature), float(dV), SFE_KINDS[kind], int(pse_order),
-                                ctypes.byref(tot), per.ctypes.data_as(_dp),
-                                ctypes.c_void_p(stream.cuda_stream if stream is not None else 0))
+    with torch.cuda.device(h.device):
+        st = lib.rism3d_sfe_noalloc(n_sites, n_points, ctypes.c_void_p(h.data_ptr()),
+                                    ctypes.c_void_p(c.data_ptr()),
+                                    ctypes.c_void_p(d.data_ptr() if d is not None else 0), prho,
+                                    float(temperature), float(dV), SFE_KINDS[kind], int(pse_order),
+                                    ctypes.byref(tot), per.ctypes.data_as(_dp),
+                                    ctypes.c_void_p(stream.cuda_stream if stream is not None else 0))
     if st != OK:
         raise RismError(st, lib.rism3d_last_error(None).decode())
     return tot.value, per

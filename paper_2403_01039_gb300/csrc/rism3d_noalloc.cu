@@ -2,13 +2,12 @@
 // device memory.
 //
 // rism3d_get_sfe reduces into per-block partial sums held in the context's workspace. Some
-// callers have no context and cannot obtain scratch memory: code running while a CUDA
-// stream is being captured into a graph (cudaMalloc during a global-mode capture is an
-// error that invalidates the capture), code whose device memory budget is fixed in advance
-// by a host framework that owns every allocation, and latency-critical loops where an
-// allocation would synchronise the device. rism3d_sfe_noalloc serves them: its scratch is
-// the file-scope array below, which every GPU that loads the library holds until the
-// process exits.
+// callers have no context and cannot obtain scratch memory: code whose device memory
+// budget is fixed in advance by a host framework that owns every allocation (a memory pool
+// that hands out all of the device), and latency-critical loops where a cudaMalloc or
+// cudaFree would synchronise the device. rism3d_sfe_noalloc serves them: its scratch is the
+// file-scope array below, which every GPU that loads the library holds until the process
+// exits. The call waits for its stream to finish before it returns.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -86,6 +85,16 @@ rism3d_status bad(rism3d_status st, const char *msg) {
     return st;
 }
 
+// True if p is device (or managed) memory that device dev can read.
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();     // clear the error this query left
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
 }  // namespace
 
 extern "C" rism3d_status rism3d_sfe_noalloc(int n_sites, long long n_points, const double *h,
@@ -110,6 +119,8 @@ extern "C" rism3d_status rism3d_sfe_noalloc(int n_sites, long long n_points, con
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return bad(RISM3D_ECUDA, "rism3d_sfe_noalloc: no usable current device");
+    if (!on_device(h, dev) || !on_device(c, dev) || (kind == RISM3D_SFE_PSE && !on_device(d, dev)))
+        return bad(RISM3D_EINVAL, "rism3d_sfe_noalloc: h, c and d must be device memory of the current device");
     double *scratch = nullptr;
     {
         // One-time set-up per device, with that device current: the device address of the
@@ -132,11 +143,16 @@ extern "C" rism3d_status rism3d_sfe_noalloc(int n_sites, long long n_points, con
     k_sfe_fields<<<dim3(kScratchBlocks, n_sites), 256, 0, s>>>(h, c, kind == RISM3D_SFE_PSE ? d : nullptr,
                                                               n_points, kind, pse_order, scratch);
     k_sfe_fields_finish<<<1, 32, 0, s>>>(scratch, n_sites);
+    cudaError_t e = cudaGetLastError();        // launch errors, before anything is copied
+    if (e != cudaSuccess) {
+        char msg[200];
+        snprintf(msg, sizeof(msg), "rism3d_sfe_noalloc: launch: %s", cudaGetErrorString(e));
+        return bad(RISM3D_ECUDA, msg);
+    }
     double sums[kScratchSites];
-    cudaError_t e = cudaMemcpyAsync(sums, scratch + kScratchSites * kScratchBlocks,
-                                    (size_t)n_sites * sizeof(double), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(sums, scratch + kScratchSites * kScratchBlocks, (size_t)n_sites * sizeof(double),
+                        cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         char msg[200];
         snprintf(msg, sizeof(msg), "rism3d_sfe_noalloc: %s", cudaGetErrorString(e));

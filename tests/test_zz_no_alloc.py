@@ -1,10 +1,11 @@
 """rism3d_sfe_noalloc: the SFE entry point that allocates no device memory.
 
-Some callers cannot allocate: code running while its stream is captured into a CUDA graph,
-or a host framework that owns every device allocation. This test checks, on the GPU and
-through the C ABI, that the no-allocation entry point gives the same SFE as the context's
-rism3d_get_sfe, on two calls in a row (the static scratch is shared between calls), and
-that it rejects more sites than its static scratch holds. The file is named so that pytest
+Some callers cannot allocate: a host framework that owns every device allocation, or a
+latency-critical loop in which cudaMalloc would synchronise the device. This test checks, on
+the GPU and through the C ABI, that the no-allocation entry point gives the same SFE as the
+context's rism3d_get_sfe, on two calls in a row (the static scratch is shared between
+calls), that it rejects more sites than its static scratch holds, and that it rejects
+fields outside device memory before launching anything. The file is named so that pytest
 collects it last."""
 import numpy as np
 import pytest
@@ -53,3 +54,20 @@ def test_noalloc_rejects_too_many_sites():
     with pytest.raises(capi.RismError) as e:
         capi.sfe_noalloc(h, h, np.full(n, 0.03), 298.15, 0.125)
     assert e.value.status == capi.EINVAL and "static scratch" in str(e.value)
+
+
+def test_noalloc_rejects_host_memory():
+    """Pinned host memory (which the GPU could even read) is refused by the pointer check,
+    before any kernel runs."""
+    import ctypes
+    lib = capi.load()
+    h = torch.zeros((1, 64), dtype=torch.float64, device="cuda")
+    host = torch.zeros((1, 64), dtype=torch.float64).pin_memory()
+    rho = np.full(1, 0.03)
+    tot = ctypes.c_double()
+    for hp, cp in ((host, h), (h, host)):
+        st = lib.rism3d_sfe_noalloc(1, 64, ctypes.c_void_p(hp.data_ptr()), ctypes.c_void_p(cp.data_ptr()),
+                                    None, rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 298.15, 0.125,
+                                    capi.SFE_KINDS["kh"], 1, ctypes.byref(tot), None, None)
+        assert st == capi.EINVAL
+        assert "device memory" in lib.rism3d_last_error(None).decode()
