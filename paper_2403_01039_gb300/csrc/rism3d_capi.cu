@@ -148,6 +148,7 @@ struct rism3d_ctx {
     Ctrl *ctrl_host = nullptr;                 // pinned
     cudaGraphExec_t graph = nullptr;
     bool has_solute = false;
+    bool offset_live = false;                  // the iterate may have a nonzero offset tau0
     int cur_slot = 0;
     int last_kind = kKH, last_order = 1;
     std::vector<double> atom_host;
@@ -194,8 +195,8 @@ static rism3d_status fail(rism3d_ctx *ctx, rism3d_status st, const char *fmt, ..
 namespace {
 
 struct Layout {
-    size_t ctrl, bu, phi, w, psi, spec, X, R, T, anchor, phase, table, tw, partials, sfe, atoms, sites, staging,
-        total;
+    size_t ctrl, bu, phi, w, wref, psi, spec, X, R, T, tau0, anchor, phase, table, tw, partials, sfe, atoms,
+        sites, staging, total;
 };
 
 struct Geometry {
@@ -221,11 +222,13 @@ Layout make_layout(const Geometry &g) {
     L.bu = take((size_t)g.nv * g.G * g.s);
     L.phi = take((size_t)g.G * g.s);
     L.w = take((size_t)g.nv * g.G * g.s);
+    L.wref = take((size_t)g.nv * g.G * g.s);
     L.psi = take(specN * c);
     L.spec = take((size_t)g.nv * specN * c);
     L.X = take((size_t)g.M * g.nv * g.G * g.s);
     L.R = take((size_t)g.M * g.nv * g.G * g.s);
     L.T = take((size_t)g.nv * g.G * g.s);
+    L.tau0 = take((size_t)g.nv * g.G * g.s);
     L.anchor = take((size_t)2 * g.nv * g.G * g.s);
     L.phase = take((size_t)kPhaseChunk * (g.Nx + g.Ny + g.Kz + 1) * c);
     L.table = take((size_t)g.nk * (g.nv + 1) * g.nv * g.s);
@@ -355,6 +358,7 @@ void fill_fields(rism3d_ctx *ctx, const Geometry &g, const Layout &L, Fields<T> 
     f.bu = reinterpret_cast<T *>(b + L.bu);
     f.phi = reinterpret_cast<T *>(b + L.phi);
     f.w = reinterpret_cast<T *>(b + L.w);
+    f.wref = reinterpret_cast<T *>(b + L.wref);
     f.psi = reinterpret_cast<C *>(b + L.psi);
     f.psi_nyq = f.psi + f.specN;
     f.spec = reinterpret_cast<C *>(b + L.spec);
@@ -362,8 +366,9 @@ void fill_fields(rism3d_ctx *ctx, const Geometry &g, const Layout &L, Fields<T> 
     f.X = reinterpret_cast<T *>(b + L.X);
     f.R = reinterpret_cast<T *>(b + L.R);
     f.Tc = reinterpret_cast<T *>(b + L.T);
-    f.csr_a = reinterpret_cast<T *>(b + L.anchor);
-    f.h_a = f.csr_a + (long long)g.nv * g.G;
+    f.tau0 = reinterpret_cast<T *>(b + L.tau0);
+    f.g_a = reinterpret_cast<T *>(b + L.anchor);
+    f.h_a = f.g_a + (long long)g.nv * g.G;
     f.phase = reinterpret_cast<C *>(b + L.phase);
     f.table = reinterpret_cast<T *>(b + L.table);
     f.nk = g.nk;
@@ -602,8 +607,8 @@ rism3d_status iteration(rism3d_ctx *ctx, bool with_mdiis) {
 // site-point (P = n_v Nx Ny Nz of them, s bytes per real, z = (Kz + 1) / Kz for the half
 // spectrum) plane_fwd moves the history it combines (Y_i per stored pair, R_i as well
 // under dynamic damping, + 1 for the new tau, or 1 to load tau), w (1), the spectrum it
-// writes (z) and the anchor (1 read, 1 write on
-// refresh); pencil reads and writes the spectrum (2 z) plus Psi (z/n_v) until the first
+// writes (z) and the anchor g_a (1 read, 1 write on refresh; a refresh also reads and
+// writes tau0, writes w and rewrites each stored Y it combines); pencil reads and writes the spectrum (2 z) plus Psi (z/n_v) until the first
 // anchor; plane_inv reads the spectrum (z), tau and w (2), the history residuals, the
 // anchor h_a, and writes R and Y (2) and h_a on refresh.
 void account_iterations(rism3d_ctx *ctx, const Ctrl &c) {
@@ -616,14 +621,16 @@ void account_iterations(rism3d_ctx *ctx, const Ctrl &c) {
     if (ctx->fp32() && split_planes(ctx->f32)) {
         // split passes: the element kernels also write / read the transform input / output
         ctx->stats.bytes[10] += P * s * ((double)c.acc_fwd_units + (double)c.acc_upd_r + 2.0 * it +
-                                         (double)c.acc_anchor + (double)c.acc_refresh);
+                                         (double)c.acc_anchor + 4.0 * (double)c.acc_refresh +
+                                         2.0 * (double)c.acc_shift);
         ctx->stats.bytes[11] += P * s * it * (1.0 + z);
         ctx->stats.bytes[12] += P * s * it * (z + 1.0);
         ctx->stats.bytes[13] += P * s * (it * 5.0 + (double)c.acc_hist + (double)c.acc_anchor +
                                          (double)c.acc_refresh);
     } else {
         ctx->stats.bytes[0] += P * s * ((double)c.acc_fwd_units + (double)c.acc_upd_r + it * (1.0 + z) +
-                                        (double)c.acc_anchor + (double)c.acc_refresh);
+                                        (double)c.acc_anchor + 4.0 * (double)c.acc_refresh +
+                                        2.0 * (double)c.acc_shift);
         ctx->stats.bytes[2] += P * s * (it * (z + 4.0) + (double)c.acc_hist + (double)c.acc_anchor +
                                         (double)c.acc_refresh);
     }
@@ -724,6 +731,7 @@ rism3d_status to_working(rism3d_ctx *ctx, const double *src, int on_device, int 
         CUDA_TRY(ctx, launch_guess_from_t<float>(ctx->f32, slot, dsrc, ctx->stream));
     else
         CUDA_TRY(ctx, launch_guess_from_t<double>(ctx->f64, slot, dsrc, ctx->stream));
+    ctx->offset_live = false;
     return RISM3D_OK;
 }
 
@@ -943,6 +951,7 @@ rism3d_status rism3d_set_solute(rism3d_ctx *ctx, int n_atoms, const double *xyz,
         tm.stop(P * sb);
     }
     ctx->cur_slot = 0;
+    ctx->offset_live = false;
     ctx->n_atoms = n_atoms;
     ctx->has_solute = true;
     ctx->last_kind = kKH;
@@ -974,6 +983,13 @@ static rism3d_status solve_begin(rism3d_ctx *ctx, int closure, int pse_order, do
     rism3d_status st = build_graph(ctx);
     if (st != RISM3D_OK) return st;
     if (!ctx->chunk_ev) CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->chunk_ev, cudaEventDisableTiming));
+    if (ctx->offset_live) {              // restart from the last iterate with tau0 = 0
+        if (ctx->fp32())
+            CUDA_TRY(ctx, launch_flatten<float>(ctx->f32, ctx->stream));
+        else
+            CUDA_TRY(ctx, launch_flatten<double>(ctx->f64, ctx->stream));
+    }
+    ctx->offset_live = true;
     Ctrl &c = *ctx->ctrl_host;
     reset_ctrl(ctx, c);
     closure_stages(closure, pse_order, tol, c);
@@ -1234,7 +1250,10 @@ static rism3d_status guess_crop(rism3d_ctx *ctx, int mode, const int *corner, in
         CUDA_TRY(ctx, launch_guess_crop<float>(ctx->f32, mode, slot, corner, crop, out, in, ctx->stream));
     else
         CUDA_TRY(ctx, launch_guess_crop<double>(ctx->f64, mode, slot, corner, crop, out, in, ctx->stream));
-    if (mode == 2) ctx->cur_slot = 0;
+    if (mode == 2) {
+        ctx->cur_slot = 0;
+        ctx->offset_live = false;
+    }
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return RISM3D_OK;
 }

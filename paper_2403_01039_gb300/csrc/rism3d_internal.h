@@ -83,7 +83,8 @@ struct Ctrl {
     int hist_slot[kMaxHist];
     double rms;                     // RMS of the last residual
     // defect-correction anchor: h = h_a + L(c^sr - c^sr_a) with L the linear map of
-    // steps 3-5; refreshed (c^sr_a = c^sr, h_a = h) whenever the RMS falls below next_refresh
+    // steps 3-5; refreshed (g_a = g, h_a = h and the iterate offset tau0 moved to the current
+    // iterate) whenever the RMS falls below next_refresh
     int anchor_valid;
     int refresh;
     double next_refresh;
@@ -94,6 +95,7 @@ struct Ctrl {
     long long acc_hist;             // history residuals read by plane_inv
     long long acc_anchor;           // iterations that read the anchor (plane_fwd and plane_inv)
     long long acc_refresh;          // iterations that wrote the anchor
+    long long acc_shift;            // stored Y fields rewritten in the new offset on refresh
     long long acc_psi;              // iterations whose pencil pass read Psi
     double B[kMaxHist * kMaxHist];  // Gram matrix indexed by ring slot
 };
@@ -112,12 +114,14 @@ struct Fields {
     long long specN;                // Nx * Ny * Kz complex values per site (kz < Kz)
     T *bu;                          // [nv][G] beta * u (outputs and SFE)
     T *phi;                         // [G] long-range field phi (f_g = beta q_g phi)
-    T *w;                           // [nv][G] f - beta*u; the iteration uses d = w + tau
+    T *w;                           // [nv][G] f - beta*u + tau0; the iteration uses d = w + delta
+    T *wref;                        // [nv][G] f - beta*u (w with tau0 = 0)
     C *psi, *psi_nyq;               // beta Phi~ / dV on [Nx][Ny][Kz] and the kz = Kz plane [Nx][Ny]
     C *spec, *spec_nyq;             // [nv][Nx][Ny][Kz], [nv][Nx][Ny]
     T *X, *R;                       // ring [M][nv][G]: X holds Y = tau + eta R, R the residual
-    T *Tc;                          // [nv][G] the current iterate tau = t - f
-    T *csr_a, *h_a;                 // anchor fields [nv][G]
+    T *Tc;                          // [nv][G] the current iterate offset delta = tau - tau0
+    T *tau0;                        // [nv][G] iterate offset: tau = t - f = tau0 + delta
+    T *g_a, *h_a;                   // anchor fields [nv][G]: g and h at the anchor point
     C *phase;                       // per-atom axis phase tables [kPhaseChunk][Nx + Ny + Kz + 1]
     T *table;                       // [nk][nv + 1][nv]: X_ag / G and the charge row -Q_g / G
     int nk;
@@ -166,6 +170,8 @@ cudaError_t launch_longrange(const Fields<T> &f, const double *atoms, int n_atom
 template <typename T> cudaError_t launch_init_guess(const Fields<T> &f, int slot, cudaStream_t s);
 template <typename T>
 cudaError_t launch_guess_from_t(const Fields<T> &f, int slot, const double *src, cudaStream_t s);
+// tau = tau0 + delta -> delta, tau0 = 0, w = wref (before a solve restarts from its iterate)
+template <typename T> cudaError_t launch_flatten(const Fields<T> &f, cudaStream_t s);
 // field: 1 g, 2 c, 3 h, 4 t, 5 beta u, 6 phi, 7 R
 template <typename T>
 cudaError_t launch_get_field(const Fields<T> &f, int field, int slot, int kind, int order,

@@ -566,8 +566,9 @@ struct FwdArgs {
     const T *dcoef;              // [MAXH] coefficients of R_i (dynamic damping only)
     const long long *slot_off;   // [MAXH] ring offsets of the combined pairs (shared memory)
     int upd_n, upd_r, do_update, kind, order, anchor, refresh;
-    T *tcur, *ca;                // this block's part of the new iterate and of c^sr_a
-    const T *wp;                 // this block's part of w = f - beta u
+    T *tcur, *ga;                // this block's part of the iterate offset delta and of g_a
+    T *wp;                       // this block's part of w = f - beta u + tau0 (d = w + delta)
+    T *t0;                       // this block's part of tau0 (written on refresh)
     const typename Cx<T>::type *pre;   // half grid: exp(-i pi p / Kz) per packed element, else null
 };
 
@@ -575,6 +576,39 @@ struct FwdArgs {
 // rows (e = row * Kz + m; complex element m packs the reals 2m, 2m + 1), written into the
 // row buffer. tid / nthr split them, two elements per thread and step with every load
 // issued before any store.
+//
+// The iterate is tau = tau0 + delta: the stored history Y_i and the current field hold
+// delta, w holds f - beta u + tau0 and the anchor holds g_a, the closure's g at the anchor
+// point. With c^sr = g - 1 - tau (Eq. 31) the transform input c^sr - c^sr_a is then
+// (g - g_a) - delta, which stays exact where the solute core makes g = g_a = 0 and |tau| is
+// in the hundreds: no rounding at the size of tau enters the iteration. A refresh moves the
+// offset to the current iterate (tau0 += delta, w += delta, Y_i -= delta, delta = 0) and
+// stores g_a = g.
+// Refresh of one packed pair at offset o: the offset moves to the current iterate.
+template <typename T, int MAXH>
+__device__ __forceinline__ void fwd_refresh(const Fields<T> &f, const FwdArgs<T, MAXH> &A, long long o,
+                                            typename Vec2<T>::type t, typename Vec2<T>::type dv,
+                                            typename Vec2<T>::type g) {
+    typedef typename Vec2<T>::type V2;
+    V2 t0 = ld2(A.t0 + o);
+    t0.x += t.x;
+    t0.y += t.y;
+    *reinterpret_cast<V2 *>(A.t0 + o) = t0;
+    *reinterpret_cast<V2 *>(A.wp + o) = dv;       // w + delta: the new anchor point's d
+    *reinterpret_cast<V2 *>(A.ga + o) = g;
+    V2 z;
+    z.x = z.y = (T)0;
+    *reinterpret_cast<V2 *>(A.tcur + o) = z;
+    if (A.do_update)
+        for (int i = 0; i < A.upd_n; ++i) {       // the stored pairs in the new coordinates
+            T *yb = f.X + A.slot_off[i];
+            V2 y = ld2(yb + o);
+            y.x -= t.x;
+            y.y -= t.y;
+            *reinterpret_cast<V2 *>(yb + o) = y;
+        }
+}
+
 template <typename T, int MAXH>
 __device__ __forceinline__ void fwd_elements(const Fields<T> &f, const FwdArgs<T, MAXH> &A,
                                              typename Cx<T>::type *buf, int y0, int e0, int e1, int tid,
@@ -624,33 +658,35 @@ __device__ __forceinline__ void fwd_elements(const Fields<T> &f, const FwdArgs<T
         const V2 wA = ld2(A.wp + oA), wB = ld2(A.wp + oB);
         V2 aA, aB;
         if (A.anchor) {
-            aA = ld2(A.ca + oA);
-            aB = ld2(A.ca + oB);
+            aA = ld2(A.ga + oA);
+            aB = ld2(A.ga + oB);
+        } else {
+            aA.x = aA.y = aB.x = aB.y = (T)1;   // no anchor: c^sr = (g - 1) - tau
         }
-        V2 cA, cB;
-        cA.x = closure_g(wA.x + tA.x, A.kind, A.order) - (T)1 - tA.x;
-        cA.y = closure_g(wA.y + tA.y, A.kind, A.order) - (T)1 - tA.y;
-        cB.x = closure_g(wB.x + tB.x, A.kind, A.order) - (T)1 - tB.x;
-        cB.y = closure_g(wB.y + tB.y, A.kind, A.order) - (T)1 - tB.y;
-        C dA = cmk(cA.x, cA.y), dB = cmk(cB.x, cB.y);
-        if (A.anchor) {                        // transform only c^sr - c^sr_a
-            dA.x -= aA.x;
-            dA.y -= aA.y;
-            dB.x -= aB.x;
-            dB.y -= aB.y;
-        }
+        V2 dvA, dvB, gA, gB;
+        dvA.x = wA.x + tA.x;
+        dvA.y = wA.y + tA.y;
+        dvB.x = wB.x + tB.x;
+        dvB.y = wB.y + tB.y;
+        gA.x = closure_g(dvA.x, A.kind, A.order);
+        gA.y = closure_g(dvA.y, A.kind, A.order);
+        gB.x = closure_g(dvB.x, A.kind, A.order);
+        gB.y = closure_g(dvB.y, A.kind, A.order);
+        C dA = cmk((gA.x - aA.x) - tA.x, (gA.y - aA.y) - tA.y);
+        C dB = cmk((gB.x - aB.x) - tB.x, (gB.y - aB.y) - tB.y);
         if (A.pre) {                           // half grid: z shift of the packed element
             dA = cmul(dA, A.pre[mA]);
             dB = cmul(dB, A.pre[mB]);
         }
-        if (A.do_update) *reinterpret_cast<V2 *>(A.tcur + oA) = tA;
-        if (A.refresh) *reinterpret_cast<V2 *>(A.ca + oA) = cA;
-        buf[yA * pitch + mA] = dA;
-        if (has1) {
-            if (A.do_update) *reinterpret_cast<V2 *>(A.tcur + oB) = tB;
-            if (A.refresh) *reinterpret_cast<V2 *>(A.ca + oB) = cB;
-            buf[yB * pitch + mB] = dB;
+        if (A.refresh) {
+            fwd_refresh<T, MAXH>(f, A, oA, tA, dvA, gA);
+            if (has1) fwd_refresh<T, MAXH>(f, A, oB, tB, dvB, gB);
+        } else if (A.do_update) {
+            *reinterpret_cast<V2 *>(A.tcur + oA) = tA;
+            if (has1) *reinterpret_cast<V2 *>(A.tcur + oB) = tB;
         }
+        buf[yA * pitch + mA] = dA;
+        if (has1) buf[yB * pitch + mB] = dB;
     }
 }
 
@@ -707,8 +743,9 @@ k_plane_fwd(Fields<T> f) {
     A.anchor = ctl->anchor_valid;
     A.refresh = ctl->refresh;
     A.tcur = f.Tc + (long long)gam * f.G + (long long)x * Ny * f.Nz;
-    A.ca = f.csr_a + siteoff;
+    A.ga = f.g_a + siteoff;
     A.wp = f.w + siteoff;
+    A.t0 = f.tau0 + siteoff;
     A.pre = half ? tw_z : nullptr;
     const C phx = half ? f.tw_xs[x] : cmk((T)1, (T)0);
     __syncthreads();
@@ -1193,6 +1230,7 @@ static __device__ void mdiis_pre(Ctrl *ctl, const double *sums, MdiisScratch &sc
     ctl->acc_hist += hist_n;
     ctl->acc_anchor += ctl->anchor_valid;
     ctl->acc_refresh += ctl->refresh;
+    ctl->acc_shift += ctl->refresh && ctl->do_update ? ctl->upd_n : 0;
     ctl->acc_psi += ctl->anchor_valid == 0;
     const int cur = ctl->cur;
     ctl->eta_slot[cur] = ctl->eta;    // plane_inv stored Y_cur = t + eta R_cur
@@ -1200,7 +1238,7 @@ static __device__ void mdiis_pre(Ctrl *ctl, const double *sums, MdiisScratch &sc
     const double rms = sqrt(rr * ctl->inv_count);
     ctl->rms = rms;
     ctl->iter += 1;
-    if (ctl->refresh) {               // this iteration wrote c^sr_a and h_a
+    if (ctl->refresh) {               // this iteration wrote g_a, h_a and moved the offset
         ctl->refresh = 0;
         ctl->anchor_valid = 1;
     }
@@ -1476,7 +1514,8 @@ static __global__ void k_mdiis(Ctrl *ctl_g, const double *partials, int nblocks)
 // FP32 form, far pairs are evaluated in FP32 (their Coulomb and phi terms accumulated in
 // FP64) and near pairs (r < 1.5 max sigma_ag, where the r^-12 term is large enough for FP32
 // coordinate rounding to show) entirely in FP64. Writes beta*u (capped at 1e4), phi and
-// w = beta q phi - beta*u.
+// w = beta q phi - beta*u (both the kept copy wref and the working field w, whose offset
+// tau0 is zero until a solve refreshes it).
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_potential(Fields<T> f, const double *atoms, int n_atoms, const double *site_sig,
@@ -1586,8 +1625,10 @@ k_potential(Fields<T> f, const double *atoms, int n_atoms, const double *site_si
     for (int g = 0; g < nv; ++g) {
         double v = beta * ((double)lj[g] + ljd[g] + C * site_q[g] * coul);
         v = v > 1e4 ? 1e4 : v;
+        const T wv = (T)(beta * site_q[g] * phiv - v);
         f.bu[(long long)g * G + p] = (T)v;
-        f.w[(long long)g * G + p] = (T)(beta * site_q[g] * phiv - v);
+        f.wref[(long long)g * G + p] = wv;
+        f.w[(long long)g * G + p] = wv;
     }
     f.phi[p] = (T)phiv;
 }
@@ -1708,11 +1749,12 @@ __global__ void k_guess_crop_out(Fields<T> f, int mode, int slot, int i0, int j0
         if (mode == 0)
             out[id] = tanhf((float)f.bu[src] * 0.25f);
         else
-            out[id] = (float)f.Tc[src];
+            out[id] = (float)((double)f.tau0[src] + (double)f.Tc[src]);
     }
 }
 
-// The iterate of `slot` (whole field): tau = crop values inside the crop, 0 outside.
+// The iterate of `slot` (whole field): tau = crop values inside the crop, 0 outside (offset
+// tau0 = 0, w = wref).
 template <typename T>
 __global__ void k_guess_crop_in(Fields<T> f, int slot, int i0, int j0, int k0, int n, const float *in) {
     const long long total = (long long)f.nv * f.G;
@@ -1731,6 +1773,8 @@ __global__ void k_guess_crop_in(Fields<T> f, int slot, int i0, int j0, int k0, i
         if (ci >= 0 && ci < n && cj >= 0 && cj < n && ck >= 0 && ck < n)
             v = (T)in[(((long long)g * n + ci) * n + cj) * n + ck];
         dst[id] = v;
+        f.tau0[id] = (T)0;
+        f.w[id] = f.wref[id];
     }
 }
 
@@ -1745,17 +1789,20 @@ cudaError_t launch_guess_crop(const Fields<T> &f, int mode, int slot, const int 
 }
 
 // ------------------------------------------------------------------ small helpers
-// Step 1: t = f, i.e. tau = 0 in the current-iterate field (the ring slot argument of the
-// launcher only names where the next residual goes).
+// Step 1: t = f, i.e. tau = 0: delta = 0 in the current-iterate field, offset tau0 = 0 and
+// w = wref (the ring slot argument of the launcher only names where the next residual goes).
 template <typename T>
 __global__ void k_init_guess(Fields<T> f) {
     const long long n = (long long)f.nv * f.G;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
+         i += (long long)gridDim.x * blockDim.x) {
         f.Tc[i] = (T)0;
+        f.tau0[i] = (T)0;
+        f.w[i] = f.wref[i];
+    }
 }
 
-// tau = t - beta q phi from a caller field t (FP64), into ring slot `slot`.
+// tau = t - beta q phi from a caller field t (FP64) as delta, with offset tau0 = 0.
 template <typename T>
 __global__ void k_guess_from_t(Fields<T> f, const double *src) {
     const long long n = (long long)f.nv * f.G;
@@ -1764,6 +1811,21 @@ __global__ void k_guess_from_t(Fields<T> f, const double *src) {
         const int g = (int)(i / f.G);
         const long long p = i - (long long)g * f.G;
         f.Tc[i] = (T)(src[i] - f.bq[g] * (double)f.phi[p]);
+        f.tau0[i] = (T)0;
+        f.w[i] = f.wref[i];
+    }
+}
+
+// Before a solve restarts from the last iterate: tau = tau0 + delta becomes delta with
+// tau0 = 0 and w = wref, so that the unanchored first iterations transform c^sr whole.
+template <typename T>
+__global__ void k_flatten(Fields<T> f) {
+    const long long n = (long long)f.nv * f.G;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        f.Tc[i] = f.tau0[i] + f.Tc[i];
+        f.tau0[i] = (T)0;
+        f.w[i] = f.wref[i];
     }
 }
 
@@ -1783,15 +1845,16 @@ __global__ void k_get_field(Fields<T> f, int field, int slot, int kind, int orde
         } else {
             const int g = (int)(i / f.G);
             const long long p = i - (long long)g * f.G;
-            const T tau = f.Tc[i];
+            const T delta = f.Tc[i];
+            const double tau = (double)f.tau0[i] + (double)delta;
             const double fq = f.bq[g] * (double)f.phi[p];
             if (field == 4) {
-                v = (double)tau + fq;
+                v = tau + fq;
             } else {
-                const T gv = closure_g(f.w[i] + tau, kind, order);
+                const T gv = closure_g(f.w[i] + delta, kind, order);
                 if (field == 1) v = (double)gv;
                 else if (field == 3) v = (double)(gv - (T)1);
-                else v = (double)(gv - (T)1 - tau) - fq;      // c = h - t
+                else v = ((double)gv - 1.0 - tau) - fq;      // c = h - t
             }
         }
         dst[i] = v;
@@ -1818,6 +1881,7 @@ k_sfe(Fields<T> f, int slot, int kind, int order, int sfe_kind, int sfe_order, d
     __shared__ double red[32];
     const int g = blockIdx.y;
     const T *tt = f.Tc + (long long)g * f.G;
+    const T *t0 = f.tau0 + (long long)g * f.G;
     const T *wp = f.w + (long long)g * f.G;
     const double bq = f.bq[g];
     double acc = 0.0;
@@ -1825,11 +1889,12 @@ k_sfe(Fields<T> f, int slot, int kind, int order, int sfe_kind, int sfe_order, d
     for (int i = 2; i <= sfe_order + 1; ++i) fact *= i;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < f.G;
          p += (long long)gridDim.x * blockDim.x) {
-        const T tau = tt[p];
-        const T d = wp[p] + tau;
+        const T delta = tt[p];
+        const T d = wp[p] + delta;
         const T gv = closure_g(d, kind, order);
         const double h = (double)(gv - (T)1);
-        const double c = (double)(gv - (T)1 - tau) - bq * (double)f.phi[p];   // c = h - t
+        const double tau = (double)t0[p] + (double)delta;
+        const double c = ((double)gv - 1.0 - tau) - bq * (double)f.phi[p];   // c = h - t
         double v = -c - 0.5 * h * c;
         if (sfe_kind == 5) v = c;                                // int c dr (PMV, Eq. 19)
         else if (sfe_kind == 2) v += 0.5 * h * h;                // HNC, Eq. 17
@@ -1977,7 +2042,8 @@ cudaError_t launch_sfe_gradient(const Fields<T> &f, int slot, int kind, int orde
 // ------------------------------------------------------------------ split plane passes
 // The plane passes in two kernels each, for x planes [x0, x1), so that the streaming
 // element work of one half of the planes can run beside the transforms of the other:
-//   fwd_elem : MDIIS update, closure, c^sr - c^sr_a  -> the spectrum buffer (real layout)
+//   fwd_elem : MDIIS update, closure, c^sr - c^sr_a (refresh of the iterate offset)
+//              -> the spectrum buffer (real layout)
 //   fft_fwd  : z and y transforms of those planes, in place (spectrum layout)
 //   fft_inv  : inverse y and z transforms, in place back to the real layout
 //   inv_elem : residual, Y, Gram-row partial sums
@@ -2041,16 +2107,30 @@ __global__ void __launch_bounds__(256) k_fwd_elem(Fields<float> f, int x0, int x
             t = ld4(f.Tc + o);
         }
         const float4 w = ld4(f.w + o);
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (anchor) a = ld4(f.csr_a + o);
-        float4 c;
-        c.x = closure_g(w.x + t.x, kind, order) - 1.f - t.x;
-        c.y = closure_g(w.y + t.y, kind, order) - 1.f - t.y;
-        c.z = closure_g(w.z + t.z, kind, order) - 1.f - t.z;
-        c.w = closure_g(w.w + t.w, kind, order) - 1.f - t.w;
-        if (do_update) *reinterpret_cast<float4 *>(f.Tc + o) = t;
-        if (refresh) *reinterpret_cast<float4 *>(f.csr_a + o) = c;
-        *reinterpret_cast<float4 *>(cs + o) = make_float4(c.x - a.x, c.y - a.y, c.z - a.z, c.w - a.w);
+        // c^sr - c^sr_a = (g - g_a) - delta (g_a = 1 before the first anchor), as in plane_fwd
+        float4 a = make_float4(1.f, 1.f, 1.f, 1.f);
+        if (anchor) a = ld4(f.g_a + o);
+        const float4 dv = make_float4(w.x + t.x, w.y + t.y, w.z + t.z, w.w + t.w);
+        const float4 gv = make_float4(closure_g(dv.x, kind, order), closure_g(dv.y, kind, order),
+                                      closure_g(dv.z, kind, order), closure_g(dv.w, kind, order));
+        if (refresh) {
+            float4 t0 = ld4(f.tau0 + o);
+            t0 = make_float4(t0.x + t.x, t0.y + t.y, t0.z + t.z, t0.w + t.w);
+            *reinterpret_cast<float4 *>(f.tau0 + o) = t0;
+            *reinterpret_cast<float4 *>(f.w + o) = dv;
+            *reinterpret_cast<float4 *>(f.g_a + o) = gv;
+            *reinterpret_cast<float4 *>(f.Tc + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (do_update)
+                for (int i = 0; i < upd_n; ++i) {
+                    float *yb = f.X + slot_off[i] + o;
+                    const float4 y = ld4(yb);
+                    *reinterpret_cast<float4 *>(yb) = make_float4(y.x - t.x, y.y - t.y, y.z - t.z, y.w - t.w);
+                }
+        } else if (do_update) {
+            *reinterpret_cast<float4 *>(f.Tc + o) = t;
+        }
+        *reinterpret_cast<float4 *>(cs + o) = make_float4((gv.x - a.x) - t.x, (gv.y - a.y) - t.y,
+                                                          (gv.z - a.z) - t.z, (gv.w - a.w) - t.w);
     }
 }
 
@@ -2455,6 +2535,10 @@ cudaError_t launch_guess_from_t(const Fields<T> &f, int, const double *src, cuda
     k_guess_from_t<T><<<152 * 8, 256, 0, s>>>(f, src);
     return cudaGetLastError();
 }
+template <typename T> cudaError_t launch_flatten(const Fields<T> &f, cudaStream_t s) {
+    k_flatten<T><<<152 * 8, 256, 0, s>>>(f);
+    return cudaGetLastError();
+}
 template <typename T>
 cudaError_t launch_get_field(const Fields<T> &f, int field, int slot, int kind, int order,
                              double *dst, cudaStream_t s) {
@@ -2498,6 +2582,7 @@ cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sf
                                              cudaStream_t);                                     \
     template cudaError_t launch_init_guess<T>(const Fields<T> &, int, cudaStream_t);            \
     template cudaError_t launch_guess_from_t<T>(const Fields<T> &, int, const double *, cudaStream_t); \
+    template cudaError_t launch_flatten<T>(const Fields<T> &, cudaStream_t);                     \
     template cudaError_t launch_get_field<T>(const Fields<T> &, int, int, int, int, double *,   \
                                              cudaStream_t);                                     \
     template cudaError_t launch_sfe<T>(const Fields<T> &, int, int, int, int, int, double *,    \
