@@ -1,9 +1,11 @@
 #!/usr/bin/env python
 """Benchmark: converged 3D-RISM solves/s (and site-gridpoint-iterations/s) at 1e-6 residual.
 
-Workload (default ``solute50_128``): a seeded 50-atom synthetic solute (10 A sphere, net
-charge 0) in 3-site water + 0.1 M NaCl (5 sites), 128^3 grid at 0.5 A, KH closure, MDIIS
-with 5 vectors, FP32 form, tolerance 1e-6. One step is one whole solve through the C ABI:
+Workload (default ``globule2000_256``, the largest configuration that fits one GPU): a
+seeded 2000-atom synthetic globule (16 A sphere, net charge +8) in 3-site water + 0.1 M NaCl
+(5 sites), 256^3 grid at 0.375 A, KH closure, MDIIS with 10 vectors, FP32 form (FP64 Gram,
+MDIIS solve, SFE and Coulomb sums), tolerance 1e-6. ``--workload solute50_128`` is the
+50-atom, 128^3 x 0.5 A, MDIIS-5 configuration. One step is one whole solve through the C ABI:
 rism3d_set_solute (potential + long-range field + initial guess), rism3d_solve (all
 iterations), rism3d_get_sfe. The solvent susceptibility comes from the library's own 1D
 solver (rism1d_xrism) once, before timing.
@@ -37,15 +39,17 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="solute50_128")
+    p.add_argument("--workload", default="globule2000_256")
     p.add_argument("--no-cufft", action="store_true",
                    help="skip the cuFFT comparison (torch.fft transforms of the same fields)")
     p.add_argument("--precision", type=int, default=32, choices=[32, 64])
     p.add_argument("--closure", default="kh", choices=["kh", "pse", "hnc"])
     p.add_argument("--pse-order", type=int, default=3)
     p.add_argument("--tol", type=float, default=1e-6)
-    p.add_argument("--e2e-steps", type=int, default=5)
-    p.add_argument("--cpu-sample-iters", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-sample-iters", type=int, default=2)
+    p.add_argument("--cpu-sample-atoms", type=int, default=4,
+                   help="atoms whose direct potential sums the CPU baseline times (scaled to all)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--inflight", type=int, default=8, help="batch64: jobs in flight")
     p.add_argument("--split-passes", action="store_true",
@@ -185,36 +189,71 @@ def _cores_used(*clocks):
     return max(1, int(round(ratio))), ratio
 
 
-def cpu_baseline(args, w, solv, grid, solute, n_iter_gpu):
-    """The FP64 oracle as it stands, timed on a bounded sample of the same workload: the
-    once-per-solute setup (direct potential sums, long-range fields, X on the grid) plus
-    a few iterations of steps 2-6; extrapolated to a whole solve with the iteration count
-    the oracle needs for this workload (stored reference), else the GPU solve's count."""
-    import numpy as np
-    from oracle import rism3d as orc, closure as cl
+def oracle_sample(solv, grid, solute, closure, pse_order, mdiis_nvec, n_iter, n_atoms_sample, warm=0):
+    """The FP64 oracle as it stands, timed on a bounded sample of one solve of a workload.
+
+    Setup: the oracle's Problem built with the first a = n_atoms_sample atoms (its direct
+    potential sums of Eqs. 22, 29 and 30 grow with the atom count, the rest does not), plus
+    those a atoms' sums timed alone; the whole solute's setup is then
+    T_problem(a) + (n / a - 1) T_sums(a). With a >= n the whole solute is built and timed.
+    Iterations: n_iter iterations of steps 2-6 on that Problem (their cost does not depend on
+    the atoms), after ``warm`` untimed ones. Returns (t_setup, t_iter, clocks, description)."""
+    from oracle import rism3d as orc, closure as cl, potential as pot
     kinds = {"kh": cl.KH, "pse": cl.PSE, "hnc": cl.HNC}
+    n = len(solute["q"])
+    a = min(n, max(1, int(n_atoms_sample)))
+    sub = {k: solute[k][:a] for k in ("xyz", "q", "sigma", "eps")}
     with _HostClock() as cs:
-        P = orc.Problem(solv, grid, solute)
+        P = orc.Problem(solv, grid, sub)
+    clocks = [cs]
     t_setup = cs.wall
-    n = args.cpu_sample_iters
+    how = "setup of all %d atoms %.1f s" % (n, t_setup)
+    if a < n:
+        with _HostClock() as ca:
+            pot.beta_u(P.n, P.spacing, P.origin, sub["xyz"], sub["q"], sub["sigma"], sub["eps"], P.site_q,
+                       P.site_sig, P.site_eps, P.temperature)
+            pot.phi_long_range(P.n, P.spacing, P.origin, sub["xyz"], sub["q"])
+            pot.phik_long_range(P.n, P.spacing, P.origin, sub["xyz"], sub["q"])
+        clocks.append(ca)
+        t_setup = cs.wall + (n / a - 1.0) * ca.wall
+        how = ("setup with %d of %d atoms %.1f s, of which the atom sums %.1f s, scaled to all atoms "
+               "%.1f s" % (a, n, cs.wall, ca.wall, t_setup))
+    if warm:
+        orc.solve(P, kinds[closure], pse_order, tol=1e-300, max_iter=warm, mdiis_nvec=mdiis_nvec)
     with _HostClock() as ci:
-        orc.solve(P, kinds[args.closure], args.pse_order, tol=1e-300, max_iter=n,
-                  mdiis_nvec=w["mdiis_nvec"])
-    t_iter = ci.wall / n
-    cores, ratio = _cores_used(cs, ci)
-    ref = os.path.join(ROOT, "tests", "golden", "%s_reference.npz" % args.workload)
-    key = "%s_%g_iterations" % ({"kh": "kh", "pse": "pse3"}.get(args.closure, args.closure), args.tol)
-    n_full, src = n_iter_gpu, "the GPU solve's iteration count"
+        orc.solve(P, kinds[closure], pse_order, tol=1e-300, max_iter=n_iter, mdiis_nvec=mdiis_nvec)
+    clocks.append(ci)
+    t_iter = ci.wall / n_iter
+    return t_setup, t_iter, clocks, how + "; %d iterations %.2f s each" % (n_iter, t_iter)
+
+
+def oracle_iterations(workload, closure, tol, fallback):
+    """The oracle's own iteration count to ``tol`` for a workload (stored reference), else
+    ``fallback`` = (count, source)."""
+    import numpy as np
+    ref = os.path.join(ROOT, "tests", "golden", "%s_reference.npz" % workload)
+    key = "%s_%g_iterations" % ({"kh": "kh", "pse": "pse3"}.get(closure, closure), tol)
     if os.path.exists(ref):
         d = np.load(ref)
         if key in d:
-            n_full, src = int(d[key]), "the oracle's own iteration count (stored reference)"
+            return int(d[key]), "the oracle's own iteration count (stored reference)"
+    return fallback
+
+
+def cpu_baseline(args, w, solv, grid, solute, n_iter_gpu):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of the same
+    workload (oracle_sample), extrapolated to a whole solve with the iteration count the
+    oracle needs for this workload (stored reference), else the GPU solve's count."""
+    import numpy as np
+    t_setup, t_iter, clocks, how = oracle_sample(solv, grid, solute, args.closure, args.pse_order,
+                                                 w["mdiis_nvec"], args.cpu_sample_iters, args.cpu_sample_atoms)
+    cores, ratio = _cores_used(*clocks)
+    n_full, src = oracle_iterations(args.workload, args.closure, args.tol,
+                                    (n_iter_gpu, "the GPU solve's iteration count"))
     t_solve = t_setup + n_full * t_iter
     return dict(value=1.0 / t_solve, unit="solves/s", cores=cores, kind="oracle",
-                sample="oracle setup (%.1f s) + %d iterations (%.2f s each) of %s, host CPU "
-                       "time / wall time %.2f (%d cores available), extrapolated to %d "
-                       "iterations (%s)"
-                       % (t_setup, n, t_iter, args.workload, ratio, os.cpu_count() or 0, n_full, src),
+                sample="%s of %s; host CPU time / wall time %.2f (%d cores available); extrapolated to "
+                       "%d iterations (%s)" % (how, args.workload, ratio, os.cpu_count() or 0, n_full, src),
                 site_gridpoint_iters_per_s=len(solv["q"]) * float(np.prod(grid["n"])) / t_iter)
 
 
@@ -222,7 +261,6 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from oracle import rism3d as orc, closure as cl
     import numpy as np
     from paper_2403_01039_gb300 import synth
     w = synth.WORKLOADS[args.workload]
@@ -235,32 +273,24 @@ def run_reference(args):
     solv.update(chi=r1["chi"], dk=r1["dk"])
     grid = synth.cubic_grid(w["n"], w["spacing"])
     solute = synth.workload_solute(args.workload)
-    kinds = {"kh": cl.KH, "pse": cl.PSE, "hnc": cl.HNC}
-    with _HostClock() as cs:
-        P = orc.Problem(solv, grid, solute)
-    t_setup = cs.wall
     # one step = one iteration of steps 2-6 (a bounded sample of the solve)
-    orc.solve(P, kinds[args.closure], args.pse_order, tol=1e-300, max_iter=args.warmup,
-              mdiis_nvec=w["mdiis_nvec"])
-    with _HostClock() as ci:
-        orc.solve(P, kinds[args.closure], args.pse_order, tol=1e-300, max_iter=args.steps,
-                  mdiis_nvec=w["mdiis_nvec"])
-    t_iter = ci.wall / args.steps
-    cores, ratio = _cores_used(cs, ci)
-    ref = os.path.join(ROOT, "tests", "golden", "%s_reference.npz" % args.workload)
-    key = "%s_%g_iterations" % ({"kh": "kh", "pse": "pse3"}.get(args.closure, args.closure), args.tol)
-    if os.path.exists(ref) and key in np.load(ref):
-        n_full, src = int(np.load(ref)[key]), "stored oracle reference"
-    elif len(sites["q"]) * int(np.prod(grid["n"])) <= 1 << 20:       # small: count them
-        n_full = orc.solve(P, kinds[args.closure], args.pse_order, tol=args.tol,
-                           mdiis_nvec=w["mdiis_nvec"])["iterations"]
-        src = "counted by an untimed oracle solve"
-    else:
-        n_full, src = 127, "assumed (solute50_128's count; no stored reference)"
+    t_setup, t_iter, clocks, how = oracle_sample(solv, grid, solute, args.closure, args.pse_order,
+                                                 w["mdiis_nvec"], args.steps, args.cpu_sample_atoms,
+                                                 warm=args.warmup)
+    cores, ratio = _cores_used(*clocks)
+    n_full, src = oracle_iterations(args.workload, args.closure, args.tol, (None, None))
+    if n_full is None:
+        if len(sites["q"]) * int(np.prod(grid["n"])) <= 1 << 20:       # small: count them
+            from oracle import rism3d as orc, closure as cl
+            P = orc.Problem(solv, grid, solute)
+            kind = {"kh": cl.KH, "pse": cl.PSE, "hnc": cl.HNC}[args.closure]
+            n_full = orc.solve(P, kind, args.pse_order, tol=args.tol, mdiis_nvec=w["mdiis_nvec"])["iterations"]
+            src = "counted by an untimed oracle solve"
+        else:
+            n_full, src = 569, "assumed (the FP64 GPU solve's count on globule2000_256; no stored reference)"
     value = 1.0 / (t_setup + n_full * t_iter)
-    sample = ("oracle setup %.1f s + %d timed iterations (%.2f s each), host CPU time / wall "
-              "time %.2f (%d cores available), extrapolated to the %d iterations of a converged "
-              "solve (%s)" % (t_setup, args.steps, t_iter, ratio, os.cpu_count() or 0, n_full, src))
+    sample = ("%s; host CPU time / wall time %.2f (%d cores available); extrapolated to the %d "
+              "iterations of a converged solve (%s)" % (how, ratio, os.cpu_count() or 0, n_full, src))
     line = dict(impl="reference", metric=METRIC, value=value, unit="solves/s", n_gpus=args.gpus,
                 steps=args.steps, warmup=args.warmup, ms_per_step=t_iter * 1e3, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
@@ -408,26 +438,48 @@ def run_ours(args):
     dom = max(kern, key=lambda k: share_ms[k])
     kd = kern[dom]
     per_launch_s = avg_ms[dom] / 1e3
-    bytes_per_launch = kd["bytes"] / max(worked[dom], 1)
-    achieved = bytes_per_launch / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
     total_ms = sum(share_ms.values())
+    # algorithmic bytes of the survey's model (s bytes per real, per site-point and
+    # iteration): closure read 2s, two-pass transform 4s, residual and Gram (M + 2)s, update
+    # (2M + 1)s, in all (3M + 9)s; split by kernel as plane_fwd = update + closure + plane
+    # write (2M + 4)s, pencil 2s, plane_inv = plane read + residual (M + 3)s, and 2s for each
+    # y-pencil pass of the row-chunked planes (the third transform pass, outside the base model)
+    sb = 4.0 if args.precision == 32 else 8.0
+    M = w["mdiis_nvec"]
+    P = nv * float(G)
+    model_units = {"plane_fwd": 2 * M + 4, "pencil": 2, "plane_inv": M + 3, "ypencil_fwd": 2, "ypencil_inv": 2}
+    model_bytes = {k: u * sb * P for k, u in model_units.items()}
+    lib_bytes_per_launch = kd["bytes"] / max(worked[dom], 1)
+    bytes_per_launch = model_bytes.get(dom, lib_bytes_per_launch)
+    achieved = bytes_per_launch / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+    it_keys = [k for k in per_iter + per_iter2 if k in kern]
+    it_ms = sum(share_ms[k] for k in it_keys) / stats["iterations"] if stats["iterations"] else None
+    iter_bytes = (3 * M + 9) * sb * P
+    iter_gbs = iter_bytes / (it_ms / 1e3) / 1e9 if it_ms else None
     roofline = dict(bound="hbm", kernel=dom, achieved=achieved, peak=peak, unit="GB/s",
                     frac=achieved / peak, peak_source=peak_src,
                     frac_of_nominal=achieved / NOMINAL_HBM_GBS, nominal_peak=NOMINAL_HBM_GBS,
                     traffic=ncu_traffic(dom, args.workload),
-                    algorithmic_bytes_per_launch=bytes_per_launch, avg_launch_ms=per_launch_s * 1e3,
-                    timed_launches=kd["timed"], share=share_ms[dom] / total_ms if total_ms else None)
+                    algorithmic_bytes_per_launch=bytes_per_launch,
+                    bytes_model="(3M+9)s per site-point and iteration; %s: %s" % (
+                        dom, "%ds" % model_units[dom] if dom in model_units else "library counter"),
+                    library_bytes_per_launch=lib_bytes_per_launch,
+                    library_frac=(lib_bytes_per_launch / per_launch_s / 1e9 / peak) if per_launch_s > 0 else None,
+                    avg_launch_ms=per_launch_s * 1e3,
+                    timed_launches=kd["timed"], share=share_ms[dom] / total_ms if total_ms else None,
+                    iteration=dict(model_bytes=iter_bytes, ms=it_ms, achieved=iter_gbs,
+                                   frac=(iter_gbs / peak) if iter_gbs else None,
+                                   step_frac=iter_bytes * iters_all / (world * secs) / 1e9 / peak))
     launches = int(sum(k["launches"] for k in kern.values()))
     kernels_out = {k: dict(launches=v["launches"], timed=v["timed"],
                            ms_per_launch=avg_ms[k] if v["timed"] else None,
                            GBps=(v["bytes"] / max(worked[k], 1) / (avg_ms[k] / 1e3) / 1e9) if avg_ms[k] else None,
+                           model_GBps=(model_bytes[k] / (avg_ms[k] / 1e3) / 1e9) if (avg_ms[k] and k in model_bytes) else None,
                            share=(share_ms[k] / total_ms) if total_ms else None)
                    for k, v in kern.items() if v["launches"]}
 
     cufft = None
     if rank == 0 and not args.no_cufft:
-        it_keys = [k for k in per_iter + per_iter2 if k in kern]
-        it_ms = sum(share_ms[k] for k in it_keys) / stats["iterations"] if stats["iterations"] else None
         cufft = cufft_comparison(nv, grid["n"], args.precision, it_ms)
 
     cpu = None

@@ -980,11 +980,12 @@ struct InvArgs {
 };
 
 // Residual R = h + 1 - g (Eq. 33) of the elements e in [e0, e1) of the block's rows, stored
-// into the ring, and the thread's Gram sums <R, R_i> (acc[i + 1]) and sum R^2 (acc[0]).
-template <typename T, int MAXH>
+// into the ring and back into the row buffer (in place of h, for the Gram pass that follows),
+// with the thread's sum of R^2 in acc.
+template <typename T>
 __device__ __forceinline__ void inv_elements(const Fields<T> &f, const InvArgs<T> &A,
-                                             const typename Cx<T>::type *buf, int y0, int e0, int e1,
-                                             int tid, int nthr, GramAcc<T> (&acc)[MAXH + 1]) {
+                                             typename Cx<T>::type *buf, int y0, int e0, int e1,
+                                             int tid, int nthr, GramAcc<T> &acc) {
     typedef typename Cx<T>::type C;
     typedef typename Vec2<T>::type V2;
     const int Kz = f.Kz, pitch = f.pitch;
@@ -995,7 +996,7 @@ __device__ __forceinline__ void inv_elements(const Fields<T> &f, const InvArgs<T
         const int yB = has1 ? fdiv(i1, f.dKz) : yA, mB = has1 ? i1 - yB * Kz : mA;
         const long long oA = (long long)(y0 + yA) * f.Nz + 2 * mA;
         const long long oB = (long long)(y0 + yB) * f.Nz + 2 * mB;
-        // loads of both elements first: t, w, anchor, history residuals
+        // loads of both elements first: delta, w, anchor
         const V2 tA = ld2(A.tcur + oA), tB = ld2(A.tcur + oB);
         const V2 wA = ld2(A.wp + oA), wB = ld2(A.wp + oB);
         V2 aA, aB;
@@ -1003,13 +1004,6 @@ __device__ __forceinline__ void inv_elements(const Fields<T> &f, const InvArgs<T
             aA = ld2(A.ha + oA);
             aB = ld2(A.ha + oB);
         }
-        V2 qA[MAXH], qB[MAXH];
-#pragma unroll
-        for (int i = 0; i < MAXH; ++i)
-            if (i < A.hist_n) {
-                qA[i] = ld2(f.R + A.hoff[i] + oA);
-                qB[i] = ld2(f.R + A.hoff[i] + oB);
-            }
         C hcA = buf[yA * pitch + mA], hcB = buf[yB * pitch + mB];
         if (A.post) {                          // half grid: undo the z shift
             hcA = cmul(hcA, cconj(A.post[mA]));
@@ -1039,38 +1033,72 @@ __device__ __forceinline__ void inv_elements(const Fields<T> &f, const InvArgs<T
             hB.x = hcB.x;
             hB.y = hcB.y;
         }
-        acc[0].add(rA.x, rA.x);
-        acc[0].add(rA.y, rA.y);
-#pragma unroll
-        for (int i = 0; i < MAXH; ++i)
-            if (i < A.hist_n) {
-                acc[i + 1].add(rA.x, qA[i].x);
-                acc[i + 1].add(rA.y, qA[i].y);
-            }
+        acc.add(rA.x, rA.x);
+        acc.add(rA.y, rA.y);
         if (A.refresh) *reinterpret_cast<V2 *>(A.ha + oA) = hA;
         *reinterpret_cast<V2 *>(A.rcur + oA) = rA;
-        {
-            V2 yA;
-            yA.x = tA.x + A.eta * rA.x;
-            yA.y = tA.y + A.eta * rA.y;
-            *reinterpret_cast<V2 *>(A.ycur + oA) = yA;
-        }
+        V2 ysA;
+        ysA.x = tA.x + A.eta * rA.x;
+        ysA.y = tA.y + A.eta * rA.y;
+        *reinterpret_cast<V2 *>(A.ycur + oA) = ysA;
+        buf[yA * pitch + mA] = cmk(rA.x, rA.y);
         if (has1) {
-            acc[0].add(rB.x, rB.x);
-            acc[0].add(rB.y, rB.y);
-#pragma unroll
-            for (int i = 0; i < MAXH; ++i)
-                if (i < A.hist_n) {
-                    acc[i + 1].add(rB.x, qB[i].x);
-                    acc[i + 1].add(rB.y, qB[i].y);
-                }
+            acc.add(rB.x, rB.x);
+            acc.add(rB.y, rB.y);
             if (A.refresh) *reinterpret_cast<V2 *>(A.ha + oB) = hB;
             *reinterpret_cast<V2 *>(A.rcur + oB) = rB;
-            V2 yB;
-            yB.x = tB.x + A.eta * rB.x;
-            yB.y = tB.y + A.eta * rB.y;
-            *reinterpret_cast<V2 *>(A.ycur + oB) = yB;
+            V2 ysB;
+            ysB.x = tB.x + A.eta * rB.x;
+            ysB.y = tB.y + A.eta * rB.y;
+            *reinterpret_cast<V2 *>(A.ycur + oB) = ysB;
+            buf[yB * pitch + mB] = cmk(rB.x, rB.y);
         }
+    }
+}
+
+// Gram row of the new residual, <R, R_i> for each stored residual i, over the block's rows:
+// R from the row buffer, R_i streamed from the ring, one history value at a time (one
+// accumulator in registers, four loads in flight per thread). The warp sums go to
+// red[(i + 1) * nw + warp].
+template <typename T>
+__device__ __forceinline__ void gram_row(const Fields<T> &f, const InvArgs<T> &A,
+                                         const typename Cx<T>::type *buf, int y0, int nyb, double *red) {
+    typedef typename Cx<T>::type C;
+    typedef typename Vec2<T>::type V2;
+    const int Kz = f.Kz, pitch = f.pitch;
+    const int n = nyb * Kz;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int nthr = blockDim.x;
+    for (int h = 0; h < A.hist_n; ++h) {
+        const T *q = f.R + A.hoff[h];
+        GramAcc<T> acc;
+        acc.zero();
+        int e = threadIdx.x;
+        for (; e + 3 * nthr < n; e += 4 * nthr) {
+            V2 qv[4];
+            C rv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int ei = e + u * nthr;
+                const int y = fdiv(ei, f.dKz), m = ei - y * Kz;
+                qv[u] = ld2(q + (long long)(y0 + y) * f.Nz + 2 * m);
+                rv[u] = buf[y * pitch + m];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                acc.add(rv[u].x, qv[u].x);
+                acc.add(rv[u].y, qv[u].y);
+            }
+        }
+        for (; e < n; e += nthr) {
+            const int y = fdiv(e, f.dKz), m = e - y * Kz;
+            const V2 qv = ld2(q + (long long)(y0 + y) * f.Nz + 2 * m);
+            const C rv = buf[y * pitch + m];
+            acc.add(rv.x, qv.x);
+            acc.add(rv.y, qv.y);
+        }
+        acc.warp_reduce();
+        if (lane == 0) red[(h + 1) * nw + warp] = acc.value();
     }
 }
 
@@ -1158,9 +1186,8 @@ k_plane_inv(Fields<T> f) {
         fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, +1);
     }
 
-    GramAcc<T> acc[MAXH + 1];
-#pragma unroll
-    for (int i = 0; i <= MAXH; ++i) acc[i].zero();
+    GramAcc<T> acc;
+    acc.zero();
     if constexpr (LZ > 0) {
         constexpr int RW = 256 / LZ;
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1172,7 +1199,7 @@ k_plane_inv(Fields<T> f) {
                 c2r_rows(buf + (long)r0 * pitch, nr, LZ, pitch, tw_z, f.dKz1h, lane, 32, nyc == 1);
             __syncwarp();
             fft_rows_warp<C, LZ>(buf + (long)r0 * pitch, nr, pitch, tw_h, +1, lane);
-            inv_elements<T, MAXH>(f, A, buf, y0, r0 * LZ, (r0 + nr) * LZ, lane, 32, acc);
+            inv_elements<T>(f, A, buf, y0, r0 * LZ, (r0 + nr) * LZ, lane, 32, acc);
         }
     } else {
         if (half)
@@ -1181,18 +1208,15 @@ k_plane_inv(Fields<T> f) {
             c2r_rows(buf, nyb, Kz, pitch, tw_z, f.dKz1h, threadIdx.x, blockDim.x, nyc == 1);
         __syncthreads();
         fft_smem<C, MaxC<T>::v>(buf, f.ph, 1, nyb, pitch, f.chunk_rows, tw_h, +1);
-        inv_elements<T, MAXH>(f, A, buf, y0, 0, nyb * Kz, threadIdx.x, blockDim.x, acc);
+        inv_elements<T>(f, A, buf, y0, 0, nyb * Kz, threadIdx.x, blockDim.x, acc);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const long long nblocks = (long long)f.nv * f.Nx * nyc;
     const long long blk = ((long long)gam * f.Nx + x) * nyc + yc;
-#pragma unroll
-    for (int i = 0; i <= MAXH; ++i) {
-        if (i <= A.hist_n) {
-            acc[i].warp_reduce();
-            if (lane == 0) red[i * nw + warp] = acc[i].value();
-        }
-    }
+    acc.warp_reduce();
+    if (lane == 0) red[warp] = acc.value();
+    __syncthreads();                       // every row's R is in the buffer
+    gram_row<T>(f, A, buf, y0, nyb, red);
     __syncthreads();
     if (threadIdx.x <= A.hist_n) {
         double s = 0.0;

@@ -5,6 +5,7 @@ import json
 import os
 import sys
 
+import numpy as np
 import pytest
 
 from conftest import ROOT
@@ -22,7 +23,7 @@ def test_defaults_meet_the_timing_rules(bench, monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     a = bench.parse()
     assert a.gpus == 1 and a.warmup >= 3 and a.steps >= 1 and a.impl == "ours"
-    assert a.workload == "solute50_128" and a.tol == 1e-6 and a.precision == 32
+    assert a.workload == "globule2000_256" and a.tol == 1e-6 and a.precision == 32
 
 
 def test_peak_lookup(bench):
@@ -68,3 +69,18 @@ def test_cufft_comparison_fails_soft(bench):
         pytest.skip("the soft failure is for hosts without a GPU")
     r = bench.cufft_comparison(3, (8, 8, 8), 32, 0.1)
     assert set(r) == {"error"}
+
+
+def test_oracle_sample_scales_the_atom_sums(bench):
+    """The bounded CPU sample builds the oracle's Problem from a few atoms and scales the
+    atom-dependent sums to the whole solute: the estimate must lie between the subset's cost
+    and the subset's cost times n / a."""
+    from paper_2403_01039_gb300 import synth
+    solv = synth.water_3site()
+    chi = np.load(os.path.join(bench.ROOT, "tests", "golden", "chi_water3.npz"))
+    solv.update(chi=chi["chi"], dk=float(chi["dk"]))
+    grid = synth.cubic_grid(16, 0.5)
+    sol = synth.random_solute(12, 4.0, 5)
+    t_setup, t_iter, clocks, how = bench.oracle_sample(solv, grid, sol, "kh", 3, 5, 2, 3)
+    assert t_iter > 0 and len(clocks) == 3 and "3 of 12 atoms" in how
+    assert clocks[0].wall <= t_setup <= clocks[0].wall * 4 + clocks[1].wall * 4
