@@ -126,6 +126,12 @@ typedef struct {
                                  k is zero, the transform carries the factor
                                  exp(-i pi sum_d n_d / N_d) and the fields are antiperiodic
                                  over the box */
+    int ypencil_pass;         /* row-chunked planes only. 0 (default): when a plane's chunks
+                                 number 2, 4 or 8 and split it evenly (integer k grid), they
+                                 run as one thread-block cluster that does the y transform
+                                 through distributed shared memory; 1: the y transform as a
+                                 separate y-pencil pass over the spectrum. Same results
+                                 within rounding. */
     void *cuda_stream;        /* cudaStream_t to run on; NULL: the library creates one */
     void *workspace;          /* device buffer of >= rism3d_workspace_bytes bytes, 256-byte
                                  aligned, owned by the caller and kept alive until

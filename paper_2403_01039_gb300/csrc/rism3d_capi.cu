@@ -205,6 +205,8 @@ struct Geometry {
     FftPlan px, py, ph;
     int pitch, W, pencil_pitch, chunk_rows, chunk_cols, chunk_x;
     int slab_rows, nyc, Wy, ypitch, chunk_y;
+    int cl, chunk_ys;                           // cluster y transform (0: y-pencil pass)
+    FftPlan pys;
     size_t plane_smem, pencil_smem, ypencil_smem;
 };
 
@@ -267,6 +269,8 @@ rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, cons
         return fail(nullptr, RISM3D_EINVAL, "mdiis_damp must be in (0, 2]");
     if (op->slab_rows < 0) return fail(nullptr, RISM3D_EINVAL, "slab_rows must be >= 0");
     if (op->kgrid != 0 && op->kgrid != 1) return fail(nullptr, RISM3D_EINVAL, "kgrid must be 0 or 1");
+    if (op->ypencil_pass != 0 && op->ypencil_pass != 1)
+        return fail(nullptr, RISM3D_EINVAL, "ypencil_pass must be 0 or 1");
     if (op->split_passes != 0 && op->split_passes != 1) return fail(nullptr, RISM3D_EINVAL, "split_passes must be 0 or 1");
     if (op->timing < 0 || op->timing > 2) return fail(nullptr, RISM3D_EINVAL, "timing must be 0, 1 or 2");
     if (op->accelerator != 0 && op->accelerator != 1)
@@ -304,6 +308,15 @@ rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, cons
     }
     g.nyc = (g.Ny + g.slab_rows - 1) / g.slab_rows;
     g.plane_smem = plane_bytes(g.slab_rows);
+    // row chunks that split the plane evenly into 2, 4 or 8 form a cluster that does the y
+    // transform (its local part needs a plan of the chunk length and S twiddles more)
+    g.cl = 0;
+    if (g.nyc > 1 && !op->ypencil_pass && op->kgrid == 0 && (g.nyc == 2 || g.nyc == 4 || g.nyc == 8) &&
+        g.Ny == g.nyc * g.slab_rows && make_plan(g.slab_rows, g.pys) &&
+        g.plane_smem + c * g.slab_rows <= kMaxSmem) {
+        g.cl = g.nyc;
+        g.plane_smem += c * g.slab_rows;
+    }
     if (g.plane_smem > kMaxSmem)
         return fail(nullptr, RISM3D_EUNSUPPORTED,
                     "a row chunk of %d rows x %d needs %zu bytes of shared memory (limit %zu)", g.slab_rows,
@@ -335,6 +348,11 @@ rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, cons
     g.py.seq_per_warp = warp_seqs(g.py, maxc);
     g.ph.seq_per_warp = warp_seqs(g.ph, maxc);
     g.chunk_rows = fft_chunk(g.ph, kThreadsPlane, maxc);
+    g.chunk_ys = 1;
+    if (g.cl) {
+        g.pys.seq_per_warp = warp_seqs(g.pys, maxc);
+        g.chunk_ys = fft_chunk(g.pys, kThreadsPlane, maxc);
+    }
     g.chunk_cols = fft_chunk(g.py, kThreadsPlane, maxc);
     g.chunk_x = fft_chunk(g.px, kThreadsPencil, maxc);
     g.chunk_y = fft_chunk(g.py, kThreadsPencil, maxc);
@@ -391,6 +409,10 @@ void fill_fields(rism3d_ctx *ctx, const Geometry &g, const Layout &L, Fields<T> 
     f.pitch = g.pitch;
     f.slab_rows = g.slab_rows;
     f.nyc = g.nyc;
+    f.cl = g.cl;
+    f.pys = g.pys;
+    f.chunk_ys = g.chunk_ys;
+    f.dK1 = make_fastdiv(g.Kz + 1);
     f.Wy = g.Wy;
     f.ypitch = g.ypitch;
     f.ytiles_main = g.Nx * ((g.Kz + g.Wy - 1) / g.Wy);
@@ -512,7 +534,7 @@ struct Launch {
 int iteration_plan(const rism3d_ctx *ctx, bool with_mdiis, Launch *L) {
     const bool fp32 = ctx->fp32();
     const bool split = fp32 ? split_planes(ctx->f32) : false;
-    const bool ysplit = (fp32 ? ctx->f32.nyc : ctx->f64.nyc) > 1;
+    const bool ysplit = fp32 ? (ctx->f32.nyc > 1 && ctx->f32.cl == 0) : (ctx->f64.nyc > 1 && ctx->f64.cl == 0);
     int n = 0;
     if (split) {
         L[n++] = {10, 0, 0, 0};
@@ -636,7 +658,8 @@ void account_iterations(rism3d_ctx *ctx, const Ctrl &c) {
     }
     const int nyc = ctx->fp32() ? ctx->f32.nyc : ctx->f64.nyc;
     ctx->stats.bytes[3] += 8.0 * ctx->nv * ctx->Nx * nyc * (it + (double)c.acc_hist);
-    if (nyc > 1) {                    // y pencils read and write the spectrum
+    const int cl = ctx->fp32() ? ctx->f32.cl : ctx->f64.cl;
+    if (nyc > 1 && cl == 0) {         // y pencils read and write the spectrum
         ctx->stats.bytes[8] += P * s * z * 2.0 * it;
         ctx->stats.bytes[9] += P * s * z * 2.0 * it;
     }

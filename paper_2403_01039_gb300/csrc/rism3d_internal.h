@@ -135,6 +135,11 @@ struct Fields {
     int chunk_rows, chunk_cols_fwd, chunk_x;   // batch chunk sizes of the in-place FFTs
     int pitch;                      // complex row pitch of a plane in shared memory
     int slab_rows, nyc;             // rows per plane block and row chunks per plane (1: whole)
+    int cl;                         // > 1: the nyc row chunks of a plane form a thread-block
+                                    // cluster that does the y transform (no y-pencil pass)
+    FftPlan pys;                    // cluster y transform: local length slab_rows
+    int chunk_ys;
+    FastDiv dK1;                    // Kz + 1
     int Wy, ypitch, ytiles_main, ytiles_nyq, chunk_y;   // y-pencil pass (split planes only)
     int W;                          // columns per pencil tile
     int tiles_main, tiles_nyq;

@@ -22,6 +22,7 @@
 // w = f - beta*u, so that d = -beta*u + t = w + tau and c^sr = g - 1 - t + f = g - 1 - tau
 // (Eq. 31) without the large long-range parts of t and beta*u; since the MDIIS weights sum
 // to one, iterating on tau is the same iteration as on t.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -36,6 +37,7 @@
 #endif
 
 namespace rism {
+namespace cg = cooperative_groups;
 
 // ------------------------------------------------------------------ complex helpers
 __host__ __device__ __forceinline__ float2 cmk(float a, float b) { return make_float2(a, b); }
@@ -558,6 +560,60 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// ------------------------------------------------------------------ y transform across a cluster
+// When a y-z plane exceeds one block's shared memory, its R = Ny / S row chunks of S rows go
+// to the R blocks of a thread-block cluster (block rank r holds rows r S .. r S + S - 1) and
+// the length-Ny y transform is split as Ny = R x S (decimation in frequency): with
+// y = n + S j and k = R k' + r,
+//   X[R k' + r] = sum_n exp(-2 pi i n k' / S) [exp(-2 pi i n r / Ny) sum_j x_j[n] W_R^{j r}],
+// so a radix-R step across the cluster (distributed shared memory) followed by a local
+// length-S transform leaves X[R k' + r] in row k' of block r; the inverse runs the local
+// transform first and the cross-block step last. Each row position (n, column) is owned by
+// one block, which reads the R values from the R blocks and writes the R results back, so
+// no position is read after another block has written it; a cluster barrier before and
+// after orders the step against the local work.
+template <typename C, int R>
+__device__ __forceinline__ void cluster_radix(C *buf, int S, int K1, int pitch, const FastDiv &dK1,
+                                              const C *tw_y, int sign) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int P = S * K1;
+    const int p0 = (int)((long long)P * rank / R), p1 = (int)((long long)P * (rank + 1) / R);
+    C *rb[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) rb[j] = cl.map_shared_rank(buf, j);
+    cl.sync();
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const int n = fdiv(p, dK1), col = p - n * K1;
+        const int off = n * pitch + col;
+        C v[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) v[j] = rb[j][off];
+        if (sign > 0) {                      // inverse: B_r[n] exp(+2 pi i n r / Ny), then the DFT
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], cconj(tw_y[n * r]));
+        }
+        Dft<R>::run(v, sign);
+        if (sign < 0) {                      // forward: the DFT, then exp(-2 pi i n r / Ny)
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw_y[n * r]);
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j) rb[j][off] = v[j];
+    }
+    cl.sync();
+}
+
+template <typename C>
+__device__ __forceinline__ void cluster_y_step(C *buf, int R, int S, int K1, int pitch, const FastDiv &dK1,
+                                               const C *tw_y, int sign) {
+    switch (R) {
+        case 2: cluster_radix<C, 2>(buf, S, K1, pitch, dK1, tw_y, sign); break;
+        case 4: cluster_radix<C, 4>(buf, S, K1, pitch, dK1, tw_y, sign); break;
+        default: cluster_radix<C, 8>(buf, S, K1, pitch, dK1, tw_y, sign); break;
+    }
+}
+
 // ------------------------------------------------------------------ pass 1: plane_fwd
 // Per-launch values of the update and closure, shared by the element loops.
 template <typename T, int MAXH>
@@ -709,12 +765,15 @@ k_plane_fwd(Fields<T> f) {
     C *tw_y = tw_h + Kz;
     C *tw_z = tw_y + Ny;
     C *tw_q = tw_z + (Kz + 1);
+    C *tw_s = reinterpret_cast<C *>(reinterpret_cast<double *>(tw_q + Kz) + (kMaxHist + 1) * (kThreadsPlane / 32));
     const bool half = f.half;
     for (int i = threadIdx.x; i < Kz; i += blockDim.x) tw_h[i] = f.tw_h[i];
     for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw_y[i] = f.tw_y[i];
     for (int i = threadIdx.x; i <= Kz; i += blockDim.x) tw_z[i] = f.tw_z[i];
     if (half)
         for (int i = threadIdx.x; i < Kz; i += blockDim.x) tw_q[i] = f.tw_q[i];
+    if (f.cl > 1)              // length-S twiddles of the local y transform: W_Ny^(R m)
+        for (int i = threadIdx.x; i < f.slab_rows; i += blockDim.x) tw_s[i] = f.tw_y[i * f.cl];
 
     // block = (x plane, row chunk yc, site): rows y0 .. y0 + nyb of plane x
     const int nyc = f.nyc;
@@ -795,6 +854,19 @@ k_plane_fwd(Fields<T> f) {
             }
         }
         __syncthreads();
+    } else if (f.cl > 1) {
+        // the y transform across the cluster (all Kz + 1 columns, unpacked): the cross-block
+        // radix step, then the local length-S transform; row y then holds ky = R y + yc
+        cluster_y_step<C>(buf, f.cl, nyb, Kz + 1, pitch, f.dK1, tw_y, -1);
+        fft_smem<C, MaxC<T>::v>(buf, f.pys, pitch, Kz + 1, 1, f.chunk_ys, tw_s, -1);
+        C *dst = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz;
+        for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
+            const int y = fdiv(idx, f.dKz), k = idx - y * Kz;
+            dst[(long long)(f.cl * y + yc) * Kz + k] = buf[y * pitch + k];
+        }
+        C *dn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny;
+        for (int y = threadIdx.x; y < nyb; y += blockDim.x) dn[f.cl * y + yc] = buf[y * pitch + Kz];
+        return;
     }
     C *dst = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz + (long long)y0 * Kz;
     for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
@@ -1152,18 +1224,34 @@ k_plane_inv(Fields<T> f) {
     A.post = half ? tw_z : nullptr;
     const C phx = half ? f.tw_xs[x] : cmk((T)1, (T)0);
 
-    const C *src = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz + (long long)y0 * Kz;
+    const bool clus = f.cl > 1;
+    // row y of the block takes spectrum row ky = y0 + y, or ky = R y + yc across a cluster
+    const int rstride = clus ? f.cl : 1, roff = clus ? yc : y0;
+    if (clus) {
+        C *tw_s = reinterpret_cast<C *>(red + (kMaxHist + 1) * (kThreadsPlane / 32));
+        for (int i = threadIdx.x; i < nyb; i += blockDim.x) tw_s[i] = f.tw_y[i * f.cl];
+    }
+    const C *src = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz;
     if (sizeof(T) == 4) {                     // 8-byte elements: asynchronous copies
         for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
             const int y = fdiv(idx, f.dKz), k = idx - y * Kz;
-            cp_async8(&buf[y * pitch + k], &src[idx]);
+            cp_async8(&buf[y * pitch + k], &src[(long long)(rstride * y + roff) * Kz + k]);
         }
         if (!half) {
-            const C *sn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny + y0;
-            for (int y = threadIdx.x; y < nyb; y += blockDim.x) cp_async8(&buf[y * pitch + Kz], &sn[y]);
+            const C *sn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny;
+            for (int y = threadIdx.x; y < nyb; y += blockDim.x)
+                cp_async8(&buf[y * pitch + Kz], &sn[rstride * y + roff]);
         }
         cp_async_wait();
+    } else if (clus) {
+        for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
+            const int y = fdiv(idx, f.dKz), k = idx - y * Kz;
+            buf[y * pitch + k] = src[(long long)(rstride * y + roff) * Kz + k];
+        }
+        const C *sn = f.spec_nyq + ((long long)gam * f.Nx + x) * Ny;
+        for (int y = threadIdx.x; y < nyb; y += blockDim.x) buf[y * pitch + Kz] = sn[rstride * y + roff];
     } else {
+        src += (long long)y0 * Kz;
         for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
             const int y = fdiv(idx, f.dKz), k = idx - y * Kz;
             buf[y * pitch + k] = src[idx];
@@ -1184,6 +1272,12 @@ k_plane_inv(Fields<T> f) {
         }
         __syncthreads();
         fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, +1);
+    } else if (clus) {
+        // inverse y transform across the cluster: the local length-S transform (it ends with
+        // a block barrier), then the cross-block radix step
+        C *tw_s = reinterpret_cast<C *>(red + (kMaxHist + 1) * (kThreadsPlane / 32));
+        fft_smem<C, MaxC<T>::v>(buf, f.pys, pitch, Kz + 1, 1, f.chunk_ys, tw_s, +1);
+        cluster_y_step<C>(buf, f.cl, nyb, Kz + 1, pitch, f.dK1, tw_y, +1);
     }
 
     GramAcc<T> acc;
@@ -2339,7 +2433,8 @@ __global__ void __launch_bounds__(kThreadsPlane, RISM_MINBLOCKS_F32) k_fft_inv(F
 // ------------------------------------------------------------------ launchers
 template <typename T> size_t plane_smem_bytes(const Fields<T> &f) {
     typedef typename Cx<T>::type C;
-    return sizeof(C) * ((size_t)f.slab_rows * f.pitch + f.Kz + f.Ny + f.Kz + 1 + f.Kz) +
+    return sizeof(C) * ((size_t)f.slab_rows * f.pitch + f.Kz + f.Ny + f.Kz + 1 + f.Kz +
+                        (f.cl > 1 ? f.slab_rows : 0)) +
            (kMaxHist + 1) * (kThreadsPlane / 32) * sizeof(double) + 16;
 }
 template <typename T> size_t pencil_smem_bytes(const Fields<T> &f) {
@@ -2469,43 +2564,57 @@ template <typename T> cudaError_t launch_ypencil(const Fields<T> &f, int sign, c
     k_ypencil<T><<<f.ytiles_main + f.ytiles_nyq, kThreadsPencil, ypencil_smem_bytes(f), s>>>(f, sign);
     return cudaGetLastError();
 }
-template <typename T, int LZ> void plane_fwd_lz(const Fields<T> &f, dim3 grid, size_t sm, cudaStream_t s) {
-    // the update combines up to M stored pairs
-    if (f.M <= 5)
-        k_plane_fwd<T, 5, LZ><<<grid, kThreadsPlane, sm, s>>>(f);
-    else if (f.M <= 8)
-        k_plane_fwd<T, 8, LZ><<<grid, kThreadsPlane, sm, s>>>(f);
-    else
-        k_plane_fwd<T, kMaxHist, LZ><<<grid, kThreadsPlane, sm, s>>>(f);
+// A plane kernel launch; with f.cl > 1 the row chunks of each plane are launched as one
+// thread-block cluster of f.cl blocks (grid x = Nx * nyc, consecutive blocks of one plane).
+template <typename T>
+cudaError_t plane_launch(void (*kernel)(Fields<T>), const Fields<T> &f, dim3 grid, size_t sm, cudaStream_t s) {
+    if (f.cl > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(kThreadsPlane);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)f.cl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kernel, f);
+    }
+    kernel<<<grid, kThreadsPlane, sm, s>>>(f);
+    return cudaGetLastError();
 }
-template <typename T, int LZ> void plane_inv_lz(const Fields<T> &f, dim3 grid, size_t sm, cudaStream_t s) {
+template <typename T, int LZ> cudaError_t plane_fwd_lz(const Fields<T> &f, dim3 grid, size_t sm, cudaStream_t s) {
+    // the update combines up to M stored pairs
+    if (f.M <= 5) return plane_launch<T>(k_plane_fwd<T, 5, LZ>, f, grid, sm, s);
+    if (f.M <= 8) return plane_launch<T>(k_plane_fwd<T, 8, LZ>, f, grid, sm, s);
+    return plane_launch<T>(k_plane_fwd<T, kMaxHist, LZ>, f, grid, sm, s);
+}
+template <typename T, int LZ> cudaError_t plane_inv_lz(const Fields<T> &f, dim3 grid, size_t sm, cudaStream_t s) {
     // the Gram row pairs the new residual with at most M - 1 stored ones
-    if (f.M <= 5)
-        k_plane_inv<T, 4, LZ><<<grid, kThreadsPlane, sm, s>>>(f);
-    else if (f.M <= 8)
-        k_plane_inv<T, 8, LZ><<<grid, kThreadsPlane, sm, s>>>(f);
-    else
-        k_plane_inv<T, kMaxHist, LZ><<<grid, kThreadsPlane, sm, s>>>(f);
+    if (f.M <= 5) return plane_launch<T>(k_plane_inv<T, 4, LZ>, f, grid, sm, s);
+    if (f.M <= 8) return plane_launch<T>(k_plane_inv<T, 8, LZ>, f, grid, sm, s);
+    return plane_launch<T>(k_plane_inv<T, kMaxHist, LZ>, f, grid, sm, s);
 }
 template <typename T> cudaError_t launch_plane_fwd(const Fields<T> &f, cudaStream_t s) {
     const size_t sm = plane_smem_bytes(f);
     const dim3 grid(f.Nx * f.nyc, f.nv);
     switch (plane_lz(f)) {
-        case 64: plane_fwd_lz<T, sizeof(T) == 4 ? 64 : 0>(f, grid, sm, s); break;
-        case 128: plane_fwd_lz<T, sizeof(T) == 4 ? 128 : 0>(f, grid, sm, s); break;
-        default: plane_fwd_lz<T, 0>(f, grid, sm, s); break;
+        case 64: return plane_fwd_lz<T, sizeof(T) == 4 ? 64 : 0>(f, grid, sm, s);
+        case 128: return plane_fwd_lz<T, sizeof(T) == 4 ? 128 : 0>(f, grid, sm, s);
+        default: return plane_fwd_lz<T, 0>(f, grid, sm, s);
     }
-    return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_plane_inv(const Fields<T> &f, cudaStream_t s) {
     const size_t sm = plane_smem_bytes(f);
     const dim3 grid(f.Nx * f.nyc, f.nv);
     switch (plane_lz(f)) {
-        case 64: plane_inv_lz<T, sizeof(T) == 4 ? 64 : 0>(f, grid, sm, s); break;
-        case 128: plane_inv_lz<T, sizeof(T) == 4 ? 128 : 0>(f, grid, sm, s); break;
-        default: plane_inv_lz<T, 0>(f, grid, sm, s); break;
+        case 64: return plane_inv_lz<T, sizeof(T) == 4 ? 64 : 0>(f, grid, sm, s);
+        case 128: return plane_inv_lz<T, sizeof(T) == 4 ? 128 : 0>(f, grid, sm, s);
+        default: return plane_inv_lz<T, 0>(f, grid, sm, s);
     }
-    return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_pencil(const Fields<T> &f, cudaStream_t s) {
     const size_t sm = pencil_smem_bytes(f);

@@ -328,28 +328,34 @@ def test_solve_fp64_modified_anderson(water_nacl, gi):
 
 # ------------------------------------------------------------------ planes split into row chunks
 @pytest.mark.parametrize("precision", [64, 32])
-@pytest.mark.parametrize("gi", [0, 1])
-def test_residual_split_planes(water_nacl, precision, gi):
-    """Row-chunked plane passes plus the y-pencil pass (the path of grids whose y-z plane
-    exceeds shared memory, forced here with 8-row chunks; Ny = 20 leaves a ragged chunk)
-    against the oracle, element by element."""
+@pytest.mark.parametrize("gi,slab,ypencil", [(0, 8, True), (1, 8, True), (0, 4, False), (0, 8, False),
+                                              (0, 16, False)])
+def test_residual_split_planes(water_nacl, precision, gi, slab, ypencil):
+    """Row-chunked plane passes (the path of grids whose y-z plane exceeds shared memory,
+    forced here with small chunks) against the oracle, element by element: with the y-pencil
+    pass (Ny = 20 in 8-row chunks leaves a ragged chunk), and with the chunks of a 32^3 plane
+    as a cluster of 8, 4 or 2 blocks doing the y transform through distributed shared memory
+    (local transforms of length 4, 8 and 16)."""
     grid = GRIDS[gi]
     sol = charged_solute()
     P = orc.Problem(water_nacl, grid, sol)
     t = P.f + 0.3 * np.random.default_rng(5 + gi).standard_normal(P.f.shape)
     ref, g, _ = P.residual(t, cl.KH, 1)
-    with solver(water_nacl, grid, precision, slab_rows=8) as S:
+    with solver(water_nacl, grid, precision, slab_rows=slab, ypencil_pass=ypencil, timing=True) as S:
         S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
         got = S.residual(t, "kh")
+        st = S.stats()["kernels"]
     scale = max(1.0, float(np.max(np.abs(g))), float(np.max(np.abs(ref))))
     assert float(np.max(np.abs(got - ref))) < (1e-10 if precision == 64 else 2e-4) * scale
+    assert (st["ypencil_fwd"]["launches"] > 0) == ypencil
 
 
-def test_solve_split_planes_fp64(water_nacl):
+@pytest.mark.parametrize("ypencil", [True, False])
+def test_solve_split_planes_fp64(water_nacl, ypencil):
     grid = GRIDS[0]
     sol = charged_solute()
     P, ref = _oracle(water_nacl, grid, sol, cl.KH, 1, 1e-6)
-    with solver(water_nacl, grid, 64, slab_rows=8, timing=True) as S:
+    with solver(water_nacl, grid, 64, slab_rows=8, ypencil_pass=ypencil, timing=True) as S:
         S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
         rep = S.solve("kh", tol=1e-6)
         g = S.get("g")
@@ -357,7 +363,8 @@ def test_solve_split_planes_fp64(water_nacl):
     assert rep["converged"] and abs(rep["iterations"] - ref["iterations"]) <= 2
     assert np.max(np.abs(g - ref["g"])) <= 1e-6
     k = st["kernels"]
-    assert k["ypencil_fwd"]["timed"] == k["plane_fwd"]["timed"] > 0
+    assert k["plane_fwd"]["timed"] > 0
+    assert k["ypencil_fwd"]["timed"] == (k["plane_fwd"]["timed"] if ypencil else 0)
 
 
 # ------------------------------------------------------------------ protein scale (256^3)
