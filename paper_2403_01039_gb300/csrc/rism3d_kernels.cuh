@@ -1641,7 +1641,8 @@ k_potential(Fields<T> f, const double *atoms, int n_atoms, const double *site_si
             double oz, double dx, double dy, double dz) {
     constexpr int TILE = 64;
     constexpr bool kMixed = sizeof(T) == 4;
-    __shared__ double ax[TILE], ay[TILE], az[TILE], aq[TILE], anear2[TILE];
+    __shared__ double ax[TILE], ay[TILE], az[TILE], aq[TILE];
+    __shared__ T anear2[TILE];
     __shared__ double dsig2[TILE][kMaxSites], deps4[TILE][kMaxSites];
     __shared__ T sx[TILE], sy[TILE], sz[TILE], sq[TILE];
     __shared__ T ssig2[TILE][kMaxSites], seps4[TILE][kMaxSites];
@@ -1693,14 +1694,14 @@ k_potential(Fields<T> f, const double *atoms, int n_atoms, const double *site_si
                 ssig2[i][g] = (T)dsig2[i][g];
                 seps4[i][g] = (T)deps4[i][g];
             }
-            anear2[i] = kMixed ? 2.25 * smax * smax : -1.0;
+            anear2[i] = kMixed ? (T)(2.25 * smax * smax) : (T)-1;
         }
         __syncthreads();
         if (active) {
             for (int i = 0; i < na; ++i) {
                 const T ddx = px - sx[i], ddy = py - sy[i], ddz = pz - sz[i];
                 const T r2f = ddx * ddx + ddy * ddy + ddz * ddz;
-                if (kMixed && (double)r2f < anear2[i]) {
+                if (kMixed && r2f < anear2[i]) {
                     const double ex = pxd - ax[i], ey = pyd - ay[i], ez = pzd - az[i];
                     double r2 = ex * ex + ey * ey + ez * ez;
                     r2 = r2 < 1e-8 ? 1e-8 : r2;
@@ -1718,11 +1719,24 @@ k_potential(Fields<T> f, const double *atoms, int n_atoms, const double *site_si
                     }
                 } else {
                     const T r2 = r2f < (T)1e-8 ? (T)1e-8 : r2f;
-                    const T ir2 = (T)1 / r2;
-                    const T r = sqrt(r2);
-                    const T ir = (T)1 / r;
+                    T ir, ir2, r, om;
+                    if constexpr (kMixed) {
+                        // far pairs (r above 1.5 sigma_ag >= 2.6 A): 1 - e^{-r} >= 0.93, so the
+                        // fast exponential keeps ~1e-7; 1/r stays correctly rounded, since the
+                        // Coulomb and phi sums of a charged solute cancel to a few % of the sum
+                        // of their magnitudes and a biased 1/r would show at 1e-5
+                        r = sqrtf(r2);
+                        ir = 1.f / r;
+                        ir2 = ir * ir;
+                        om = 1.f - __expf(-r);
+                    } else {
+                        ir2 = (T)1 / r2;
+                        r = sqrt(r2);
+                        ir = (T)1 / r;
+                        om = (T)(-expm1(-r));
+                    }
                     coul_f.add(sq[i] * ir);
-                    phi_f.add(sq[i] * (T)(-expm1(-r)) * ir);
+                    phi_f.add(sq[i] * om * ir);
 #pragma unroll
                     for (int g = 0; g < kMaxSites; ++g) {
                         if (g < nv) {
