@@ -56,6 +56,12 @@ def parse():
                    help="run the plane passes as split element/transform kernels")
     p.add_argument("--no-kernel-events", action="store_true",
                    help="time the solves without per-kernel CUDA events (no roofline)")
+    p.add_argument("--profile-iters", type=int, default=0,
+                   help="profiling case for ncu: one solve of the workload capped at this many "
+                        "iterations, no timing, no JSON line")
+    p.add_argument("--nx", type=int, default=0,
+                   help="with --profile-iters: grid planes along x (0: the workload's own), a "
+                        "smaller case with the same per-plane launch shapes")
     return p.parse_args()
 
 
@@ -169,16 +175,21 @@ def ncu_traffic(kernel, workload):
 
 
 class _HostClock:
-    """Wall and process CPU time (all threads) of a host region: their ratio is the number
+    """Wall and CPU time (all threads of this process and its finished children) of a host region: their ratio is the number
     of host cores the oracle kept busy, which numpy's BLAS may make more than one."""
 
+    @staticmethod
+    def _cpu():
+        t = os.times()           # this process (all threads) and its finished child processes
+        return t.user + t.system + t.children_user + t.children_system
+
     def __enter__(self):
-        self.w0, self.c0 = time.perf_counter(), time.process_time()
+        self.w0, self.c0 = time.perf_counter(), self._cpu()
         return self
 
     def __exit__(self, *exc):
         self.wall = time.perf_counter() - self.w0
-        self.cpu = time.process_time() - self.c0
+        self.cpu = self._cpu() - self.c0
         return False
 
 
@@ -189,7 +200,8 @@ def _cores_used(*clocks):
     return max(1, int(round(ratio))), ratio
 
 
-def oracle_sample(solv, grid, solute, closure, pse_order, mdiis_nvec, n_iter, n_atoms_sample, warm=0):
+def oracle_sample(solv, grid, solute, closure, pse_order, mdiis_nvec, n_iter, n_atoms_sample, warm=0, par=1,
+                  budget_s=0.0):
     """The FP64 oracle as it stands, timed on a bounded sample of one solve of a workload.
 
     Setup: the oracle's Problem built with the first a = n_atoms_sample atoms (its direct
@@ -197,22 +209,28 @@ def oracle_sample(solv, grid, solute, closure, pse_order, mdiis_nvec, n_iter, n_
     those a atoms' sums timed alone; the whole solute's setup is then
     T_problem(a) + (n / a - 1) T_sums(a). With a >= n the whole solute is built and timed.
     Iterations: n_iter iterations of steps 2-6 on that Problem (their cost does not depend on
-    the atoms), after ``warm`` untimed ones. Returns (t_setup, t_iter, clocks, description)."""
+    the atoms), after ``warm`` untimed ones; with ``budget_s`` > 0 the iterations continue
+    past n_iter until they have taken that long (at most 20). ``par`` > 1 runs the oracle's
+    parallel forms on that many host cores (potential sums over x-plane slabs in processes,
+    iteration steps site by site in threads). Returns (t_setup, t_iter, clocks, description)."""
     from oracle import rism3d as orc, closure as cl, potential as pot
     kinds = {"kh": cl.KH, "pse": cl.PSE, "hnc": cl.HNC}
     n = len(solute["q"])
-    a = min(n, max(1, int(n_atoms_sample)))
+    a = min(n, max(1, int(n_atoms_sample)) * max(1, par))     # a few atoms per core
     sub = {k: solute[k][:a] for k in ("xyz", "q", "sigma", "eps")}
     with _HostClock() as cs:
-        P = orc.Problem(solv, grid, sub)
+        P = orc.Problem(solv, grid, sub, workers=par, threads=par)
     clocks = [cs]
     t_setup = cs.wall
     how = "setup of all %d atoms %.1f s" % (n, t_setup)
     if a < n:
         with _HostClock() as ca:
-            pot.beta_u(P.n, P.spacing, P.origin, sub["xyz"], sub["q"], sub["sigma"], sub["eps"], P.site_q,
-                       P.site_sig, P.site_eps, P.temperature)
-            pot.phi_long_range(P.n, P.spacing, P.origin, sub["xyz"], sub["q"])
+            args = (P.n, P.spacing, P.origin, sub["xyz"], sub["q"], sub["sigma"], sub["eps"], P.site_q,
+                    P.site_sig, P.site_eps, P.temperature, False)
+            if par > 1:
+                orc._potentials_parallel(args, par)
+            else:
+                orc._potentials_slab(args + (None,))
             pot.phik_long_range(P.n, P.spacing, P.origin, sub["xyz"], sub["q"])
         clocks.append(ca)
         t_setup = cs.wall + (n / a - 1.0) * ca.wall
@@ -222,6 +240,11 @@ def oracle_sample(solv, grid, solute, closure, pse_order, mdiis_nvec, n_iter, n_
         orc.solve(P, kinds[closure], pse_order, tol=1e-300, max_iter=warm, mdiis_nvec=mdiis_nvec)
     with _HostClock() as ci:
         orc.solve(P, kinds[closure], pse_order, tol=1e-300, max_iter=n_iter, mdiis_nvec=mdiis_nvec)
+    if budget_s > 0 and ci.wall < budget_s and n_iter < 20:
+        # time again with as many iterations as fit the budget (the history is rebuilt)
+        n_iter = int(min(20, max(n_iter + 1, n_iter * budget_s / max(ci.wall, 1e-9))))
+        with _HostClock() as ci:
+            orc.solve(P, kinds[closure], pse_order, tol=1e-300, max_iter=n_iter, mdiis_nvec=mdiis_nvec)
     clocks.append(ci)
     t_iter = ci.wall / n_iter
     return t_setup, t_iter, clocks, how + "; %d iterations %.2f s each" % (n_iter, t_iter)
@@ -243,18 +266,29 @@ def oracle_iterations(workload, closure, tol, fallback):
 def cpu_baseline(args, w, solv, grid, solute, n_iter_gpu):
     """The FP64 oracle as it stands on the host cores, on a bounded sample of the same
     workload (oracle_sample), extrapolated to a whole solve with the iteration count the
-    oracle needs for this workload (stored reference), else the GPU solve's count."""
+    oracle needs for this workload (stored reference), else the GPU solve's count: once on
+    one core (the line's value) and once with the oracle's parallel forms on every core."""
     import numpy as np
-    t_setup, t_iter, clocks, how = oracle_sample(solv, grid, solute, args.closure, args.pse_order,
-                                                 w["mdiis_nvec"], args.cpu_sample_iters, args.cpu_sample_atoms)
-    cores, ratio = _cores_used(*clocks)
     n_full, src = oracle_iterations(args.workload, args.closure, args.tol,
                                     (n_iter_gpu, "the GPU solve's iteration count"))
-    t_solve = t_setup + n_full * t_iter
-    return dict(value=1.0 / t_solve, unit="solves/s", cores=cores, kind="oracle",
-                sample="%s of %s; host CPU time / wall time %.2f (%d cores available); extrapolated to "
-                       "%d iterations (%s)" % (how, args.workload, ratio, os.cpu_count() or 0, n_full, src),
-                site_gridpoint_iters_per_s=len(solv["q"]) * float(np.prod(grid["n"])) / t_iter)
+    legs = []
+    ncpu = os.cpu_count() or 1
+    for par in (1, ncpu):
+        t_setup, t_iter, clocks, how = oracle_sample(solv, grid, solute, args.closure, args.pse_order,
+                                                     w["mdiis_nvec"], args.cpu_sample_iters,
+                                                     args.cpu_sample_atoms, par=par, budget_s=10.0)
+        cores, ratio = _cores_used(*clocks)
+        legs.append(dict(value=1.0 / (t_setup + n_full * t_iter), unit="solves/s", cores=cores, kind="oracle",
+                         sample="%s of %s; host CPU time / wall time %.2f (%d cores available, %d used by "
+                                "the oracle's parallel forms); extrapolated to %d iterations (%s)"
+                                % (how, args.workload, ratio, ncpu, par, n_full, src),
+                         site_gridpoint_iters_per_s=len(solv["q"]) * float(np.prod(grid["n"])) / t_iter))
+        if ncpu == 1:
+            break
+    out = dict(legs[0])
+    if len(legs) > 1:
+        out["all_cores"] = legs[1]
+    return out
 
 
 def run_reference(args):
@@ -505,6 +539,23 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile_case(args):
+    """One solve of the workload (its grid, or --nx planes of it), capped at --profile-iters
+    iterations: the kernels a profiler captures, with the same per-plane launch shapes."""
+    from paper_2403_01039_gb300 import build, capi
+    build.build()
+    w, solv, grid, solute = workload_inputs(args.workload, product_chi)
+    if args.nx:
+        grid = dict(grid, n=(args.nx,) + tuple(grid["n"][1:]),
+                    origin=(-(args.nx // 2) * grid["spacing"][0],) + tuple(grid["origin"][1:]))
+    with capi.Solver(solv, grid, precision=args.precision, mdiis_nvec=w["mdiis_nvec"],
+                     max_iter=args.profile_iters) as S:
+        S.set_solute(solute["xyz"], solute["q"], solute["sigma"], solute["eps"])
+        rep = S.solve(args.closure, args.pse_order, args.tol, check=False)
+        print("profile case %s grid %s: %d iterations, rms %.3e, workspace %.2f GB"
+              % (args.workload, grid["n"], rep["iterations"], rep["rms"], S.workspace.numel() / 1e9))
+
+
 def run_batch(args):
     """--workload batch64: 64 seeded solutes (20-120 atoms) on uneven cubic grids (64-128,
     sizes with factors 2, 3, 5 only) in 3-site water, KH, tol 1e-6, FP32. A step is the whole
@@ -592,6 +643,8 @@ def main():
             sys.exit("--impl reference times the oracle on one solve of a single-solute workload "
                      "(%s); %s has no such form" % (", ".join(sorted(synth.WORKLOADS)), args.workload))
         run_reference(args)
+    elif args.profile_iters > 0:
+        run_profile_case(args)
     elif args.workload == "batch64":
         run_batch(args)
     else:

@@ -55,9 +55,12 @@ class Problem:
     convention; it exists only for the whole-cell shift test. ``kgrid`` = "integer" (the
     periodic grid) or "half" (half-integer k on every axis). ``workers`` > 1 evaluates the
     direct potential sums of Eqs. 22 and 29 over slabs of x planes in that many processes
-    (each grid point's sum is the same as in one process)."""
+    (each grid point's sum is the same as in one process); ``threads`` > 1 runs the steps of
+    an iteration site by site in that many threads (the same operations per site; only the
+    order of the contraction's sum over sites may differ in rounding)."""
 
-    def __init__(self, solvent, grid, solute, minimum_image=False, kgrid="integer", workers=1):
+    def __init__(self, solvent, grid, solute, minimum_image=False, kgrid="integer", workers=1, threads=1):
+        self.threads = int(threads)
         self.n = tuple(int(v) for v in grid["n"])
         self.spacing = tuple(float(v) for v in grid["spacing"])
         self.origin = tuple(float(v) for v in grid["origin"])
@@ -118,8 +121,40 @@ class Problem:
         htil = np.einsum("a...,ag...->g...", ctil, self.chik)                 # Eq. 13
         return np.fft.irfftn(htil, s=self.n, axes=axes) / self.dV           # step 5
 
+    def map_sites(self, fn, n_sites=None):
+        """[fn(site) for every site], in ``threads`` threads when more than one."""
+        n = self.n_sites if n_sites is None else n_sites
+        if self.threads <= 1:
+            return [fn(g) for g in range(n)]
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(min(self.threads, n)) as ex:
+            return list(ex.map(fn, range(n)))
+
+    def residual_threaded(self, t, kind, pse_order):
+        """residual() with every step split by site over ``threads`` threads (integer k grid)."""
+        axes = (0, 1, 2)
+        d = np.empty_like(t)
+        g = np.empty_like(t)
+        csr = np.empty_like(t)
+
+        def close(a):
+            d[a] = -self.bu[a] + t[a]
+            g[a] = cl.closure_g(d[a], kind, pse_order)
+            csr[a] = g[a] - 1.0 - t[a] + self.f[a]                          # Eq. 31
+        self.map_sites(close)
+        ctil = self.map_sites(lambda a: self.dV * np.fft.rfftn(csr[a], axes=axes) - self.ftil[a])   # Eq. 32
+        R = np.empty_like(t)
+
+        def contract(gam):
+            htil = sum(ctil[a] * self.chik[a, gam] for a in range(self.n_sites))   # Eq. 13
+            R[gam] = np.fft.irfftn(htil, s=self.n, axes=axes) / self.dV + 1.0 - g[gam]   # Eq. 33
+        self.map_sites(contract)
+        return R, g, d
+
     def residual(self, t, kind, pse_order):
         """One application of steps 2-5: returns (R, g, d) with R = t' - t = h + 1 - g."""
+        if self.threads > 1 and self.kgrid == "integer":
+            return self.residual_threaded(t, kind, pse_order)
         d, g = self.closure(t, kind, pse_order)
         csr = g - 1.0 - t + self.f                                           # Eq. 31
         h = self.rism_h(csr)
@@ -210,7 +245,10 @@ def solve(problem, kind=cl.KH, pse_order=3, tol=1e-6, max_iter=10000, mdiis_nvec
             if total >= max_iter:
                 break
             # step 6: MDIIS
-            row = np.array([float(np.sum(Ri * R)) for Ri in hist_R] + [float(np.sum(R * R))])
+            if P.threads > 1:
+                row = np.array([sum(P.map_sites(lambda a: float(np.sum(Ri[a] * R[a])))) for Ri in hist_R + [R]])
+            else:
+                row = np.array([float(np.sum(Ri * R)) for Ri in hist_R] + [float(np.sum(R * R))])
             hist_t.append(t)
             hist_R.append(R)
             k = len(hist_R)
@@ -233,7 +271,15 @@ def solve(problem, kind=cl.KH, pse_order=3, tol=1e-6, max_iter=10000, mdiis_nvec
                 hist_R.pop(0)
             gram = gram[dropped:, dropped:]
             eta = mdiis.damping(rms, mdiis_damp, dynamic_damp)
-            t = sum(ci * (ti + eta * Ri) for ci, ti, Ri in zip(c, hist_t, hist_R))
+            if P.threads > 1:
+                tn = np.empty_like(t)
+
+                def update(a):
+                    tn[a] = sum(ci * (ti[a] + eta * Ri[a]) for ci, ti, Ri in zip(c, hist_t, hist_R))
+                P.map_sites(update)
+                t = tn
+            else:
+                t = sum(ci * (ti + eta * Ri) for ci, ti, Ri in zip(c, hist_t, hist_R))
         if not converged:
             break
     d, g = P.closure(t, kind, pse_order)
