@@ -52,6 +52,8 @@ def parse():
                    help="atoms whose direct potential sums the CPU baseline times (scaled to all)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--inflight", type=int, default=8, help="batch64: jobs in flight")
+    p.add_argument("--no-forms", action="store_true",
+                   help="skip the batched and learned-guess forms measured after the main line")
     p.add_argument("--split-passes", action="store_true",
                    help="run the plane passes as split element/transform kernels")
     p.add_argument("--no-kernel-events", action="store_true",
@@ -520,6 +522,21 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, w, solv, grid, solute, reps[-1]["iterations"])
 
+    # the batched and learned-guess forms, each against the plain solve of its own workload
+    forms = None
+    ws_gb = S.workspace.numel() / 1e9
+    if rank == 0 and not args.no_forms:
+        S.close()
+        S.workspace = None                    # the forms create their own contexts
+        torch.cuda.empty_cache()
+        forms = {}
+        for name, fn in (("batch64", lambda: batch_measure(32, 1e-6, args.inflight, 1, 1)),
+                         ("learned_guess_solute50_128", lambda: learned_guess_measure())):
+            try:
+                forms[name] = fn()
+            except Exception as exc:          # context for the line, never fails the bench
+                forms[name] = dict(error="%s: %s" % (type(exc).__name__, exc))
+
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit="solves/s", n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=secs * 1e3 / args.steps, higher_is_better=True,
@@ -528,11 +545,12 @@ def run_ours(args):
                     config=dict(workload=args.workload, grid="%d^3 x %.3g A" % (w["n"], w["spacing"]),
                                 sites=nv, atoms=len(solute["q"]), closure=args.closure, tol=args.tol,
                                 mdiis=w["mdiis_nvec"], parallelism="replicas" if world > 1 else "single",
-                                l2="inputs larger than L2 (working set %.2f GB)" % (S.workspace.numel() / 1e9)),
+                                l2="inputs larger than L2 (working set %.2f GB)" % ws_gb),
                     site_gridpoint_iters_per_s=sgi, iterations_per_solve=iters_all / (world * args.steps),
                     roofline=roofline, cpu_baseline=cpu,
                     e2e=dict(value=e2e_val, unit="solves/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
-                    gpu_launches=launches, clocks=clk, kernels=kernels_out, cufft_comparison=cufft)
+                    gpu_launches=launches, clocks=clk, kernels=kernels_out, cufft_comparison=cufft,
+                    forms=forms)
         print(json.dumps(line), flush=True)
     S.close()
     if world > 1:
@@ -556,83 +574,126 @@ def run_profile_case(args):
               % (args.workload, grid["n"], rep["iterations"], rep["rms"], S.workspace.numel() / 1e9))
 
 
-def run_batch(args):
-    """--workload batch64: 64 seeded solutes (20-120 atoms) on uneven cubic grids (64-128,
-    sizes with factors 2, 3, 5 only) in 3-site water, KH, tol 1e-6, FP32. A step is the whole
-    batch: every job's set_solute + solve + SFE, once one at a time and once through
-    rism3d_solve_batch; value is the batched solves/s, the one-at-a-time rate is reported
-    beside it. Contexts are created (one per grid) before timing."""
+def batch_measure(precision, tol, inflight, steps, warmup, with_clocks=False):
+    """The batch64 form: 64 seeded solutes (20-120 atoms) on uneven cubic grids (64-128, sizes
+    with factors 2, 3, 5 only) in 3-site water, KH, MDIIS 5. A step is the whole batch: every
+    job's set_solute + solve + SFE, once one at a time and once through rism3d_solve_batch.
+    Contexts are created (one per grid) and their pencil tiles tuned before timing."""
     import numpy as np
     import torch
 
-    from paper_2403_01039_gb300 import build, capi, synth
+    from paper_2403_01039_gb300 import capi, synth
 
-    build.build()
-    torch.cuda.set_device(0)
     sites = synth.water_3site()
     chi, dk, _, _ = capi.xrism(sites)
     solv = dict(sites, chi=chi, dk=dk)
     work = synth.batch_workload()
-    solvers = [capi.Solver(solv, w["grid"], precision=args.precision, mdiis_nvec=5) for w in work]
-    # pencil tiles autotuned per grid, once per context (before timing)
-    tuned = []
-    for S, w in zip(solvers, work):
-        sol = w["solute"]
-        S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
-        tuned.append(S.tune()[0])
-
-    def one_at_a_time():
-        its = 0
+    solvers = [capi.Solver(solv, w["grid"], precision=precision, mdiis_nvec=5) for w in work]
+    try:
+        tuned = []
         for S, w in zip(solvers, work):
             sol = w["solute"]
             S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
-            its += S.solve("kh", tol=args.tol)["iterations"]
-            S.sfe("kh")
-        return its
+            tuned.append(S.tune()[0])
 
-    site_points = [len(sites["q"]) * float(np.prod(w["grid"]["n"])) for w in work]
-    spi = []                                  # site-point-iterations of each batched pass
+        def one_at_a_time():
+            its = 0
+            for S, w in zip(solvers, work):
+                sol = w["solute"]
+                S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+                its += S.solve("kh", tol=tol)["iterations"]
+                S.sfe("kh")
+            return its
 
-    def batched():
-        jobs = [dict(solver=S, solute=w["solute"], closure="kh", tol=args.tol, sfe="kh")
-                for S, w in zip(solvers, work)]
-        res = capi.solve_batch(jobs, max_inflight=args.inflight)
-        bad = [r for r in res if r["status"] != "OK"]
-        if bad:
-            raise RuntimeError("batch job failed: %s" % bad[0])
-        spi.append(sum(p * r["iterations"] for p, r in zip(site_points, res)))
-        return sum(r["iterations"] for r in res)
+        site_points = [len(sites["q"]) * float(np.prod(w["grid"]["n"])) for w in work]
+        spi = []
 
-    def timed(fn):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        its = sum(fn() for _ in range(args.steps))
-        torch.cuda.synchronize()
-        return time.perf_counter() - t0, its
+        def batched():
+            jobs = [dict(solver=S, solute=w["solute"], closure="kh", tol=tol, sfe="kh")
+                    for S, w in zip(solvers, work)]
+            res = capi.solve_batch(jobs, max_inflight=inflight)
+            bad = [r for r in res if r["status"] != "OK"]
+            if bad:
+                raise RuntimeError("batch job failed: %s" % bad[0])
+            spi.append(sum(p * r["iterations"] for p, r in zip(site_points, res)))
+            return sum(r["iterations"] for r in res)
 
-    clocks = ClockSampler(0)
-    t_seq, it_seq = timed(one_at_a_time)
-    clocks.start()
-    t_bat, it_bat = timed(batched)
-    clk = clocks.stop()
-    n = len(work) * args.steps
-    line = dict(metric=METRIC, value=n / t_bat, unit="solves/s", n_gpus=1, steps=args.steps,
-                warmup=args.warmup, ms_per_step=t_bat * 1e3 / args.steps, higher_is_better=True,
+        def timed(fn):
+            for _ in range(warmup):
+                fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its = sum(fn() for _ in range(steps))
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0, its
+
+        t_seq, it_seq = timed(one_at_a_time)
+        clocks = ClockSampler(0) if with_clocks else None
+        if clocks:
+            clocks.start()
+        t_bat, it_bat = timed(batched)
+        clk = clocks.stop() if clocks else None
+    finally:
+        for S in solvers:
+            S.close()
+    n = len(work) * steps
+    return dict(batched=n / t_bat, one_at_a_time=n / t_seq, speedup=t_seq / t_bat, unit="solves/s",
+                jobs=len(work), steps=steps, warmup=warmup, inflight=inflight, tol=tol,
+                batched_iterations=it_bat, one_at_a_time_iterations=it_seq, t_batched_s=t_bat,
+                site_gridpoint_iters_per_s=sum(spi[-steps:]) / t_bat,
+                pencil_widths={str(k): tuned.count(k) for k in sorted(set(tuned))}, clocks=clk)
+
+
+def learned_guess_measure(n_seeds=8, tol=1e-6):
+    """The learned-initial-guess form on held-out solutes of the solute50_128 kind (seeds
+    60000..): set_solute + solve from the zero guess against set_solute + network + solve
+    from the network's guess, with the stored trained weights; FP32, 128^3, KH."""
+    import numpy as np
+    import torch
+
+    from paper_2403_01039_gb300 import capi, guess, synth
+
+    wpath = os.path.join(ROOT, "paper_2403_01039_gb300", "data", "guess_unet_solute50_128.npz")
+    W = np.load(wpath)
+    crop = int(W["crop"])
+    solv = guess._solvent()
+    net = capi.UNet3D(5, 5, crop, tuple(int(c) for c in W["channels"]))
+    try:
+        net.set_params(W["params"])
+        with capi.Solver(solv, synth.cubic_grid(128, 0.5), precision=32, mdiis_nvec=5) as S:
+            seeds = [guess.TEST_SEED0 + i for i in range(n_seeds)]
+            guess.evaluate(S, net, seeds[:1], tol=tol)                  # warm-up
+            ev = guess.evaluate(S, net, seeds, tol=tol)
+    finally:
+        net.close()
+    zi, gi = np.array(ev["zero_iters"]), np.array(ev["guess_iters"])
+    return dict(seeds="%d held-out solutes, seeds %d-%d" % (n_seeds, seeds[0], seeds[-1]),
+                zero_guess=dict(iterations_mean=float(zi.mean()), solves_per_s=len(zi) / float(np.sum(ev["zero_s"]))),
+                learned_guess=dict(iterations_mean=float(gi.mean()), solves_per_s=len(gi) / float(np.sum(ev["guess_s"]))),
+                fewer_iterations=int(np.sum(gi < zi)), more_iterations=int(np.sum(gi > zi)),
+                speedup=float(np.sum(ev["zero_s"]) / np.sum(ev["guess_s"])), unit="solves/s", tol=tol)
+
+
+def run_batch(args):
+    """--workload batch64 (batch_measure): value is the batched solves/s, the one-at-a-time
+    rate is reported beside it."""
+    import torch
+
+    from paper_2403_01039_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    m = batch_measure(args.precision, args.tol, args.inflight, args.steps, args.warmup, with_clocks=True)
+    line = dict(metric=METRIC, value=m["batched"], unit="solves/s", n_gpus=1, steps=args.steps,
+                warmup=args.warmup, ms_per_step=m["t_batched_s"] * 1e3 / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f32" if args.precision == 32 else "f64",
                 data="synthetic",
-                config=dict(workload="batch64", jobs=len(work), grids="64-128 cubic (2,3,5 sizes) x 0.5 A",
-                            sites=len(sites["q"]), atoms="20-120", closure="kh", tol=args.tol, mdiis=5,
-                            inflight=args.inflight, parallelism="single",
-                            pencil_widths={str(k): tuned.count(k) for k in sorted(set(tuned))}),
-                one_at_a_time=dict(value=n / t_seq, unit="solves/s", iterations=it_seq),
-                batched_iterations=it_bat,
-                site_gridpoint_iters_per_s=sum(spi[-args.steps:]) / t_bat,
-                clocks=clk)
+                config=dict(workload="batch64", jobs=m["jobs"], grids="64-128 cubic (2,3,5 sizes) x 0.5 A",
+                            sites=3, atoms="20-120", closure="kh", tol=args.tol, mdiis=5,
+                            inflight=args.inflight, parallelism="single", pencil_widths=m["pencil_widths"]),
+                one_at_a_time=dict(value=m["one_at_a_time"], unit="solves/s", iterations=m["one_at_a_time_iterations"]),
+                batched_iterations=m["batched_iterations"],
+                site_gridpoint_iters_per_s=m["site_gridpoint_iters_per_s"], clocks=m["clocks"])
     print(json.dumps(line), flush=True)
-    for S in solvers:
-        S.close()
 
 
 def main():

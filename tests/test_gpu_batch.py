@@ -1,6 +1,6 @@
 """The batched form (rism3d_solve_batch): independent solutes on uneven grids solved
-concurrently must give exactly what one-at-a-time solves give, honour the time limit and
-reject job lists it cannot schedule."""
+concurrently must give exactly what one-at-a-time solves give, match the FP64 oracle on
+every distinct grid, honour the time limit and reject job lists it cannot schedule."""
 import numpy as np
 import pytest
 
@@ -93,3 +93,32 @@ def test_batch_shared_stream_and_rejected_context(water3):
         assert all(r["status"] == "ESTATE" for r in res)
         with pytest.raises(capi.RismError):
             A.solve("kh")                                          # no solute was set
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batch_matches_oracle(water3, precision):
+    """Every job of the uneven-grid batch against the oracle: FP64 against the oracle run with
+    the same algorithm and tolerance (max|dg| <= 1e-6, |dSFE| <= 1e-4 kcal/mol, iterations
+    +-2), FP32 (converged to 1e-7) against the oracle at 1e-10 (1e-3, 0.05 kcal/mol)."""
+    from oracle import rism3d as orc, closure as cl
+    tol = 1e-6 if precision == 64 else 1e-7
+    solvers = [capi.Solver(water3, grid, precision=precision, slab_rows=slab) for grid, _, slab in JOBS]
+    try:
+        jobs = [dict(solver=S, solute=_solute(k, JOBS[k][1]), closure="kh", tol=tol, sfe="kh")
+                for k, S in enumerate(solvers)]
+        res = capi.solve_batch(jobs, max_inflight=3)
+        for k, (r, S) in enumerate(zip(res, solvers)):
+            grid, n_atoms, _ = JOBS[k]
+            P = orc.Problem(water3, grid, _solute(k, n_atoms))
+            ref = orc.solve(P, cl.KH, 1, tol=1e-6 if precision == 64 else 1e-10, mdiis_nvec=5)
+            sref = orc.sfe(P, ref, cl.SFE_KH)[0]
+            assert r["status"] == "OK" and r["converged"], r
+            dg = float(np.max(np.abs(S.get("g") - ref["g"])))
+            if precision == 64:
+                assert dg <= 1e-6 and abs(r["sfe"] - sref) <= 1e-4, (k, dg, r["sfe"], sref)
+                assert abs(r["iterations"] - ref["iterations"]) <= 2, (k, r["iterations"], ref["iterations"])
+            else:
+                assert dg <= 1e-3 and abs(r["sfe"] - sref) <= 0.05, (k, dg, r["sfe"], sref)
+    finally:
+        for S in solvers:
+            S.close()
