@@ -522,6 +522,23 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, w, solv, grid, solute, reps[-1]["iterations"])
 
+    # measured FMA rates of this GPU; the FP64 form is bound by FP64 arithmetic rather than HBM
+    fma = None
+    if rank == 0:
+        try:
+            fma = {"fp32_tflops": capi.fma_rate(32) / 1e12, "fp64_tflops": capi.fma_rate(64) / 1e12}
+        except Exception as exc:
+            fma = dict(error="%s: %s" % (type(exc).__name__, exc))
+    alu = None
+    if fma and "fp64_tflops" in fma and args.precision == 64:
+        # the survey's arithmetic model per site-point and iteration: the R2C + C2R pair
+        # 5 log2(N^3), closure ~20, contraction 2 n_v, MDIIS ~6M
+        flops = 5.0 * np.log2(float(G)) + 20.0 + 2.0 * nv + 6.0 * w["mdiis_nvec"]
+        ach = flops * sgi / 1e12
+        alu = dict(bound="fp64 alu", flops_per_site_point_iteration=flops, achieved=ach,
+                   peak=fma["fp64_tflops"], unit="TFLOP/s", frac=ach / fma["fp64_tflops"],
+                   peak_source="measured FP64 FMA rate (rism3d_fma_rate)")
+
     # the batched and learned-guess forms, each against the plain solve of its own workload
     forms = None
     ws_gb = S.workspace.numel() / 1e9
@@ -550,7 +567,7 @@ def run_ours(args):
                     roofline=roofline, cpu_baseline=cpu,
                     e2e=dict(value=e2e_val, unit="solves/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                     gpu_launches=launches, clocks=clk, kernels=kernels_out, cufft_comparison=cufft,
-                    forms=forms)
+                    fma_rates=fma, roofline_fp64_alu=alu, forms=forms)
         print(json.dumps(line), flush=True)
     S.close()
     if world > 1:

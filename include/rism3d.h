@@ -325,6 +325,13 @@ rism3d_status rism3d_sfe_noalloc(int n_sites, long long n_points, const double *
                                  int kind, int pse_order, double *total, double *per_site,
                                  void *cuda_stream);
 
+/* FP32 (precision 32) or FP64 (64) fused multiply-add throughput of the current device in
+ * flop/s (2 per FMA), measured with CUDA events around a kernel of independent FMA chains
+ * on every SM (best of five runs). A measurement of the machine for the roofline of the
+ * arithmetic-bound FP64 form, not part of the method: the paper has no counterpart.
+ * RISM3D_EINVAL for another precision or a NULL pointer, RISM3D_ECUDA on a CUDA error. */
+rism3d_status rism3d_fma_rate(int precision, double *flops_per_s);
+
 /* Message of the last failure on ctx (or of the last failed create when ctx is NULL). */
 const char *rism3d_last_error(const rism3d_ctx *ctx);
 

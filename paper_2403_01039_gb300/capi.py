@@ -120,6 +120,7 @@ def load():
     sig.update({
         "rism3d_sfe_noalloc": (c_int, [c_int, ctypes.c_longlong, c_void_p, c_void_p, c_void_p, _dp,
                                        c_double, c_double, c_int, c_int, P(c_double), _dp, c_void_p]),
+        "rism3d_fma_rate": (c_int, [c_int, P(c_double)]),
         "rism1d_options_default": (None, [P(Rism1dOptions)]),
         "rism1d_xrism": (c_int, [P(Rism1dSolvent), P(Rism1dOptions), _dp, _dp, P(c_int), _dp]),
         "rism1d_xrism_ex": (c_int, [P(Rism1dSolvent), P(Rism1dOptions), _dp, _dp, _dp, _dp, _dp,
@@ -243,6 +244,16 @@ def sfe_noalloc(h, c, rho, temperature, dV, kind="kh", pse_order=3, d=None, stre
     if st != OK:
         raise RismError(st, lib.rism3d_last_error(None).decode())
     return tot.value, per
+
+
+def fma_rate(precision):
+    """FP32 (32) or FP64 (64) FMA throughput of the current device in flop/s (rism3d_fma_rate)."""
+    lib = load()
+    r = ctypes.c_double()
+    st = lib.rism3d_fma_rate(int(precision), ctypes.byref(r))
+    if st != OK:
+        raise RismError(st, "rism3d_fma_rate failed")
+    return r.value
 
 
 def xrism(sites, n_r=2048, dr=0.05, closure="kh", tol=1e-10, charge_steps=10, thermo=False,
