@@ -100,7 +100,7 @@ def make_full(workload, closures=((cl.KH, 3, "kh"), (cl.PSE, 3, "pse3")), tols=(
             np.savez_compressed(os.path.join(HERE, "%s_reference.npz" % workload), **out)
 
 
-def make_globule(workload="globule2000_256", tol=1e-10, snapshots=(1e-6, 1e-8), workers=6):
+def make_globule(workload="globule2000_256", tol=1e-10, snapshots=(1e-6, 1e-8), workers=8, threads=5):
     """One KH oracle solve of the protein-scale workload to ``tol``, with the solutions a
     solve stopped at each of ``snapshots`` returns (the same run). Stores, for each
     tolerance, g, c and t at 4096 seeded grid points (all sites), the whole x = N/2 plane
@@ -113,7 +113,7 @@ def make_globule(workload="globule2000_256", tol=1e-10, snapshots=(1e-6, 1e-8), 
                 temperature=s["temperature"], chi=chi["chi"], dk=float(chi["dk"]))
     grid = synth.cubic_grid(w["n"], w["spacing"])
     t0 = time.time()
-    P = rism3d.Problem(solv, grid, synth.workload_solute(workload), workers=workers)
+    P = rism3d.Problem(solv, grid, synth.workload_solute(workload), workers=workers, threads=threads)
     print("setup %.0f s" % (time.time() - t0), flush=True)
     pts = sample_points(w["n"], 4096, 7)
     idx = (slice(None), pts[:, 0], pts[:, 1], pts[:, 2])
