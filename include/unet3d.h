@@ -19,7 +19,15 @@
  * concatenation. Parameters are one flat FP32 vector, layer by layer, each layer's weights
  * ([out][in][3][3][3], or [out][in] for the last) followed by its biases.
  *
- * Arithmetic: FP32 with FP32 accumulation (direct convolutions over shared-memory tiles).
+ * Arithmetic, chosen at creation (unet3d_create_ex):
+ *   UNET3D_FP32  FP32 activations, FP32 direct convolutions over shared-memory tiles.
+ *   UNET3D_BF16  BF16 activations (channels-last inside the network), the 3x3x3
+ *                convolutions, their data gradients and their weight gradients as implicit
+ *                GEMMs on the tensor cores (tcgen05.mma, BF16 operands, FP32 accumulation in
+ *                tensor memory); the 1x1x1 output layer, loss and Adam in FP32. Parameters,
+ *                gradients and moments stay FP32 in both forms (the same flat vector), so
+ *                parameters trained in one form run in the other. Needs c0, c1, c2 multiples
+ *                of 16 with c2 + c1 <= 256; the input channels are padded to a multiple of 16.
  * Every array argument is device memory of the current CUDA device unless stated; every
  * call returns 0 on success, else a nonzero code with a message in unet3d_last_error():
  * 1 bad arguments, 2 allocation failure, 3 a CUDA error, 4 a call out of order.
@@ -36,10 +44,17 @@ extern "C" {
 
 typedef struct unet3d unet3d;
 
+enum { UNET3D_FP32 = 0, UNET3D_BF16 = 1 };
+
 /* Allocates parameters, gradients, Adam moments and the activations of one crop.
  * n_in, n_out >= 1; crop >= 4 and divisible by 4; channels >= 1. stream: cudaStream_t or
  * NULL (the legacy default stream). Returns 1 on bad arguments, 2 on allocation failure. */
 int unet3d_create(int n_in, int n_out, int crop, int c0, int c1, int c2, void *stream, unet3d **out);
+
+/* unet3d_create with the arithmetic form (UNET3D_FP32 or UNET3D_BF16); returns 1 when the
+ * channels do not suit the form. unet3d_create is unet3d_create_ex(..., UNET3D_FP32, ...). */
+int unet3d_create_ex(int n_in, int n_out, int crop, int c0, int c1, int c2, int arith, void *stream,
+                     unet3d **out);
 
 /* Number of FP32 parameters (weights and biases of all layers). */
 size_t unet3d_param_count(const unet3d *net);
@@ -68,6 +83,20 @@ int unet3d_mse(unet3d *net, const float *y, const float *target, size_t count, d
 int unet3d_adam(unet3d *net, float lr, float beta1, float beta2, float eps, int t);
 
 const char *unet3d_last_error(void);
+
+/* One 3x3x3 convolution of the BF16 form on caller buffers (device memory; BF16 arrays are
+ * channels-last, voxel p of the n^3 volume at [p][channels]), for callers that run single
+ * layers and for checking the tensor-core kernels against a reference convolution:
+ *   mode 0: out[p][o] = bf16(b[o] + sum_c sum_tap w[o][c][tap] in[p + tap - 1][c]), in
+ *           [n^3][cin], out [n^3][cout], b FP32 [cout] or NULL, ReLU when relu != 0;
+ *   mode 1: data gradient, in = dL/dy [n^3][cout], out = dL/dx [n^3][cin] (BF16);
+ *   mode 2: weight gradient, in = x [n^3][cin], in2 = dL/dy [n^3][cout],
+ *           out = dL/dw FP32 [cout][cin][27].
+ * w is FP32 [cout][cin][27] (rounded to BF16 for the products); zero padding outside the
+ * volume. cin and cout multiples of 16 (cout <= 128; cin <= 128 in mode 1). Allocates its
+ * scratch on the device and returns after the stream has finished (synchronous). */
+int unet3d_conv3_bf16(int mode, int n, int cin, int cout, const void *in, const void *in2, const float *w,
+                      const float *b, int relu, void *out, void *stream);
 
 void unet3d_destroy(unet3d *net);
 

@@ -18,10 +18,29 @@ Loss: mean squared error over all outputs.
 
 Every routine is a plain definition (direct sums over the 27 taps); the backward pass is
 the chain rule through the same definitions.
+
+BF16 storage form (``store=bf16_round``): the network of the BF16 configuration keeps its
+activations and their gradients as bfloat16 values and multiplies BF16 weights; forward()
+and backward() then round, at the points where that form stores a value, with the plain
+definition of bfloat16 rounding (the FP32 value rounded to 8 significand bits, to nearest,
+ties to even). Sums and products stay FP64.
 """
 import numpy as np
 
 CHANNELS = (16, 32, 64)
+
+
+def bf16_round(a):
+    """a rounded to the nearest bfloat16 value (ties to even), returned as float64: the
+    float32 value of a keeps its upper 16 bits after adding half of the dropped range."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _keep(a):
+    return a
 
 
 def conv3(x, w, b):
@@ -90,21 +109,23 @@ def init_params(n_in, n_out, seed, channels=CHANNELS):
     return params
 
 
-def forward(params, x):
-    """Returns (y, cache) for one crop x [n_in, n, n, n]."""
+def forward(params, x, store=None):
+    """Returns (y, cache) for one crop x [n_in, n, n, n]. ``store`` (e.g. bf16_round) is
+    applied to the input, to the 3x3x3 weights and to every stored activation."""
+    st = store or _keep
     cache = {}
 
     def block(name, inp, k):
-        a = conv3(inp, *params[k])
-        ra = np.maximum(a, 0.0)
-        b = conv3(ra, *params[k + 1])
-        rb = np.maximum(b, 0.0)
+        a = conv3(inp, st(params[k][0]), params[k][1])
+        ra = st(np.maximum(a, 0.0))
+        b = conv3(ra, st(params[k + 1][0]), params[k + 1][1])
+        rb = st(np.maximum(b, 0.0))
         cache[name] = (inp, a, ra, b)
         return rb
 
-    e1 = block("e1", x, 0)
-    e2 = block("e2", pool(e1), 2)
-    m = block("m", pool(e2), 4)
+    e1 = block("e1", st(x), 0)
+    e2 = block("e2", st(pool(e1)), 2)
+    m = block("m", st(pool(e2)), 4)
     d2 = block("d2", np.concatenate([up(m), e2]), 6)
     d1 = block("d1", np.concatenate([up(d2), e1]), 8)
     y = conv1(d1, *params[10])
@@ -112,32 +133,35 @@ def forward(params, x):
     return y, cache
 
 
-def backward(params, cache, gy):
-    """Gradients [[gw, gb], ...] of the loss given dL/dy, in the order of params."""
+def backward(params, cache, gy, store=None):
+    """Gradients [[gw, gb], ...] of the loss given dL/dy, in the order of params. With
+    ``store``, the data gradients of the 3x3x3 layers use the stored (rounded) weights and
+    every stored activation gradient is rounded; weight and bias gradients are not."""
+    st = store or _keep
     grads = [None] * len(params)
     d1 = cache["out"]
     grads[10] = [np.einsum("oijk,cijk->oc", gy, d1), gy.sum(axis=(1, 2, 3))]
-    g = np.einsum("oc,oijk->cijk", params[10][0], gy)
+    g = st(np.einsum("oc,oijk->cijk", params[10][0], gy))
 
     def block_back(name, g_out, k):
         inp, a, ra, b = cache[name]
         gb_ = g_out * (b > 0)
-        gra, gw1, gbias1 = conv3_backward(ra, params[k + 1][0], gb_)
-        ga = gra * (a > 0)
-        ginp, gw0, gbias0 = conv3_backward(inp, params[k][0], ga)
+        gra, gw1, gbias1 = conv3_backward(ra, st(params[k + 1][0]), gb_)
+        ga = st(gra) * (a > 0)
+        ginp, gw0, gbias0 = conv3_backward(inp, st(params[k][0]), ga)
         grads[k] = [gw0, gbias0]
         grads[k + 1] = [gw1, gbias1]
-        return ginp
+        return st(ginp)
 
     c0, c1, c2 = params[0][0].shape[0], params[2][0].shape[0], params[4][0].shape[0]
     gcat1 = block_back("d1", g, 8)                     # [c1 + c0]
-    g_d2 = up_backward(gcat1[:c1])
+    g_d2 = st(up_backward(gcat1[:c1]))
     g_e1 = gcat1[c1:].copy()
     gcat2 = block_back("d2", g_d2, 6)                  # [c2 + c1]
-    g_m = up_backward(gcat2[:c2])
+    g_m = st(up_backward(gcat2[:c2]))
     g_e2 = gcat2[c2:].copy()
-    g_e2 += pool_backward(block_back("m", g_m, 4))
-    g_e1 += pool_backward(block_back("e2", g_e2, 2))
+    g_e2 = st(g_e2 + pool_backward(block_back("m", g_m, 4)))
+    g_e1 = st(g_e1 + pool_backward(block_back("e2", g_e2, 2)))
     block_back("e1", g_e1, 0)
     return grads
 

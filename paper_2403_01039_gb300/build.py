@@ -15,7 +15,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "librism3d.so")
 
 SOURCES = ["rism3d_planes_f32.cu", "rism3d_kernels_f32.cu", "rism3d_planes_f64.cu", "rism3d_kernels_f64.cu",
-           "rism3d_capi.cu", "rism3d_noalloc.cu", "rism3d_microbench.cu", "unet3d.cu",
+           "rism3d_capi.cu", "rism3d_noalloc.cu", "rism3d_microbench.cu", "unet3d.cu", "unet3d_tc.cu",
            "rism1d.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

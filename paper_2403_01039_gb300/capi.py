@@ -100,6 +100,9 @@ def load():
         "rism3d_guess_target": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
         "rism3d_set_guess_crop": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
         "unet3d_create": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, c_void_p, P(c_void_p)]),
+        "unet3d_create_ex": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, c_int, c_void_p, P(c_void_p)]),
+        "unet3d_conv3_bf16": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                                      c_void_p, c_void_p]),
         "unet3d_param_count": (c_size_t, [c_void_p]),
         "unet3d_set_params": (c_int, [c_void_p, P(ctypes.c_float)]),
         "unet3d_get_params": (c_int, [c_void_p, P(ctypes.c_float)]),
@@ -537,17 +540,21 @@ class Solver:
 
 class UNet3D:
     """The learned-guess network of ``unet3d.h`` (device kernels of the library); tensors
-    are float32 CUDA tensors, parameters a flat float32 numpy vector."""
+    are float32 CUDA tensors, parameters a flat float32 numpy vector. ``arith`` is "fp32"
+    (UNET3D_FP32) or "bf16" (UNET3D_BF16: tensor-core convolutions, BF16 activations)."""
 
-    def __init__(self, n_in, n_out, crop, channels=(16, 32, 64), stream=None):
+    ARITH = {"fp32": 0, "bf16": 1}
+
+    def __init__(self, n_in, n_out, crop, channels=(16, 32, 64), stream=None, arith="fp32"):
         import torch
         self._torch = torch
         self.lib = load()
         self.n_in, self.n_out, self.crop = n_in, n_out, crop
+        self.arith = arith
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         net = ctypes.c_void_p()
-        st = self.lib.unet3d_create(n_in, n_out, crop, channels[0], channels[1], channels[2],
-                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(net))
+        st = self.lib.unet3d_create_ex(n_in, n_out, crop, channels[0], channels[1], channels[2], self.ARITH[arith],
+                                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(net))
         if st != 0:
             raise RuntimeError("unet3d_create: " + self.lib.unet3d_last_error().decode())
         self.net = net
@@ -603,6 +610,35 @@ class UNet3D:
             self.close()
         except Exception:
             pass
+
+
+def conv3_bf16(mode, n, cin, cout, inp, w, b=None, relu=False, in2=None, out=None):
+    """unet3d_conv3_bf16 on torch CUDA tensors: ``inp`` (and ``in2``) bfloat16 channels-last
+    [n^3, channels], ``w`` float32 [cout, cin, 27], ``b`` float32 [cout] or None. Mode 0
+    returns y [n^3, cout] (bfloat16), mode 1 dL/dx [n^3, cin] (bfloat16), mode 2 dL/dw
+    [cout, cin, 27] (float32)."""
+    import torch
+    lib = load()
+    dev = inp.device
+    for name, t, dt in (("inp", inp, torch.bfloat16), ("in2", in2, torch.bfloat16), ("w", w, torch.float32),
+                        ("b", b, torch.float32)):
+        if t is not None and (t.device != dev or t.dtype != dt or not t.is_contiguous()):
+            raise ValueError("%s must be a contiguous %s tensor on %s" % (name, dt, dev))
+    if mode == 0:
+        out = torch.empty((n ** 3, cout), dtype=torch.bfloat16, device=dev) if out is None else out
+    elif mode == 1:
+        out = torch.empty((n ** 3, cin), dtype=torch.bfloat16, device=dev) if out is None else out
+    else:
+        out = torch.empty((cout, cin, 27), dtype=torch.float32, device=dev) if out is None else out
+    with torch.cuda.device(dev):
+        stream = torch.cuda.current_stream()
+        st = lib.unet3d_conv3_bf16(int(mode), int(n), int(cin), int(cout), ctypes.c_void_p(inp.data_ptr()),
+                                   ctypes.c_void_p(in2.data_ptr() if in2 is not None else 0),
+                                   ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(b.data_ptr() if b is not None else 0),
+                                   int(bool(relu)), ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    if st != 0:
+        raise RuntimeError("unet3d_conv3_bf16: " + lib.unet3d_last_error().decode())
+    return out
 
 
 def flatten_params(params):

@@ -1,14 +1,19 @@
-// 3D U-Net of the learned initial guess: forward, backward, loss and Adam (FP32, direct
-// convolutions over shared-memory tiles). The network is described in unet3d.h; the
-// gradient is the chain rule through the same operations in reverse.
+// 3D U-Net of the learned initial guess: forward, backward, loss and Adam. The network is
+// described in unet3d.h; the gradient is the chain rule through the same operations in
+// reverse. Two arithmetic forms share the parameters, loss and optimiser: FP32 (direct
+// convolutions over shared-memory tiles, channels-first activations) and BF16 (implicit-GEMM
+// convolutions on the tensor cores with FP32 accumulation, channels-last BF16 activations;
+// unet3d_tc.cu).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "unet3d.h"
+#include "unet3d_tc.h"
 
 namespace {
 
@@ -387,6 +392,17 @@ struct unet3d {
     float *wt = nullptr, *part = nullptr;
     size_t part_floats = 0;
     double *mse_part = nullptr, *mse_host = nullptr;
+    // BF16 form (arith = UNET3D_BF16): channels-last BF16 activations and their gradients
+    int arith = UNET3D_FP32, cin0 = 0;       // cin0: input channels padded to a multiple of 16
+    int *status = nullptr;                   // first failure reported by a tensor-core kernel
+    __nv_bfloat16 *bx = nullptr, *bcat1 = nullptr, *be1a = nullptr, *bp1 = nullptr, *bcat2 = nullptr;
+    __nv_bfloat16 *be2a = nullptr, *bp2 = nullptr, *bma = nullptr, *bmid = nullptr, *bd2a = nullptr;
+    __nv_bfloat16 *bdec2 = nullptr, *bd1a = nullptr, *bdec1 = nullptr;
+    __nv_bfloat16 *gb_dec1 = nullptr, *gb_d1a = nullptr, *gb_cat1 = nullptr, *gb_dec2 = nullptr, *gb_d2a = nullptr;
+    __nv_bfloat16 *gb_cat2 = nullptr, *gb_mid = nullptr, *gb_ma = nullptr, *gb_p2 = nullptr, *gb_e2a = nullptr;
+    __nv_bfloat16 *gb_p1 = nullptr, *gb_e1a = nullptr;
+    __nv_bfloat16 *wprep = nullptr;          // prepared BF16 weights of the layer being run
+    float *tpart = nullptr;                  // weight- and bias-gradient partial sums
 };
 
 namespace {
@@ -396,6 +412,58 @@ long long cube(int n) { return (long long)n * n * n; }
 int alloc(unet3d *net, float **p, long long count) {
     if (cudaMalloc(p, (size_t)count * sizeof(float)) != cudaSuccess) return fail(2, "cudaMalloc failed");
     net->bufs.push_back(*p);
+    return 0;
+}
+
+int alloc_b(unet3d *net, __nv_bfloat16 **p, long long count) {
+    float *q = nullptr;
+    const int e = alloc(net, &q, (count + 1) / 2);
+    *p = reinterpret_cast<__nv_bfloat16 *>(q);
+    return e;
+}
+
+#define UNET_TRY_TC(call)                                                                       \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(3, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Failure recorded by a tensor-core kernel (a wait on a barrier that ran out), read at the
+// synchronous calls.
+int tc_status(const unet3d *net) {
+    if (!net->status) return 0;
+    int st = 0;
+    UNET_TRY(cudaMemcpyAsync(&st, net->status, sizeof(int), cudaMemcpyDeviceToHost, net->stream));
+    UNET_TRY(cudaStreamSynchronize(net->stream));
+    if (st) return fail(3, "a tensor-core convolution gave up waiting on a barrier (code " + std::to_string(st) + ")");
+    return 0;
+}
+
+tcnet::CLView cv(__nv_bfloat16 *p, int ld, int off = 0) { return tcnet::CLView{p, ld, off}; }
+
+// BF16 form: y = relu(conv3(x)) of one layer (x with cin channels, padded for layer 0)
+int conv3_tc(unet3d *net, int layer, tcnet::CLView x, int cin, int n, tcnet::CLView y) {
+    const int co = net->lco[layer];
+    UNET_TRY_TC(tcnet::prep_fwd(net->stream, net->params + net->woff[layer], co, net->lci[layer], cin, net->wprep));
+    UNET_TRY_TC(tcnet::conv3(net->stream, x, cin, net->wprep, net->params + net->boff[layer], y, co, n, 1, net->status));
+    return 0;
+}
+
+// BF16 form of conv3_back: gy (layer output gradient, masked in place), x the layer input
+// (cin channels), y the layer output; gx (cin channels) when wanted.
+int conv3_back_tc(unet3d *net, int layer, tcnet::CLView x, int cin, tcnet::CLView y, tcnet::CLView gy, int n,
+                  const tcnet::CLView *gx) {
+    const int co = net->lco[layer];
+    const long long vol = cube(n);
+    cudaStream_t s = net->stream;
+    UNET_TRY_TC(tcnet::relu_back(s, gy, y, co, vol));
+    UNET_TRY_TC(tcnet::conv3_wgrad(s, x, cin, net->lci[layer], gy, co, n, net->tpart, net->grads + net->woff[layer],
+                                   net->status));
+    UNET_TRY_TC(tcnet::bias_grad(s, gy, co, vol, net->tpart, net->grads + net->boff[layer]));
+    if (gx) {
+        UNET_TRY_TC(tcnet::prep_dgrad(s, net->params + net->woff[layer], co, cin, net->wprep));
+        UNET_TRY_TC(tcnet::conv3(s, gy, co, net->wprep, nullptr, *gx, cin, n, 0, net->status));
+    }
     return 0;
 }
 
@@ -440,6 +508,76 @@ int conv3_back(unet3d *net, int layer, const float *x, const float *y, float *gy
     return 0;
 }
 
+// BF16 form: the same network with channels-last BF16 activations (views into the
+// concatenation buffers as in the FP32 form: cat1 = [up(dec2), enc1], cat2 = [up(mid), enc2]).
+int forward_tc(unet3d *net, const float *x, float *y) {
+    const int n = net->n, h = n / 2, q = n / 4;
+    const long long V = cube(n);
+    const int c0 = net->c0, c1 = net->c1, c2 = net->c2, ci0 = net->cin0;
+    cudaStream_t s = net->stream;
+    const tcnet::CLView xb = cv(net->bx, ci0), e1a = cv(net->be1a, c0), enc1 = cv(net->bcat1, c1 + c0, c1);
+    const tcnet::CLView p1 = cv(net->bp1, c0), e2a = cv(net->be2a, c1), enc2 = cv(net->bcat2, c2 + c1, c2);
+    const tcnet::CLView p2 = cv(net->bp2, c1), ma = cv(net->bma, c2), mid = cv(net->bmid, c2);
+    const tcnet::CLView cat2 = cv(net->bcat2, c2 + c1), d2a = cv(net->bd2a, c1), dec2 = cv(net->bdec2, c1);
+    const tcnet::CLView cat1 = cv(net->bcat1, c1 + c0), d1a = cv(net->bd1a, c0), dec1 = cv(net->bdec1, c0);
+    UNET_TRY_TC(tcnet::to_cl(s, x, net->n_in, V, net->bx, ci0));
+    int e;
+    if ((e = conv3_tc(net, 0, xb, ci0, n, e1a))) return e;
+    if ((e = conv3_tc(net, 1, e1a, c0, n, enc1))) return e;
+    UNET_TRY_TC(tcnet::pool(s, enc1, c0, n, p1));
+    if ((e = conv3_tc(net, 2, p1, c0, h, e2a))) return e;
+    if ((e = conv3_tc(net, 3, e2a, c1, h, enc2))) return e;
+    UNET_TRY_TC(tcnet::pool(s, enc2, c1, h, p2));
+    if ((e = conv3_tc(net, 4, p2, c1, q, ma))) return e;
+    if ((e = conv3_tc(net, 5, ma, c2, q, mid))) return e;
+    UNET_TRY_TC(tcnet::up(s, mid, c2, q, cat2));
+    if ((e = conv3_tc(net, 6, cat2, c2 + c1, h, d2a))) return e;
+    if ((e = conv3_tc(net, 7, d2a, c1, h, dec2))) return e;
+    UNET_TRY_TC(tcnet::up(s, dec2, c1, h, cat1));
+    if ((e = conv3_tc(net, 8, cat1, c1 + c0, n, d1a))) return e;
+    if ((e = conv3_tc(net, 9, d1a, c0, n, dec1))) return e;
+    UNET_TRY_TC(tcnet::conv1(s, dec1, c0, V, net->params + net->woff[10], net->params + net->boff[10], net->n_out, y));
+    return 0;
+}
+
+int backward_tc(unet3d *net, const float *gy) {
+    const int n = net->n, h = n / 2, q = n / 4;
+    const long long V = cube(n);
+    const int c0 = net->c0, c1 = net->c1, c2 = net->c2, ci0 = net->cin0;
+    cudaStream_t s = net->stream;
+    const tcnet::CLView xb = cv(net->bx, ci0), e1a = cv(net->be1a, c0), enc1 = cv(net->bcat1, c1 + c0, c1);
+    const tcnet::CLView p1 = cv(net->bp1, c0), e2a = cv(net->be2a, c1), enc2 = cv(net->bcat2, c2 + c1, c2);
+    const tcnet::CLView p2 = cv(net->bp2, c1), ma = cv(net->bma, c2), mid = cv(net->bmid, c2);
+    const tcnet::CLView cat2 = cv(net->bcat2, c2 + c1), d2a = cv(net->bd2a, c1), dec2 = cv(net->bdec2, c1);
+    const tcnet::CLView cat1 = cv(net->bcat1, c1 + c0), d1a = cv(net->bd1a, c0), dec1 = cv(net->bdec1, c0);
+    const tcnet::CLView g_dec1 = cv(net->gb_dec1, c0), g_d1a = cv(net->gb_d1a, c0), g_cat1 = cv(net->gb_cat1, c1 + c0);
+    const tcnet::CLView g_enc1 = cv(net->gb_cat1, c1 + c0, c1), g_dec2 = cv(net->gb_dec2, c1), g_d2a = cv(net->gb_d2a, c1);
+    const tcnet::CLView g_cat2 = cv(net->gb_cat2, c2 + c1), g_enc2 = cv(net->gb_cat2, c2 + c1, c2);
+    const tcnet::CLView g_mid = cv(net->gb_mid, c2), g_ma = cv(net->gb_ma, c2), g_p2 = cv(net->gb_p2, c1);
+    const tcnet::CLView g_e2a = cv(net->gb_e2a, c1), g_p1 = cv(net->gb_p1, c0), g_e1a = cv(net->gb_e1a, c0);
+    // output layer (FP32 arithmetic)
+    UNET_TRY_TC(tcnet::conv1_wgrad(s, gy, net->n_out, dec1, V, c0, net->grads + net->woff[10]));
+    k_bias_grad<<<net->n_out, 256, 0, s>>>(gy, V, net->grads + net->boff[10]);
+    UNET_TRY(cudaGetLastError());
+    UNET_TRY_TC(tcnet::conv1_dgrad(s, gy, net->n_out, V, net->params + net->woff[10], c0, g_dec1));
+    int e;
+    if ((e = conv3_back_tc(net, 9, d1a, c0, dec1, g_dec1, n, &g_d1a))) return e;
+    if ((e = conv3_back_tc(net, 8, cat1, c1 + c0, d1a, g_d1a, n, &g_cat1))) return e;
+    UNET_TRY_TC(tcnet::up_back(s, g_cat1, c1, h, g_dec2));
+    if ((e = conv3_back_tc(net, 7, d2a, c1, dec2, g_dec2, h, &g_d2a))) return e;
+    if ((e = conv3_back_tc(net, 6, cat2, c2 + c1, d2a, g_d2a, h, &g_cat2))) return e;
+    UNET_TRY_TC(tcnet::up_back(s, g_cat2, c2, q, g_mid));
+    if ((e = conv3_back_tc(net, 5, ma, c2, mid, g_mid, q, &g_ma))) return e;
+    if ((e = conv3_back_tc(net, 4, p2, c1, ma, g_ma, q, &g_p2))) return e;
+    UNET_TRY_TC(tcnet::pool_back_add(s, g_p2, c1, h, g_enc2));
+    if ((e = conv3_back_tc(net, 3, e2a, c1, enc2, g_enc2, h, &g_e2a))) return e;
+    if ((e = conv3_back_tc(net, 2, p1, c0, e2a, g_e2a, h, &g_p1))) return e;
+    UNET_TRY_TC(tcnet::pool_back_add(s, g_p1, c0, n, g_enc1));
+    if ((e = conv3_back_tc(net, 1, e1a, c0, enc1, g_enc1, n, &g_e1a))) return e;
+    if ((e = conv3_back_tc(net, 0, xb, ci0, e1a, g_e1a, n, nullptr))) return e;
+    return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -447,15 +585,35 @@ extern "C" {
 const char *unet3d_last_error(void) { return g_err.c_str(); }
 
 int unet3d_create(int n_in, int n_out, int crop, int c0, int c1, int c2, void *stream, unet3d **out) {
+    return unet3d_create_ex(n_in, n_out, crop, c0, c1, c2, UNET3D_FP32, stream, out);
+}
+
+int unet3d_create_ex(int n_in, int n_out, int crop, int c0, int c1, int c2, int arith, void *stream, unet3d **out) {
     if (!out) return fail(1, "null out");
     *out = nullptr;
     if (n_in < 1 || n_out < 1 || crop < 4 || crop % 4 || c0 < 1 || c1 < 1 || c2 < 1)
         return fail(1, "bad sizes (crop must be a positive multiple of 4)");
+    if (arith != UNET3D_FP32 && arith != UNET3D_BF16) return fail(1, "arith must be UNET3D_FP32 or UNET3D_BF16");
+    const int cin0 = (n_in + 15) / 16 * 16;
     unet3d *net = new unet3d();
+    net->arith = arith, net->cin0 = cin0;
     net->n_in = n_in, net->n_out = n_out, net->n = crop, net->c0 = c0, net->c1 = c1, net->c2 = c2;
     net->stream = static_cast<cudaStream_t>(stream);
     const int lco[11] = {c0, c0, c1, c1, c2, c2, c1, c1, c0, c0, n_out};
     const int lci[11] = {n_in, c0, c0, c1, c1, c2, c2 + c1, c1, c1 + c0, c0, c0};
+    if (arith == UNET3D_BF16) {
+        bool ok = c0 % 16 == 0 && c1 % 16 == 0 && c2 % 16 == 0;
+        for (int l = 0; l < 10 && ok; ++l) {
+            const int ci = l == 0 ? cin0 : lci[l];
+            ok = tcnet::conv_shape_ok(ci, lco[l]) && tcnet::wgrad_shape_ok(ci, lco[l]) &&
+                 (l == 0 || tcnet::conv_shape_ok(lco[l], ci));
+        }
+        if (!ok) {
+            delete net;
+            return fail(1, "the BF16 form needs channel counts that are multiples of 16 within the tensor-core "
+                           "tile limits");
+        }
+    }
     size_t off = 0, maxw = 0;
     for (int l = 0; l < 11; ++l) {
         const size_t nw = (size_t)lco[l] * lci[l] * (l < 10 ? 27 : 1);
@@ -479,6 +637,48 @@ int unet3d_create(int n_in, int n_out, int crop, int c0, int c1, int c2, void *s
     A(&net->m, (long long)off);
     A(&net->v, (long long)off);
     A(&net->x, (long long)n_in * V);
+    if (arith == UNET3D_BF16) {
+        auto B = [&](__nv_bfloat16 **p, long long count) {
+            if (!e) e = alloc_b(net, p, count);
+        };
+        B(&net->bx, (long long)cin0 * V);
+        B(&net->bcat1, (long long)(c1 + c0) * V);
+        B(&net->be1a, (long long)c0 * V);
+        B(&net->bp1, (long long)c0 * V2);
+        B(&net->bcat2, (long long)(c2 + c1) * V2);
+        B(&net->be2a, (long long)c1 * V2);
+        B(&net->bp2, (long long)c1 * V4);
+        B(&net->bma, (long long)c2 * V4);
+        B(&net->bmid, (long long)c2 * V4);
+        B(&net->bd2a, (long long)c1 * V2);
+        B(&net->bdec2, (long long)c1 * V2);
+        B(&net->bd1a, (long long)c0 * V);
+        B(&net->bdec1, (long long)c0 * V);
+        B(&net->gb_dec1, (long long)c0 * V);
+        B(&net->gb_d1a, (long long)c0 * V);
+        B(&net->gb_cat1, (long long)(c1 + c0) * V);
+        B(&net->gb_dec2, (long long)c1 * V2);
+        B(&net->gb_d2a, (long long)c1 * V2);
+        B(&net->gb_cat2, (long long)(c2 + c1) * V2);
+        B(&net->gb_mid, (long long)c2 * V4);
+        B(&net->gb_ma, (long long)c2 * V4);
+        B(&net->gb_p2, (long long)c1 * V4);
+        B(&net->gb_e2a, (long long)c1 * V2);
+        B(&net->gb_p1, (long long)c0 * V2);
+        B(&net->gb_e1a, (long long)c0 * V);
+        size_t wmax = 0, pmax = 0;
+        const int side[10] = {crop, crop, crop / 2, crop / 2, crop / 4, crop / 4, crop / 2, crop / 2, crop, crop};
+        for (int l = 0; l < 10; ++l) {
+            const int ci = l == 0 ? cin0 : lci[l];
+            wmax = std::max(wmax, tcnet::prep_elems(ci, lco[l]));
+            pmax = std::max(pmax, tcnet::wgrad_part_floats(side[l], ci, lco[l]));
+            pmax = std::max(pmax, tcnet::bias_part_floats(lco[l]));
+        }
+        B(&net->wprep, (long long)wmax);
+        A(&net->tpart, (long long)pmax);
+        if (!e && cudaMalloc(&net->status, sizeof(int)) != cudaSuccess) e = fail(2, "cudaMalloc failed");
+        if (!e && cudaMemset(net->status, 0, sizeof(int)) != cudaSuccess) e = fail(3, "cudaMemset failed");
+    } else {
     A(&net->cat1, (long long)(c1 + c0) * V);
     A(&net->e1a, (long long)c0 * V);
     A(&net->p1, (long long)c0 * V2);
@@ -507,6 +707,7 @@ int unet3d_create(int n_in, int n_out, int crop, int c0, int c1, int c2, void *s
     A(&net->wt, (long long)maxw);
     net->part_floats = (size_t)600 * maxw;
     A(&net->part, (long long)net->part_floats);
+    }
     if (!e && cudaMalloc(&net->mse_part, kMseBlocks * sizeof(double)) != cudaSuccess) e = fail(2, "cudaMalloc failed");
     if (!e && cudaMallocHost(&net->mse_host, kMseBlocks * sizeof(double)) != cudaSuccess) e = fail(2, "cudaMallocHost failed");
     if (!e && (cudaMemset(net->m, 0, off * sizeof(float)) != cudaSuccess ||
@@ -541,7 +742,7 @@ int unet3d_get_grads(const unet3d *net, float *host) {
     if (!net || !host) return fail(1, "null argument");
     UNET_TRY(cudaMemcpyAsync(host, net->grads, net->nparam * sizeof(float), cudaMemcpyDeviceToHost, net->stream));
     UNET_TRY(cudaStreamSynchronize(net->stream));
-    return 0;
+    return tc_status(net);
 }
 
 int unet3d_forward(unet3d *net, const float *x, float *y) {
@@ -552,6 +753,12 @@ int unet3d_forward(unet3d *net, const float *x, float *y) {
     const int c0 = net->c0, c1 = net->c1, c2 = net->c2;
     cudaStream_t s = net->stream;
     UNET_TRY(cudaMemcpyAsync(net->x, x, (size_t)net->n_in * V * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (net->arith == UNET3D_BF16) {
+        const int e = forward_tc(net, net->x, y);
+        if (e) return e;
+        net->have_forward = true;
+        return 0;
+    }
     float *enc1 = net->cat1 + (long long)c1 * V, *enc2 = net->cat2 + (long long)c2 * V2;
     int e;
     if ((e = conv3(net, 0, net->x, n, net->e1a, 1))) return e;
@@ -578,6 +785,7 @@ int unet3d_forward(unet3d *net, const float *x, float *y) {
 int unet3d_backward(unet3d *net, const float *gy) {
     if (!net || !gy) return fail(1, "null argument");
     if (!net->have_forward) return fail(4, "backward before a successful forward");
+    if (net->arith == UNET3D_BF16) return backward_tc(net, gy);
     const int n = net->n, h = n / 2, q = n / 4;
     const long long V = cube(n), V2 = cube(h), V4 = cube(q);
     const int c0 = net->c0, c1 = net->c1, c2 = net->c2;
@@ -621,6 +829,7 @@ int unet3d_mse(unet3d *net, const float *y, const float *target, size_t count, d
     UNET_TRY(cudaMemcpyAsync(net->mse_host, net->mse_part, kMseBlocks * sizeof(double), cudaMemcpyDeviceToHost,
                              net->stream));
     UNET_TRY(cudaStreamSynchronize(net->stream));
+    if (int e = tc_status(net)) return e;
     double s = 0.0;
     for (int i = 0; i < kMseBlocks; ++i) s += net->mse_host[i];
     if (loss) *loss = s / (double)count;
@@ -637,12 +846,59 @@ int unet3d_adam(unet3d *net, float lr, float beta1, float beta2, float eps, int 
     return 0;
 }
 
+int unet3d_conv3_bf16(int mode, int n, int cin, int cout, const void *in, const void *in2, const float *w,
+                      const float *b, int relu, void *out, void *stream) {
+    if (mode < 0 || mode > 2 || n < 1 || !in || !w || !out || (mode == 2 && !in2)) return fail(1, "bad argument");
+    const bool ok = mode == 0 ? tcnet::conv_shape_ok(cin, cout)
+                    : mode == 1 ? tcnet::conv_shape_ok(cout, cin)
+                                : tcnet::wgrad_shape_ok(cin, cout);
+    if (!ok) return fail(1, "channel counts outside the tensor-core tile limits");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    __nv_bfloat16 *wp = nullptr;
+    float *part = nullptr;
+    int *status = nullptr;
+    int rc = 0;
+    auto run = [&]() -> int {
+        UNET_TRY(cudaMalloc(&status, sizeof(int)));
+        UNET_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+        __nv_bfloat16 *src = const_cast<__nv_bfloat16 *>(static_cast<const __nv_bfloat16 *>(in));
+        if (mode == 0 || mode == 1) {
+            UNET_TRY(cudaMalloc(&wp, tcnet::prep_elems(cin, cout) * sizeof(__nv_bfloat16)));
+            if (mode == 0) {
+                UNET_TRY(tcnet::prep_fwd(s, w, cout, cin, cin, wp));
+                UNET_TRY(tcnet::conv3(s, cv(src, cin), cin, wp, b, cv(static_cast<__nv_bfloat16 *>(out), cout), cout, n,
+                                      relu, status));
+            } else {
+                UNET_TRY(tcnet::prep_dgrad(s, w, cout, cin, wp));
+                UNET_TRY(tcnet::conv3(s, cv(src, cout), cout, wp, nullptr, cv(static_cast<__nv_bfloat16 *>(out), cin), cin,
+                                      n, 0, status));
+            }
+        } else {
+            UNET_TRY(cudaMalloc(&part, tcnet::wgrad_part_floats(n, cin, cout) * sizeof(float)));
+            __nv_bfloat16 *g = const_cast<__nv_bfloat16 *>(static_cast<const __nv_bfloat16 *>(in2));
+            UNET_TRY(tcnet::conv3_wgrad(s, cv(src, cin), cin, cin, cv(g, cout), cout, n, part, static_cast<float *>(out),
+                                        status));
+        }
+        int st = 0;
+        UNET_TRY(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        UNET_TRY(cudaStreamSynchronize(s));
+        if (st) return fail(3, "a tensor-core convolution gave up waiting on a barrier (code " + std::to_string(st) + ")");
+        return 0;
+    };
+    rc = run();
+    if (wp) cudaFree(wp);
+    if (part) cudaFree(part);
+    if (status) cudaFree(status);
+    return rc;
+}
+
 void unet3d_destroy(unet3d *net) {
     if (!net) return;
     if (net->stream) cudaStreamSynchronize(net->stream);
     for (float *p : net->bufs) cudaFree(p);
     if (net->mse_part) cudaFree(net->mse_part);
     if (net->mse_host) cudaFreeHost(net->mse_host);
+    if (net->status) cudaFree(net->status);
     delete net;
 }
 

@@ -83,3 +83,32 @@ def test_unet_backward_finite_differences(k):
     lm = unet.mse(unet.forward(params, x)[0], target)[0]
     bb[0] = old
     assert abs((lp - lm) / (2 * h) - grads[k][1][0]) <= 1e-6 * max(1.0, abs((lp - lm) / (2 * h)))
+
+
+def test_bf16_round_is_round_to_nearest_even():
+    """bf16_round against exact cases of the definition (8 significand bits, ties to even)
+    and against torch's float32 -> bfloat16 conversion on values over 17 decades."""
+    from oracle.unet import bf16_round
+    one = 1.0
+    cases = {one: one, one + 2.0 ** -8: one, one + 3 * 2.0 ** -8: one + 2.0 ** -6,
+             one + 2.0 ** -8 + 2.0 ** -20: one + 2.0 ** -7, -3.0: -3.0, 2.0 ** -130: 2.0 ** -130}
+    for a, b in cases.items():
+        assert bf16_round(np.array([a]))[0] == b, (a, b)
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal(20000) * np.exp(rng.uniform(-20, 20, 20000))
+    ref = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(bf16_round(a), ref)
+
+
+def test_bf16_storage_form_without_rounding_is_the_network():
+    """store = identity reproduces the plain forward and backward exactly."""
+    from oracle import unet as ou
+    params = ou.init_params(2, 2, seed=1, channels=(2, 3, 4))
+    x = np.random.default_rng(2).standard_normal((2, 4, 4, 4))
+    y0, c0 = ou.forward(params, x)
+    y1, c1 = ou.forward(params, x, store=lambda a: a)
+    assert np.array_equal(y0, y1)
+    g0 = ou.backward(params, c0, y0)
+    g1 = ou.backward(params, c1, y1, store=lambda a: a)
+    assert all(np.array_equal(a, b) for p, q in zip(g0, g1) for a, b in zip(p, q))
