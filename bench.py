@@ -674,17 +674,19 @@ def learned_guess_measure(n_seeds=8, tol=1e-6):
     W = np.load(wpath)
     crop = int(W["crop"])
     solv = guess._solvent()
-    net = capi.UNet3D(5, 5, crop, tuple(int(c) for c in W["channels"]))
+    arith = str(W["arith"]) if "arith" in W else "bf16"
+    net = capi.UNet3D(5, 5, crop, tuple(int(c) for c in W["channels"]), arith=arith)
     try:
         net.set_params(W["params"])
         with capi.Solver(solv, synth.cubic_grid(128, 0.5), precision=32, mdiis_nvec=5) as S:
             seeds = [guess.TEST_SEED0 + i for i in range(n_seeds)]
-            guess.evaluate(S, net, seeds[:1], tol=tol)                  # warm-up
-            ev = guess.evaluate(S, net, seeds, tol=tol)
+            guess.evaluate(S, net, seeds[:1], tol=tol, crop=crop)       # warm-up
+            ev = guess.evaluate(S, net, seeds, tol=tol, crop=crop)
     finally:
         net.close()
     zi, gi = np.array(ev["zero_iters"]), np.array(ev["guess_iters"])
-    return dict(seeds="%d held-out solutes, seeds %d-%d" % (n_seeds, seeds[0], seeds[-1]),
+    return dict(seeds="%d held-out solutes, seeds %d-%d" % (n_seeds, seeds[0], seeds[-1]), crop=crop,
+                network="%s form" % arith,
                 zero_guess=dict(iterations_mean=float(zi.mean()), solves_per_s=len(zi) / float(np.sum(ev["zero_s"]))),
                 learned_guess=dict(iterations_mean=float(gi.mean()), solves_per_s=len(gi) / float(np.sum(ev["guess_s"]))),
                 fewer_iterations=int(np.sum(gi < zi)), more_iterations=int(np.sum(gi > zi)),

@@ -78,6 +78,16 @@ int unet3d_get_grads(const unet3d *net, float *host_grads);
  * FP64 sum in a fixed order) and gy = 2 (y - target) / count on the device. */
 int unet3d_mse(unet3d *net, const float *y, const float *target, size_t count, double *loss, float *gy);
 
+/* Weighted mean squared error of y [n_out][crop^3] against target at the last forward's
+ * input x: weight core_weight (> 0) where the first input channel x[0][p] >= core_x, else 1;
+ * loss = sum w (y - target)^2 / sum w to host (synchronous, FP64 sums in a fixed order) and
+ * gy = 2 w (y - target) / sum w on the device. For the learned guess the first input channel
+ * is tanh(beta u / 4) of the first solvent site, so core_x near 1 selects the solute core,
+ * where the target iterate is large and the solve settles it within a few iterations.
+ * Returns 4 when no forward pass has completed. */
+int unet3d_mse_core(unet3d *net, const float *y, const float *target, float core_x, float core_weight,
+                    double *loss, float *gy);
+
 /* One Adam step on the parameters with the current gradient: step t >= 1, moments with
  * decay beta1, beta2, bias-corrected; p -= lr m^ / (sqrt(v^) + eps). */
 int unet3d_adam(unet3d *net, float lr, float beta1, float beta2, float eps, int t);

@@ -110,6 +110,8 @@ def load():
         "unet3d_backward": (c_int, [c_void_p, c_void_p]),
         "unet3d_get_grads": (c_int, [c_void_p, P(ctypes.c_float)]),
         "unet3d_mse": (c_int, [c_void_p, c_void_p, c_void_p, c_size_t, P(c_double), c_void_p]),
+        "unet3d_mse_core": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.c_float, ctypes.c_float, P(c_double),
+                                    c_void_p]),
         "unet3d_adam": (c_int, [c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, c_int]),
         "unet3d_last_error": (ctypes.c_char_p, []),
         "unet3d_destroy": (None, [c_void_p]),
@@ -595,6 +597,15 @@ class UNet3D:
         pg = _f32_cuda(gy, n, "gy")
         loss = ctypes.c_double()
         self._ok(self.lib.unet3d_mse(self.net, py, pt, n, ctypes.byref(loss), pg))
+        return loss.value
+
+    def mse_core(self, y, target, gy, core_x, core_weight):
+        """Weighted squared error (unet3d_mse_core): weight core_weight where the last
+        input's first channel is at least core_x."""
+        n = self.n_out * self.crop ** 3
+        loss = ctypes.c_double()
+        self._ok(self.lib.unet3d_mse_core(self.net, _f32_cuda(y, n, "y"), _f32_cuda(target, n, "target"),
+                                          float(core_x), float(core_weight), ctypes.byref(loss), _f32_cuda(gy, n, "gy")))
         return loss.value
 
     def adam(self, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -351,6 +351,40 @@ __global__ void k_mse(const float *y, const float *t, long long n, float scale, 
     }
 }
 
+// Weighted squared error: weight cw where the first input channel x0[p] >= cx (p = i % vol),
+// else 1. part[block] = (sum w d^2, sum w) in FP64; gy written by k_wmse_grad.
+__global__ void k_wmse_part(const float *y, const float *t, const float *x0, long long vol, long long n, float cx,
+                            float cw, double *part) {
+    __shared__ double red[2][8];
+    double s = 0.0, sw = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float d = y[i] - t[i];
+        const double w = x0[i % vol] >= cx ? (double)cw : 1.0;
+        s += w * (double)d * (double)d;
+        sw += w;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    }
+    if ((threadIdx.x & 31) == 0) red[0][threadIdx.x >> 5] = s, red[1][threadIdx.x >> 5] = sw;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += red[0][i], b += red[1][i];
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void k_wmse_grad(const float *y, const float *t, const float *x0, long long vol, long long n, float cx,
+                            float cw, float scale, float *gy) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float w = x0[i % vol] >= cx ? cw : 1.f;
+        gy[i] = scale * w * (y[i] - t[i]);
+    }
+}
+
 __global__ void k_adam(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
                        float eps, float bc1, float bc2) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -392,6 +426,7 @@ struct unet3d {
     float *wt = nullptr, *part = nullptr;
     size_t part_floats = 0;
     double *mse_part = nullptr, *mse_host = nullptr;
+    double *mse_blocks2 = nullptr, *mse_host2 = nullptr;   // weighted loss: (sum w d^2, sum w) per block
     // BF16 form (arith = UNET3D_BF16): channels-last BF16 activations and their gradients
     int arith = UNET3D_FP32, cin0 = 0;       // cin0: input channels padded to a multiple of 16
     int *status = nullptr;                   // first failure reported by a tensor-core kernel
@@ -836,6 +871,30 @@ int unet3d_mse(unet3d *net, const float *y, const float *target, size_t count, d
     return 0;
 }
 
+int unet3d_mse_core(unet3d *net, const float *y, const float *target, float core_x, float core_weight,
+                    double *loss, float *gy) {
+    if (!net || !y || !target || !gy || !(core_weight > 0.f)) return fail(1, "bad argument");
+    if (!net->have_forward) return fail(4, "loss before a successful forward");
+    const long long vol = cube(net->n), count = (long long)net->n_out * vol;
+    if (net->mse_blocks2 == nullptr) {
+        UNET_TRY(cudaMalloc(&net->mse_blocks2, 2 * kMseBlocks * sizeof(double)));
+        UNET_TRY(cudaMallocHost(&net->mse_host2, 2 * kMseBlocks * sizeof(double)));
+    }
+    k_wmse_part<<<kMseBlocks, 256, 0, net->stream>>>(y, target, net->x, vol, count, core_x, core_weight, net->mse_blocks2);
+    UNET_TRY(cudaGetLastError());
+    UNET_TRY(cudaMemcpyAsync(net->mse_host2, net->mse_blocks2, 2 * kMseBlocks * sizeof(double), cudaMemcpyDeviceToHost,
+                             net->stream));
+    UNET_TRY(cudaStreamSynchronize(net->stream));
+    if (int e = tc_status(net)) return e;
+    double s = 0.0, sw = 0.0;
+    for (int i = 0; i < kMseBlocks; ++i) s += net->mse_host2[2 * i], sw += net->mse_host2[2 * i + 1];
+    if (loss) *loss = s / sw;
+    k_wmse_grad<<<grid_for(count), 256, 0, net->stream>>>(y, target, net->x, vol, count, core_x, core_weight,
+                                                         (float)(2.0 / sw), gy);
+    UNET_TRY(cudaGetLastError());
+    return 0;
+}
+
 int unet3d_adam(unet3d *net, float lr, float beta1, float beta2, float eps, int t) {
     if (!net || t < 1) return fail(1, "bad argument");
     const float bc1 = 1.f - powf(beta1, (float)t), bc2 = 1.f - powf(beta2, (float)t);
@@ -899,6 +958,8 @@ void unet3d_destroy(unet3d *net) {
     if (net->mse_part) cudaFree(net->mse_part);
     if (net->mse_host) cudaFreeHost(net->mse_host);
     if (net->status) cudaFree(net->status);
+    if (net->mse_blocks2) cudaFree(net->mse_blocks2);
+    if (net->mse_host2) cudaFreeHost(net->mse_host2);
     delete net;
 }
 
