@@ -594,8 +594,10 @@ def run_profile_case(args):
 def batch_measure(precision, tol, inflight, steps, warmup, with_clocks=False):
     """The batch64 form: 64 seeded solutes (20-120 atoms) on uneven cubic grids (64-128, sizes
     with factors 2, 3, 5 only) in 3-site water, KH, MDIIS 5. A step is the whole batch: every
-    job's set_solute + solve + SFE, once one at a time and once through rism3d_solve_batch.
-    Contexts are created (one per grid) and their pencil tiles tuned before timing."""
+    job's set_solute + solve + SFE, once one at a time, once through rism3d_solve_batch (host
+    scheduler, ``inflight`` jobs at a time) and once through rism3d_solve_batch_graph (all jobs
+    as device loops in one graph launch). Contexts are created (one per grid) and their pencil
+    tiles tuned before timing."""
     import numpy as np
     import torch
 
@@ -625,10 +627,10 @@ def batch_measure(precision, tol, inflight, steps, warmup, with_clocks=False):
         site_points = [len(sites["q"]) * float(np.prod(w["grid"]["n"])) for w in work]
         spi = []
 
-        def batched():
+        def batched(one_graph=False):
             jobs = [dict(solver=S, solute=w["solute"], closure="kh", tol=tol, sfe="kh")
                     for S, w in zip(solvers, work)]
-            res = capi.solve_batch(jobs, max_inflight=inflight)
+            res = capi.solve_batch(jobs, max_inflight=inflight, one_graph=one_graph)
             bad = [r for r in res if r["status"] != "OK"]
             if bad:
                 raise RuntimeError("batch job failed: %s" % bad[0])
@@ -649,12 +651,14 @@ def batch_measure(precision, tol, inflight, steps, warmup, with_clocks=False):
         if clocks:
             clocks.start()
         t_bat, it_bat = timed(batched)
+        t_graph, it_graph = timed(lambda: batched(one_graph=True))
         clk = clocks.stop() if clocks else None
     finally:
         for S in solvers:
             S.close()
     n = len(work) * steps
     return dict(batched=n / t_bat, one_at_a_time=n / t_seq, speedup=t_seq / t_bat, unit="solves/s",
+                one_graph=n / t_graph, one_graph_speedup=t_seq / t_graph, one_graph_iterations=it_graph,
                 jobs=len(work), steps=steps, warmup=warmup, inflight=inflight, tol=tol,
                 batched_iterations=it_bat, one_at_a_time_iterations=it_seq, t_batched_s=t_bat,
                 site_gridpoint_iters_per_s=sum(spi[-steps:]) / t_bat,
@@ -710,6 +714,8 @@ def run_batch(args):
                             sites=3, atoms="20-120", closure="kh", tol=args.tol, mdiis=5,
                             inflight=args.inflight, parallelism="single", pencil_widths=m["pencil_widths"]),
                 one_at_a_time=dict(value=m["one_at_a_time"], unit="solves/s", iterations=m["one_at_a_time_iterations"]),
+                one_graph=dict(value=m["one_graph"], unit="solves/s", iterations=m["one_graph_iterations"],
+                               what="rism3d_solve_batch_graph: every job a device loop, one graph launch"),
                 batched_iterations=m["batched_iterations"],
                 site_gridpoint_iters_per_s=m["site_gridpoint_iters_per_s"], clocks=m["clocks"])
     print(json.dumps(line), flush=True)

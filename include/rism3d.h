@@ -274,6 +274,19 @@ typedef struct {
 rism3d_status rism3d_solve_batch(rism3d_batch_job *jobs, int n_jobs, int max_inflight,
                                  double time_limit_s);
 
+/* The same jobs as rism3d_solve_batch as ONE launch of one CUDA graph (no counterpart in the
+ * paper; the batched form for many solutes on uneven grids): each job is a device-side loop
+ * (a conditional while node) whose body runs the job's check_every iterations and a loop
+ * test that keeps the loop going while the job's device control block says "running", so
+ * no host round trip happens between iterations and the jobs' loops run side by side on the
+ * GPU. Set-up (solute, control block, capture of every job's loop) runs on the host before
+ * the launch; the call returns when the graph has finished. time_limit_s > 0 bounds each
+ * job on the device: the loop test compares the GPU's global timer with the job's deadline
+ * (set by its first loop test) and stops the job, which reports RISM3D_ETIMEOUT with its
+ * last iterate readable; 0 means no limit. Results are those of rism3d_solve (the same
+ * kernels in the same order). Status as rism3d_solve_batch. */
+rism3d_status rism3d_solve_batch_graph(rism3d_batch_job *jobs, int n_jobs, double time_limit_s);
+
 /* Partial molar volume of Eq. 19, V = k_B T chi_T (1 - sum_g rho_g int c_g(r) dr), in A^3 per
  * molecule, from the current iterate; kT_chi_T (A^3) is the solvent's k_B T times its
  * isothermal compressibility (rism1d_xrism_ex reports it). c_integral ([n_sites], host) may

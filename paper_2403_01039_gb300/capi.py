@@ -95,6 +95,7 @@ def load():
         "rism3d_get": (c_int, [c_void_p, c_int, c_void_p, c_size_t, c_int]),
         "rism3d_get_sfe": (c_int, [c_void_p, c_int, c_int, P(c_double), _dp]),
         "rism3d_solve_batch": (c_int, [P(BatchJob), c_int, c_int, c_double]),
+        "rism3d_solve_batch_graph": (c_int, [P(BatchJob), c_int, c_double]),
         "rism3d_tune": (c_int, [c_void_p, P(c_int), P(c_double)]),
         "rism3d_guess_input": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
         "rism3d_guess_target": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
@@ -298,11 +299,12 @@ def xrism(sites, n_r=2048, dr=0.05, closure="kh", tol=1e-10, charge_steps=10, th
     return chi, dk.value, its.value, rms.value
 
 
-def solve_batch(jobs, max_inflight=8, time_limit=0.0):
-    """Solve independent problems concurrently (``rism3d_solve_batch``). jobs: list of dicts
-    with keys solver (a Solver of its own), solute (dict xyz/q/sigma/eps, or None to keep the
-    solver's current solute), closure ("kh"), pse_order (3), tol (1e-6), sfe (None or an SFE
-    kind). Returns a list of dicts (status name, iterations, converged, rms, sfe)."""
+def solve_batch(jobs, max_inflight=8, time_limit=0.0, one_graph=False):
+    """Solve independent problems concurrently (``rism3d_solve_batch``, or with one_graph
+    ``rism3d_solve_batch_graph``: all jobs as device loops in one graph launch). jobs: list
+    of dicts with keys solver (a Solver of its own), solute (dict xyz/q/sigma/eps, or None to
+    keep the solver's current solute), closure ("kh"), pse_order (3), tol (1e-6), sfe (None or
+    an SFE kind). Returns a list of dicts (status name, iterations, converged, rms, sfe)."""
     lib = load()
     arr = (BatchJob * len(jobs))()
     keep = []
@@ -321,7 +323,10 @@ def solve_batch(jobs, max_inflight=8, time_limit=0.0):
         J.pse_order = int(d.get("pse_order", 3))
         J.tol = float(d.get("tol", 1e-6))
         J.sfe_kind = SFE_KINDS[d["sfe"]] if d.get("sfe") else 0
-    lib.rism3d_solve_batch(arr, len(jobs), int(max_inflight), float(time_limit))
+    if one_graph:
+        lib.rism3d_solve_batch_graph(arr, len(jobs), float(time_limit))
+    else:
+        lib.rism3d_solve_batch(arr, len(jobs), int(max_inflight), float(time_limit))
     out = []
     for J in arr:
         name = STATUS_NAMES[J.status] if 0 <= J.status < len(STATUS_NAMES) else str(J.status)

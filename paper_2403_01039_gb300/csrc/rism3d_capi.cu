@@ -1182,6 +1182,137 @@ rism3d_status rism3d_solve_batch(rism3d_batch_job *jobs, int n_jobs, int max_inf
     return RISM3D_OK;
 }
 
+// ------------------------------------------------------------------ batch as one graph launch
+// Loop test at the end of one body pass of a job's device loop: the first pass sets the
+// deadline (%globaltimer + limit_ns; limit_ns = 0: none); a running solve past its deadline
+// is marked stopped; the loop goes on while the solve runs.
+static __global__ void k_loop_ctl(Ctrl *c, cudaGraphConditionalHandle h, unsigned long long limit_ns) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    if (limit_ns && c->deadline == 0ULL) c->deadline = now + limit_ns;
+    if (c->status == kRunning && c->deadline != 0ULL && now > c->deadline) c->status = kStopped;
+    cudaGraphSetConditional(h, c->status == kRunning ? 1u : 0u);
+}
+
+// Adds to g one conditional while node whose body is check_every iterations of ctx followed
+// by the loop test (captured on the context's own streams).
+static rism3d_status add_device_loop(rism3d_ctx *ctx, cudaGraph_t g, unsigned long long limit_ns) {
+    cudaGraphConditionalHandle h;
+    CUDA_TRY(ctx, cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CUDA_TRY(ctx, cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if (rism3d_status st0 = ensure_side(ctx)) return st0;
+    CUDA_TRY(ctx, cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    rism3d_status st = RISM3D_OK;
+    for (int i = 0; i < ctx->opt.check_every && st == RISM3D_OK; ++i)
+        st = ctx->fp32() ? run_iteration<float>(ctx, ctx->f32, true, nullptr)
+                         : run_iteration<double>(ctx, ctx->f64, true, nullptr);
+    if (st == RISM3D_OK) {
+        k_loop_ctl<<<1, 32, 0, ctx->stream>>>(ctx->ctrl, h, limit_ns);
+        if (cudaGetLastError() != cudaSuccess) st = fail(ctx, RISM3D_ECUDA, "loop test launch");
+    }
+    cudaGraph_t out = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &out);
+    if (st != RISM3D_OK) return st;
+    if (e != cudaSuccess) return fail(ctx, RISM3D_ECUDA, "device loop capture: %s", cudaGetErrorString(e));
+    return RISM3D_OK;
+}
+
+rism3d_status rism3d_solve_batch_graph(rism3d_batch_job *jobs, int n_jobs, double time_limit_s) {
+    if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(nullptr, RISM3D_EINVAL, "bad job list");
+    if (!(time_limit_s >= 0.0)) return fail(nullptr, RISM3D_EINVAL, "time_limit_s must be >= 0");
+    for (int j = 0; j < n_jobs; ++j) {
+        jobs[j].status = RISM3D_ESTATE;
+        jobs[j].sfe = 0.0;
+        jobs[j].report = rism3d_report{};
+    }
+    int device = -1;
+    for (int j = 0; j < n_jobs; ++j) {
+        rism3d_ctx *c = jobs[j].ctx;
+        if (!c) return fail(nullptr, RISM3D_EINVAL, "job %d has no context", j);
+        if (device < 0) device = c->device;
+        if (c->device != device) return fail(nullptr, RISM3D_EINVAL, "jobs span more than one device");
+        for (int i = 0; i < j; ++i)
+            if (jobs[i].ctx == c) return fail(nullptr, RISM3D_EINVAL, "jobs %d and %d share a context", i, j);
+    }
+    if (n_jobs == 0) return RISM3D_OK;
+    DeviceGuard dg(device);
+    const unsigned long long limit_ns =
+        time_limit_s > 0.0 ? (unsigned long long)std::max(1.0, time_limit_s * 1e9) : 0ULL;
+    std::vector<char> live(n_jobs, 0);
+    cudaStream_t ls = nullptr;
+    cudaEvent_t done = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    rism3d_status rc = RISM3D_OK;
+    auto cleanup = [&]() {
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+        if (done) cudaEventDestroy(done);
+        if (ls) cudaStreamDestroy(ls);
+    };
+    if (cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess || cudaGraphCreate(&g, 0) != cudaSuccess) {
+        cleanup();
+        return fail(nullptr, RISM3D_ECUDA, "batch graph: stream, event or graph creation failed");
+    }
+    // per job: solute, control block, and its device loop in the graph
+    for (int j = 0; j < n_jobs; ++j) {
+        rism3d_batch_job &J = jobs[j];
+        rism3d_status st = RISM3D_OK;
+        if (J.n_atoms > 0) st = rism3d_set_solute(J.ctx, J.n_atoms, J.xyz, J.q, J.sigma, J.eps);
+        if (st == RISM3D_OK) st = solve_begin(J.ctx, J.closure, J.pse_order, J.tol);
+        if (st == RISM3D_OK) st = add_device_loop(J.ctx, g, limit_ns);
+        if (st == RISM3D_OK && (cudaEventRecord(J.ctx->chunk_ev, J.ctx->stream) != cudaSuccess ||
+                                cudaStreamWaitEvent(ls, J.ctx->chunk_ev, 0) != cudaSuccess))
+            st = fail(J.ctx, RISM3D_ECUDA, "batch graph: ordering after the job's set-up");
+        if (st != RISM3D_OK) {
+            J.status = st;
+            cleanup();
+            return st;
+        }
+        live[j] = 1;
+    }
+    cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, ls);
+    if (e == cudaSuccess) e = cudaEventRecord(done, ls);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(nullptr, RISM3D_ECUDA, "batch graph: %s", cudaGetErrorString(e));
+    }
+    for (int j = 0; j < n_jobs; ++j) {
+        rism3d_batch_job &J = jobs[j];
+        rism3d_status st = RISM3D_OK;
+        if (cudaStreamWaitEvent(J.ctx->stream, done, 0) != cudaSuccess)
+            st = fail(J.ctx, RISM3D_ECUDA, "batch graph: ordering before the read-back");
+        if (st == RISM3D_OK) st = solve_finish(J.ctx, &J.report, false);
+        if (st == RISM3D_OK || st == RISM3D_ETIMEOUT || st == RISM3D_ENOTCONV) {
+            // launches: every body pass runs check_every iterations' kernels
+            int slots[kMaxLaunches];
+            const int nk = iteration_slots(J.ctx, true, slots);
+            const int K = J.ctx->opt.check_every;
+            const long long passes = std::max(1, (J.report.iterations + K - 1) / K);
+            for (int k = 0; k < nk; ++k) J.ctx->stats.launches[slots[k]] += passes * K;
+        }
+        if (J.sfe_kind && (st == RISM3D_OK || st == RISM3D_ENOTCONV)) {
+            const rism3d_status s2 = rism3d_get_sfe(J.ctx, J.sfe_kind, J.pse_order, &J.sfe, nullptr);
+            if (st == RISM3D_OK) st = s2;
+        }
+        J.status = st;
+        if (st != RISM3D_OK && rc == RISM3D_OK) rc = st;
+    }
+    cudaEventSynchronize(done);
+    cleanup();
+    return rc;
+}
+
 rism3d_status rism3d_residual(rism3d_ctx *ctx, int closure, int pse_order, const double *t, double *R,
                               int on_device) {
     if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");

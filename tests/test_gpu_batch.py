@@ -1,6 +1,7 @@
-"""The batched form (rism3d_solve_batch): independent solutes on uneven grids solved
-concurrently must give exactly what one-at-a-time solves give, match the FP64 oracle on
-every distinct grid, honour the time limit and reject job lists it cannot schedule."""
+"""The batched form (rism3d_solve_batch with its host scheduler, rism3d_solve_batch_graph as
+one graph launch of device loops): independent solutes on uneven grids solved concurrently
+must give exactly what one-at-a-time solves give, match the FP64 oracle on every distinct
+grid, honour the time limit and reject job lists it cannot schedule."""
 import numpy as np
 import pytest
 
@@ -31,8 +32,8 @@ def _solute(k, n_atoms):
     return synth.random_solute(n_atoms, 10.0 * (n_atoms / 50.0) ** (1.0 / 3.0) * 0.5, 4100 + k)
 
 
-@pytest.mark.parametrize("precision", [64, 32])
-def test_batch_equals_sequential(water3, precision):
+@pytest.mark.parametrize("precision,one_graph", [(64, False), (32, False), (64, True), (32, True)])
+def test_batch_equals_sequential(water3, precision, one_graph):
     tol = 1e-6
     seq = []
     for k, (grid, n_atoms, slab) in enumerate(JOBS):
@@ -46,7 +47,7 @@ def test_batch_equals_sequential(water3, precision):
     try:
         jobs = [dict(solver=S, solute=_solute(k, JOBS[k][1]), closure="kh", tol=tol, sfe="kh")
                 for k, S in enumerate(solvers)]
-        res = capi.solve_batch(jobs, max_inflight=3)
+        res = capi.solve_batch(jobs, max_inflight=3, one_graph=one_graph)
         for k, (r, S) in enumerate(zip(res, solvers)):
             rep, sfe, g = seq[k]
             assert r["status"] == "OK" and r["converged"], r
@@ -56,6 +57,25 @@ def test_batch_equals_sequential(water3, precision):
     finally:
         for S in solvers:
             S.close()
+
+
+def test_batch_graph_device_deadline(water3):
+    """One graph launch: each job's loop test stops the job on the device once the GPU's
+    global timer passes the job's deadline (set by its first loop test); the jobs report
+    ETIMEOUT after two body passes of check_every iterations, and the contexts stay usable."""
+    grid, n_atoms, _ = JOBS[0]
+    sol = _solute(0, n_atoms)
+    with capi.Solver(water3, grid, precision=64) as A, capi.Solver(water3, grid, precision=32) as B:
+        jobs = [dict(solver=S, solute=sol, closure="kh", tol=1e-10) for S in (A, B)]
+        res = capi.solve_batch(jobs, time_limit=1e-9, one_graph=True)
+        for r in res:
+            assert r["status"] == "ETIMEOUT" and not r["converged"] and r["iterations"] == 16, r
+        assert np.all(np.isfinite(A.get("g")))
+        rep = A.solve("kh", tol=1e-6)
+        assert rep["converged"]
+        res = capi.solve_batch([dict(solver=S, solute=sol, closure="kh", tol=1e-6) for S in (A, B)], time_limit=60.0,
+                               one_graph=True)
+        assert all(r["status"] == "OK" and r["converged"] for r in res), res
 
 
 def test_batch_time_limit_and_reuse(water3):
@@ -95,8 +115,8 @@ def test_batch_shared_stream_and_rejected_context(water3):
             A.solve("kh")                                          # no solute was set
 
 
-@pytest.mark.parametrize("precision", [64, 32])
-def test_batch_matches_oracle(water3, precision):
+@pytest.mark.parametrize("precision,one_graph", [(64, False), (32, False), (32, True)])
+def test_batch_matches_oracle(water3, precision, one_graph):
     """Every job of the uneven-grid batch against the oracle: FP64 against the oracle run with
     the same algorithm and tolerance (max|dg| <= 1e-6, |dSFE| <= 1e-4 kcal/mol, iterations
     +-2), FP32 (converged to 1e-7) against the oracle at 1e-10 (1e-3, 0.05 kcal/mol)."""
@@ -106,7 +126,7 @@ def test_batch_matches_oracle(water3, precision):
     try:
         jobs = [dict(solver=S, solute=_solute(k, JOBS[k][1]), closure="kh", tol=tol, sfe="kh")
                 for k, S in enumerate(solvers)]
-        res = capi.solve_batch(jobs, max_inflight=3)
+        res = capi.solve_batch(jobs, max_inflight=3, one_graph=one_graph)
         for k, (r, S) in enumerate(zip(res, solvers)):
             grid, n_atoms, _ = JOBS[k]
             P = orc.Problem(water3, grid, _solute(k, n_atoms))
