@@ -294,6 +294,26 @@ rism3d_status rism3d_solve_batch_graph(rism3d_batch_job *jobs, int n_jobs, doubl
  * -P * V with the bulk pressure P of Eq. 20 (rism1d_xrism_ex). */
 rism3d_status rism3d_get_pmv(rism3d_ctx *ctx, double kT_chi_T, double *pmv, double *c_integral);
 
+/* Finite-size error of the SFE of a charged solute on the periodic grid (next row of the
+ * method: thermodynamics; the paper evaluates Eqs. 17-18 as box sums and gives no
+ * correction). The long-range field of Eq. 30 has no k = 0 term, so the box holds the
+ * solvent's response only at the lattice wave vectors; at long range that response is
+ * linear, with the solvent's charge response S(k) = sum_{a,g} q_a X_ag(k) rho_g q_g. delta
+ * (kcal/mol) is half the energy of that response in the solute's Eq. 29 potential on the
+ * box minus the same energy in infinite space:
+ *   delta = -(beta / 2) [ (1/V) sum_{k != 0} Re(Phi~(k) conj(phi~_box(k))) S(|k|)
+ *                        - int d^3k / (2 pi)^3 |Phi~(k)|^2 S(|k|) ],
+ * Phi~ the Eq. 30 field (without beta q_g), phi~_box the DFT of the grid field phi times dV,
+ * the integral in its orientation-averaged radial form (pair sums over the atoms,
+ * trapezoidal rule on [0, 20] 1/A, 16385 points); S below the first table point is
+ * continued as S(k_1) (k / k_1)^2. The infinite-dilution SFE is rism3d_get_sfe's total minus
+ * delta (delta grows as Q^2 / L for net charge Q and box side L; about 0.8 x the Ewald-Wigner
+ * value for a cation in water). Depends on the solute and solvent only; uses the spectrum
+ * buffer as scratch (no state a later solve or rism3d_get needs) and allocates 8.4 MB of
+ * partial sums on the first call. Cost: O(N^3 log N) plus O(n_atoms^2) pair sums (about 0.2 s
+ * for 2000 atoms). EUNSUPPORTED on the half-integer grid or with one solvent site. */
+rism3d_status rism3d_get_sfe_finite_size(rism3d_ctx *ctx, double *delta);
+
 /* Derivative of the SFE with respect to every solute atom position (the second "Eq. 21",
  * Hybrid implementation section): grad[a][k] = sum_g rho_g dV sum_grid g_g(r) du_g(r)/dR_a,k
  * in kcal/mol/A, with du/dR the analytic derivative of Eq. 22's pair terms (Lorentz-Berthelot

@@ -96,6 +96,7 @@ def load():
         "rism3d_get_sfe": (c_int, [c_void_p, c_int, c_int, P(c_double), _dp]),
         "rism3d_solve_batch": (c_int, [P(BatchJob), c_int, c_int, c_double]),
         "rism3d_solve_batch_graph": (c_int, [P(BatchJob), c_int, c_double]),
+        "rism3d_get_sfe_finite_size": (c_int, [c_void_p, P(c_double)]),
         "rism3d_tune": (c_int, [c_void_p, P(c_int), P(c_double)]),
         "rism3d_guess_input": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
         "rism3d_guess_target": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
@@ -514,6 +515,13 @@ class Solver:
         g = np.zeros((getattr(self, "n_atoms", 0), 3))
         _check(self.lib, self.ctx, self.lib.rism3d_get_sfe_gradient(self.ctx, g.ctypes.data_as(_dp)))
         return g
+
+    def sfe_finite_size(self):
+        """Finite-size error of the SFE box sum for the current solute (kcal/mol,
+        rism3d_get_sfe_finite_size): the infinite-dilution SFE is the box SFE minus it."""
+        d = ctypes.c_double()
+        _check(self.lib, self.ctx, self.lib.rism3d_get_sfe_finite_size(self.ctx, ctypes.byref(d)))
+        return d.value
 
     def stats(self):
         st = Stats()

@@ -162,6 +162,7 @@ struct rism3d_ctx {
     // state of the solve in progress (rism3d_solve and the batch scheduler)
     int run_iter_before = 0, run_closure = kKH, run_order = 1;
     std::chrono::steady_clock::time_point run_t0;
+    double *lr_buf = nullptr;                  // finite-size correction: FP64 partial sums (lazy)
 
     bool fp32() const { return precision == 32; }
 };
@@ -782,6 +783,44 @@ bool valid_closure(int kind, int order) {
 }  // namespace
 
 // ------------------------------------------------------------------ public entry points
+// Finite-size correction of the SFE (see rism3d.h): Delta = -(beta / 2) [(1 / V) sum_{k != 0}
+// Re(Phi~ conj(phi~_box)) S(k) - (1 / 2 pi^2) int k^2 |Phi~|^2 S(k) dk (orientation-averaged)].
+constexpr double kLrKmax = 20.0;          // quadrature of the infinite-space integral: [0, 20] 1/A
+constexpr int kLrQuad = 16385;            // trapezoid points (spacing 1.22e-3 1/A)
+constexpr int kLrChunks = 64;             // atom-row chunks of the pair sums
+constexpr int kLrBlocks = 304;            // blocks of the lattice sum and of the quadrature
+
+template <typename T>
+static rism3d_status lr_parts(rism3d_ctx *ctx, Fields<T> &f, double *lat, double *integ) {
+    typedef typename Cx<T>::type C;
+    FftPlan plans[3];
+    const int n[3] = {ctx->Nx, ctx->Ny, ctx->Nz};
+    for (int d = 0; d < 3; ++d)
+        if (!make_plan(n[d], plans[d]))
+            return fail(ctx, RISM3D_EUNSUPPORTED, "no transform plan for length %d", n[d]);
+    double rq[kMaxSites];
+    for (int g = 0; g < kMaxSites; ++g) rq[g] = g < ctx->nv ? ctx->rho[g] * ctx->q[g] : 0.0;
+    double q2 = 0.0;
+    for (int a = 0; a < ctx->n_atoms; ++a) q2 += ctx->atom_host[(size_t)a * kAtomStride + 3] * ctx->atom_host[(size_t)a * kAtomStride + 3];
+    const size_t nbuf = (size_t)kLrChunks * kLrQuad + 2 * kLrBlocks;
+    if (!ctx->lr_buf) CUDA_TRY(ctx, cudaMalloc(&ctx->lr_buf, nbuf * sizeof(double)));
+    double *pairs = ctx->lr_buf, *lat_part = pairs + (size_t)kLrChunks * kLrQuad, *int_part = lat_part + kLrBlocks;
+    const double c4 = (4.0 * kPi * kCoulomb) * (4.0 * kPi * kCoulomb);
+    C *scratch = reinterpret_cast<C *>(f.spec);           // free between solves; nv >= 2 checked by the caller
+    CUDA_TRY(ctx, launch_lr_parts<T>(f, scratch, plans, rq, ctx->atoms, ctx->n_atoms, kLrKmax, kLrQuad, kLrChunks,
+                                     pairs, lat_part, kLrBlocks, int_part, kLrBlocks, c4, q2, ctx->stream));
+    std::vector<double> h(2 * kLrBlocks);
+    CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), lat_part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    double sl = 0.0, si = 0.0;
+    for (int b = 0; b < kLrBlocks; ++b) sl += h[b];
+    for (int b = 0; b < kLrBlocks; ++b) si += h[kLrBlocks + b];
+    const double V = (double)ctx->G * ctx->dV;
+    *lat = sl * ctx->dV * ctx->dV / (ctx->beta * V);       // Psi = beta Phi~ / dV, phi~_box = dV DFT(phi)
+    *integ = si / (2.0 * kPi * kPi);
+    return RISM3D_OK;
+}
+
 extern "C" {
 
 const char *rism3d_version(void) { return "rism3d-gb300 0.1 (sm_103a)"; }
@@ -1389,6 +1428,22 @@ rism3d_status rism3d_get_sfe(rism3d_ctx *ctx, int kind, int pse_order, double *t
     return RISM3D_OK;
 }
 
+rism3d_status rism3d_get_sfe_finite_size(rism3d_ctx *ctx, double *delta) {
+    if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
+    if (!delta) return fail(ctx, RISM3D_EINVAL, "null delta");
+    if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "finite-size correction before set_solute");
+    if (ctx->opt.kgrid != 0)
+        return fail(ctx, RISM3D_EUNSUPPORTED, "the finite-size correction is defined on the periodic (integer) k grid");
+    if (ctx->nv < 2) return fail(ctx, RISM3D_EUNSUPPORTED, "the finite-size correction needs at least two solvent sites");
+    DeviceGuard dg(ctx->device);
+    double lat = 0.0, integ = 0.0;
+    rism3d_status st = ctx->fp32() ? lr_parts<float>(ctx, ctx->f32, &lat, &integ)
+                                   : lr_parts<double>(ctx, ctx->f64, &lat, &integ);
+    if (st != RISM3D_OK) return st;
+    *delta = -0.5 * ctx->beta * (lat - integ);
+    return RISM3D_OK;
+}
+
 static rism3d_status guess_crop(rism3d_ctx *ctx, int mode, const int *corner, int crop, float *out,
                                 const float *in) {
     if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
@@ -1591,6 +1646,7 @@ void rism3d_destroy(rism3d_ctx *ctx) {
             if (e) cudaEventDestroy(e);
         if (ctx->side) cudaStreamDestroy(ctx->side);
         if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
+        if (ctx->lr_buf) cudaFree(ctx->lr_buf);
         if (ctx->ctrl_host) cudaFreeHost(ctx->ctrl_host);
         if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     }

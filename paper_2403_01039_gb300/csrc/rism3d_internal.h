@@ -208,6 +208,16 @@ cudaError_t launch_sfe_gradient(const Fields<T> &f, int slot, int kind, int orde
                                 const double *site_eps, const double *site_q, const double *origin,
                                 const double *spacing, double *partials, double *out, cudaStream_t s);
 
+// Finite-size correction of a charged solute's SFE: phi is transformed into scratch (a
+// complex [Nx][Ny][Nz] array), plans[0..2] are the axis transforms of lengths Nx, Ny, Nz;
+// rq[g] = rho_g q_g (host); atoms [n][kAtomStride] (device); pairs [chunks][nq], lat_part
+// [lat_blocks], int_part [int_blocks] (device, FP64).
+template <typename T>
+cudaError_t launch_lr_parts(const Fields<T> &f, typename Cx<T>::type *scratch, const FftPlan *plans,
+                            const double *rq, const double *atoms, int n_atoms, double k_max, int nq, int chunks,
+                            double *pairs, double *lat_part, int lat_blocks, double *int_part, int int_blocks,
+                            double c4, double q2, cudaStream_t s);
+
 constexpr int kSfeBlocksPerSite = 152;
 constexpr int kGradBlocks = 304;
 constexpr int kPhaseChunk = 256;  // atoms per long-range pass (phase-table capacity)

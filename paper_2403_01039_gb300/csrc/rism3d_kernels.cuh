@@ -2700,6 +2700,248 @@ cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sf
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ finite-size correction
+// The correction of a charged solute's SFE needs three reductions (the energy of the
+// solvent's linear response to the long-range field of Eq. 30 on the box's k lattice with the
+// box-sampled Eq. 29 potential, and in infinite space):
+//   1. phi~_box = DFT of the grid field phi (three in-place axis passes over a complex copy);
+//   2. sum over the half spectrum of w_z Re(Psi conj(phi~_box)) S(|k|), with Psi = beta Phi~ / dV
+//      and S(k) = sum_g rho_g q_g sum_a q_a X_ag(k) from the charge row of the table;
+//   3. the radial integral of (4 pi C)^2 S(k) P(k) / (k^2 (k^2 + 1)^2), P(k) = sum_ab q_a q_b
+//      sin(k R_ab) / (k R_ab) (the orientation average of |sum_a q_a exp(-i k.R_a)|^2).
+
+// a[p] = phi[p] + 0i over the grid
+template <typename T>
+__global__ void k_lr_load_phi(Fields<T> f, typename Cx<T>::type *a) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < f.G; i += (long long)gridDim.x * blockDim.x)
+        a[i] = cmk(f.phi[i], (T)0);
+}
+
+// One axis of the forward 3D DFT of a[Nx][Ny][Nz] in place. A block loads W lines of length
+// L (z: W consecutive (x, y) lines; y and x: the lines at W consecutive z of one x or one y
+// plane, so that each row of the tile is W contiguous values), transforms them in shared
+// memory with the engine of the plane passes and writes them back.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lr_dft_axis(typename Cx<T>::type *a, int Nx, int Ny, int Nz, int axis,
+                                                     FftPlan p, int W, int pitch, int chunk) {
+    typedef typename Cx<T>::type C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *buf = reinterpret_cast<C *>(smraw);
+    const int L = p.L;
+    C *tw = buf + (long)W * pitch;
+    for (int m = threadIdx.x; m < L; m += blockDim.x) {
+        double sn, cs;
+        sincospi(-2.0 * (double)m / (double)L, &sn, &cs);
+        tw[m] = cmk((T)cs, (T)sn);
+    }
+    long long base;
+    long long estride;
+    int nw;
+    if (axis == 2) {                                   // lines (x, y), contiguous
+        const long long line0 = (long long)blockIdx.x * W;
+        nw = (int)min((long long)W, (long long)Nx * Ny - line0);
+        base = line0 * Nz;
+        estride = 1;
+    } else {
+        const int zt = (Nz + W - 1) / W;
+        const int z0 = (blockIdx.x % zt) * W, o = blockIdx.x / zt;
+        nw = min(W, Nz - z0);
+        base = axis == 1 ? (long long)o * Ny * Nz + z0 : (long long)o * Nz + z0;
+        estride = axis == 1 ? (long long)Nz : (long long)Ny * Nz;
+    }
+    const long long wstride = axis == 2 ? (long long)Nz : 1;
+    for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x) {
+        int e, w;
+        if (axis == 2) {
+            w = idx / L;
+            e = idx - w * L;
+        } else {
+            e = idx / W;
+            w = idx - e * W;
+        }
+        if (w < nw) buf[w * pitch + e] = a[base + w * wstride + e * estride];
+    }
+    __syncthreads();
+    fft_smem<C, MaxC<T>::v>(buf, p, 1, W, pitch, chunk, tw, -1);
+    for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x) {
+        int e, w;
+        if (axis == 2) {
+            w = idx / L;
+            e = idx - w * L;
+        } else {
+            e = idx / W;
+            w = idx - e * W;
+        }
+        if (w < nw) a[base + w * wstride + e * estride] = buf[w * pitch + e];
+    }
+}
+
+// S(|k|) from the charge row of the interpolation table (continued as S(k_1) (k / k_1)^2
+// below the first table point k_1 = dk); rq[g] = rho_g q_g.
+template <typename T>
+__device__ double lr_charge_response(const Fields<T> &f, const double *rq, double kmag) {
+    const int nv = f.nv;
+    const int rowlen = (nv + 1) * nv;
+    double xk = kmag * f.inv_dk, scale = 1.0;
+    if (xk < 1.0) {
+        scale = xk * xk;
+        xk = 1.0;
+    }
+    int j = (int)floor(xk);
+    if (j > f.nk - 2) j = f.nk - 2;
+    double w = xk - (double)j;
+    w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+    const T *A0 = f.table + (long long)j * rowlen + nv * nv, *A1 = A0 + rowlen;
+    double s = 0.0;
+    for (int g = 0; g < nv; ++g) s += rq[g] * ((double)A0[g] * (1.0 - w) + (double)A1[g] * w);
+    return -(double)f.G * s * scale;             // the table holds -Q_g / G
+}
+
+struct LrSites {
+    double rq[kMaxSites];
+};
+
+// part[block] = sum over the block's half-spectrum points of w_z Re(Psi conj(F)) S(|k|),
+// F = DFT(phi) (full complex array [Nx][Ny][Nz]).
+template <typename T>
+__global__ void __launch_bounds__(256) k_lr_lattice(Fields<T> f, const typename Cx<T>::type *F, LrSites sites,
+                                                    double *part) {
+    __shared__ double red[8];
+    const int Nx = f.Nx, Ny = f.Ny, Nz = f.Nz, Kz = f.Kz;
+    const long long npts = (long long)Nx * Ny * (Kz + 1);
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
+        const int kz = (int)(i % (Kz + 1));
+        const long long xy = i / (Kz + 1);
+        const int y = (int)(xy % Ny), x = (int)(xy / Ny);
+        typename Cx<T>::type psi;
+        if (kz < Kz) psi = f.psi[xy * Kz + kz];
+        else psi = f.psi_nyq[xy];
+        if (psi.x == (T)0 && psi.y == (T)0) continue;
+        const typename Cx<T>::type Fk = F[xy * Nz + kz];
+        const double kx = f.ks[0] * (double)signed_index(x, Nx), ky = f.ks[1] * (double)signed_index(y, Ny);
+        const double kzv = f.ks[2] * (double)kz;
+        const double S = lr_charge_response(f, sites.rq, sqrt(kx * kx + ky * ky + kzv * kzv));
+        const double wz = (kz == 0 || 2 * kz == Nz) ? 1.0 : 2.0;
+        acc += wz * ((double)psi.x * (double)Fk.x + (double)psi.y * (double)Fk.y) * S;
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// pairs[c][i] = sum over the atom pairs (a, b > a) with a in chunk c of q_a q_b
+// sin(k_i R_ab) / (k_i R_ab), k_i = i dk (the i = 0 value is the limit q_a q_b); atoms
+// [n][kAtomStride] (x, y, z, q, ...). A thread takes kLrRun consecutive k_i and, per pair,
+// starts sin(i x) at its first two indices with sincos and continues with the recurrence
+// sin((i + 1) x) = 2 cos(x) sin(i x) - sin((i - 1) x), x = dk R_ab.
+constexpr int kLrRun = 16;
+static __global__ void __launch_bounds__(256) k_lr_pairs(const double *atoms, int n, int rows_per_chunk, double dk, int nq,
+                                                  double *pairs) {
+    const int i0 = (blockIdx.x * blockDim.x + threadIdx.x) * kLrRun;
+    if (i0 >= nq) return;
+    const int c = blockIdx.y;
+    const int a0 = c * rows_per_chunk, a1 = min(n, a0 + rows_per_chunk);
+    double acc[kLrRun];
+#pragma unroll
+    for (int j = 0; j < kLrRun; ++j) acc[j] = 0.0;
+    double acc0 = 0.0;                                 // the k = 0 limit
+    for (int a = a0; a < a1; ++a) {
+        const double *A = atoms + (size_t)a * kAtomStride;
+        for (int b = a + 1; b < n; ++b) {
+            const double *B = atoms + (size_t)b * kAtomStride;
+            const double dx = A[0] - B[0], dy = A[1] - B[1], dz = A[2] - B[2];
+            const double x = dk * sqrt(dx * dx + dy * dy + dz * dz);
+            const double qq = A[3] * B[3];
+            acc0 += qq;
+            if (!(x > 1e-300)) continue;
+            const double cp = qq / x;
+            double sc = sin((double)i0 * x), sp = sin((double)(i0 - 1) * x);
+            const double cx = cos(x);
+#pragma unroll
+            for (int j = 0; j < kLrRun; ++j) {
+                acc[j] += cp * sc;
+                const double sn = 2.0 * cx * sc - sp;
+                sp = sc;
+                sc = sn;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kLrRun; ++j) {
+        const int i = i0 + j;
+        if (i < nq) pairs[(size_t)c * nq + i] = i == 0 ? acc0 : acc[j] / (double)i;
+    }
+}
+
+// part[block] = sum over the block's quadrature points of the trapezoid weight times
+// (4 pi C)^2 S(k) P(k) / (k^2 (k^2 + 1)^2), P(k) = sum_a q_a^2 + 2 sum_c pairs[c][i]; the
+// k = 0 point takes its limit S(k_1) / k_1^2 P(0) (4 pi C)^2.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lr_integral(Fields<T> f, LrSites sites, const double *pairs, int chunks,
+                                                     int nq, double k_max, double q2, double c4, double *part) {
+    __shared__ double red[8];
+    const double dk = k_max / (double)(nq - 1);
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
+        double P = 0.0;
+        for (int c = 0; c < chunks; ++c) P += pairs[(size_t)c * nq + i];
+        P = q2 + 2.0 * P;
+        double v;
+        if (i == 0) {
+            const double k1 = 1.0 / f.inv_dk;
+            v = c4 * lr_charge_response(f, sites.rq, k1) / (k1 * k1) * P;
+        } else {
+            const double k = dk * (double)i, k2 = k * k;
+            v = c4 * lr_charge_response(f, sites.rq, k) * P / (k2 * (k2 + 1.0) * (k2 + 1.0));
+        }
+        acc += (i == 0 || i == nq - 1 ? 0.5 : 1.0) * dk * v;
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <typename T>
+cudaError_t launch_lr_parts(const Fields<T> &f, typename Cx<T>::type *scratch, const FftPlan *plans,
+                            const double *rq, const double *atoms, int n_atoms, double k_max, int nq, int chunks,
+                            double *pairs, double *lat_part, int lat_blocks, double *int_part, int int_blocks,
+                            double c4, double q2, cudaStream_t s) {
+    typedef typename Cx<T>::type C;
+    k_lr_load_phi<T><<<152 * 8, 256, 0, s>>>(f, scratch);
+    cudaError_t e = cudaGetLastError();
+    const int n[3] = {f.Nx, f.Ny, f.Nz};
+    for (int axis = 2; axis >= 0 && e == cudaSuccess; --axis) {
+        const FftPlan &p = plans[axis];
+        const int W = 8, pitch = p.L + 1;
+        int chunk = 1 << 30;
+        for (int st = 0; st < p.nst; ++st) {
+            const int c = 256 * (MaxC<T>::v / p.radix[st]) / (p.L / p.radix[st]);
+            chunk = c < chunk ? c : chunk;
+        }
+        const size_t smem = sizeof(C) * ((size_t)W * pitch + p.L);
+        e = cudaFuncSetAttribute(k_lr_dft_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) break;
+        const long long blocks = axis == 2 ? ((long long)n[0] * n[1] + W - 1) / W
+                                           : (long long)(axis == 1 ? n[0] : n[1]) * ((n[2] + W - 1) / W);
+        k_lr_dft_axis<T><<<(unsigned)blocks, 256, smem, s>>>(scratch, n[0], n[1], n[2], axis, p, W, pitch, chunk);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+    LrSites sites;
+    for (int g = 0; g < kMaxSites; ++g) sites.rq[g] = g < f.nv ? rq[g] : 0.0;
+    k_lr_lattice<T><<<lat_blocks, 256, 0, s>>>(f, scratch, sites, lat_part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int rows = (n_atoms + chunks - 1) / chunks;
+    if (n_atoms > 1) {
+        const unsigned kb = (unsigned)((nq + 256 * kLrRun - 1) / (256 * kLrRun));
+        k_lr_pairs<<<dim3(kb, (unsigned)chunks), 256, 0, s>>>(atoms, n_atoms, rows, k_max / (double)(nq - 1), nq, pairs);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+        if ((e = cudaMemsetAsync(pairs, 0, sizeof(double) * (size_t)chunks * nq, s)) != cudaSuccess) return e;
+    }
+    k_lr_integral<T><<<int_blocks, 256, 0, s>>>(f, sites, pairs, chunks, nq, k_max, q2, c4, int_part);
+    return cudaGetLastError();
+}
+
 // Explicit instantiations, in two groups compiled in separate translation units: the plane
 // kernels (fused and split) and everything else.
 #define RISM_INSTANTIATE_PLANES(T)                                                              \
@@ -2739,6 +2981,10 @@ cudaError_t launch_sfe(const Fields<T> &f, int slot, int kind, int order, int sf
                                                 const double *, const double *, const double *, \
                                                 const double *, double *, double *, cudaStream_t);    \
     template cudaError_t launch_guess_crop<T>(const Fields<T> &, int, int, const int *, int, float *,  \
-                                              const float *, cudaStream_t);
+                                              const float *, cudaStream_t);                    \
+    template cudaError_t launch_lr_parts<T>(const Fields<T> &, typename Cx<T>::type *, const FftPlan *, \
+                                            const double *, const double *, int, double, int, int, \
+                                            double *, double *, int, double *, int, double, double, \
+                                            cudaStream_t);
 
 }  // namespace rism

@@ -76,3 +76,26 @@ def test_thermo_requires_solute(water3):
         S.set_solute(np.zeros((1, 3)), [0.0], [3.73], [0.294])
         with pytest.raises(capi.RismError):
             S.pmv(-1.0)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("gi", [0, 1])
+def test_sfe_finite_size_matches_oracle(water_nacl, precision, gi):
+    """Finite-size correction of the SFE of a charged solute (rism3d_get_sfe_finite_size)
+    against oracle.thermo: the DFT of the Eq. 29 field, the lattice sum with the solvent's
+    charge response and the orientation-averaged integral (same quadrature: [0, 20] 1/A,
+    16385 points). The result is the difference of two sums of similar size (~10x the result),
+    so the bars are 1e-9 (FP64) and 2e-4 (FP32 fields and transform) relative to the sums."""
+    sol = synth.random_solute(11, 3.0, 23, net_charge=1.0)
+    grid = GRIDS[gi]
+    P = orc.Problem(water_nacl, grid, sol)
+    S_fn = lambda k: thermo.charge_response(P.chi, P.dk, P.site_q, P.rho, k)
+    diff = thermo.lattice_minus_integral(P, sol["xyz"], sol["q"], S_fn, box_field=P.phi, k_max=20.0, n_quad=16385)
+    ref = -0.5 * P.beta * diff
+    scale = 0.5 * P.beta * abs(thermo.lattice_minus_integral(P, sol["xyz"], sol["q"], S_fn, box_field=None,
+                                                             k_max=20.0, n_quad=16385))
+    with capi.Solver(water_nacl, grid, precision=precision) as S:
+        S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+        got = S.sfe_finite_size()
+    bar = (1e-9 if precision == 64 else 2e-4) * max(abs(ref), scale, 1.0)
+    assert abs(got - ref) <= bar, (got, ref, bar)
