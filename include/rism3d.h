@@ -132,6 +132,11 @@ typedef struct {
                                  through distributed shared memory; 1: the y transform as a
                                  separate y-pencil pass over the spectrum. Same results
                                  within rounding. */
+    double anchor_ratio;      /* the transform re-anchors (h = h_a + L(c^sr - c^sr_a), iterate
+                                 offset moved to the current iterate) when the RMS first falls
+                                 below 1e-2 and then whenever it has fallen by this factor
+                                 since the last anchor; in (0, 1), default 0.1 (0 also
+                                 selects it) */
     void *cuda_stream;        /* cudaStream_t to run on; NULL: the library creates one */
     void *workspace;          /* device buffer of >= rism3d_workspace_bytes bytes, 256-byte
                                  aligned, owned by the caller and kept alive until

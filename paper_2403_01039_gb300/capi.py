@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
                 ("accelerator", ctypes.c_int), ("anderson_s1", ctypes.c_double),
                 ("anderson_s2", ctypes.c_double), ("slab_rows", ctypes.c_int),
                 ("split_passes", ctypes.c_int), ("kgrid", ctypes.c_int), ("ypencil_pass", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p),
+                ("anchor_ratio", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
@@ -343,7 +343,8 @@ class Solver:
     def __init__(self, solvent, grid, precision=32, mdiis_nvec=5, mdiis_damp=0.7,
                  dynamic_damp=False, max_iter=10000, check_every=8, max_atoms=100000,
                  timing=False, accelerator="mdiis", anderson_s=(0.2, 0.0), slab_rows=0,
-                 kgrid="integer", split_passes=False, ypencil_pass=False, stream=None, device=None):
+                 kgrid="integer", split_passes=False, ypencil_pass=False, anchor_ratio=None, stream=None,
+                 device=None):
         import torch
         self._torch = torch
         lib = load()
@@ -369,6 +370,8 @@ class Solver:
         o.kgrid = {"integer": 0, "half": 1}[kgrid]
         o.split_passes = int(bool(split_passes))
         o.ypencil_pass = int(bool(ypencil_pass))
+        if anchor_ratio is not None:
+            o.anchor_ratio = float(anchor_ratio)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
             o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)

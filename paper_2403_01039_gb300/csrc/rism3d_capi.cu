@@ -15,9 +15,21 @@
 #include <vector>
 
 #include "rism3d.h"
+
+#include <nvtx3/nvToolsExt.h>
 #include "rism3d_internal.h"
 
 using namespace rism;
+
+// NVTX range around each public call, so that a timeline (Nsight Systems, ncu --nvtx)
+// shows where the set-up, the iteration and the reductions of a solve begin and end; the
+// header-only NVTX costs nothing unless a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 namespace {
 
@@ -272,6 +284,8 @@ rism3d_status check_inputs(const rism3d_solvent *sv, const rism3d_grid *gr, cons
     if (op->kgrid != 0 && op->kgrid != 1) return fail(nullptr, RISM3D_EINVAL, "kgrid must be 0 or 1");
     if (op->ypencil_pass != 0 && op->ypencil_pass != 1)
         return fail(nullptr, RISM3D_EINVAL, "ypencil_pass must be 0 or 1");
+    if (!(op->anchor_ratio >= 0.0 && op->anchor_ratio < 1.0))
+        return fail(nullptr, RISM3D_EINVAL, "anchor_ratio must be in [0, 1) (0: the default 0.1)");
     if (op->split_passes != 0 && op->split_passes != 1) return fail(nullptr, RISM3D_EINVAL, "split_passes must be 0 or 1");
     if (op->timing < 0 || op->timing > 2) return fail(nullptr, RISM3D_EINVAL, "timing must be 0, 1 or 2");
     if (op->accelerator != 0 && op->accelerator != 1)
@@ -737,6 +751,7 @@ void reset_ctrl(rism3d_ctx *ctx, Ctrl &c) {
     c.anchor_valid = 0;
     c.refresh = 0;
     c.next_refresh = 1e-2;
+    c.anchor_ratio = ctx->opt.anchor_ratio > 0.0 ? ctx->opt.anchor_ratio : 1e-1;
 }
 
 template <typename T> Fields<T> &fields(rism3d_ctx *ctx);
@@ -838,6 +853,7 @@ void rism3d_options_default(rism3d_options *opt) {
     opt->accelerator = 0;
     opt->anderson_s1 = 0.2;
     opt->anderson_s2 = 0.0;
+    opt->anchor_ratio = 1e-1;
 }
 
 rism3d_status rism3d_workspace_bytes(const rism3d_solvent *solvent, const rism3d_grid *grid,
@@ -852,6 +868,7 @@ rism3d_status rism3d_workspace_bytes(const rism3d_solvent *solvent, const rism3d
 
 rism3d_status rism3d_create(const rism3d_solvent *sv, const rism3d_grid *gr, const rism3d_options *op,
                             rism3d_ctx **out) {
+    NvtxRange nvtx_("rism3d_create");
     if (!out) return fail(nullptr, RISM3D_EINVAL, "null out");
     *out = nullptr;
     Geometry g{};
@@ -956,6 +973,7 @@ rism3d_status rism3d_create(const rism3d_solvent *sv, const rism3d_grid *gr, con
 
 rism3d_status rism3d_set_solute(rism3d_ctx *ctx, int n_atoms, const double *xyz, const double *q,
                                 const double *sigma, const double *eps) {
+    NvtxRange nvtx_("rism3d_set_solute");
     if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
     if (n_atoms < 1 || n_atoms > ctx->opt.max_atoms)
         return fail(ctx, RISM3D_EINVAL, "n_atoms must be in 1..%d", ctx->opt.max_atoms);
@@ -1125,6 +1143,7 @@ static rism3d_status solve_finish(rism3d_ctx *ctx, rism3d_report *rep, bool stop
 }
 
 rism3d_status rism3d_solve(rism3d_ctx *ctx, int closure, int pse_order, double tol, rism3d_report *rep) {
+    NvtxRange nvtx_("rism3d_solve");
     if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
     DeviceGuard dg(ctx->device);
     rism3d_status st = solve_begin(ctx, closure, pse_order, tol);
@@ -1140,6 +1159,7 @@ rism3d_status rism3d_solve(rism3d_ctx *ctx, int closure, int pse_order, double t
 }
 
 rism3d_status rism3d_solve_batch(rism3d_batch_job *jobs, int n_jobs, int max_inflight, double time_limit_s) {
+    NvtxRange nvtx_("rism3d_solve_batch");
     if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(nullptr, RISM3D_EINVAL, "bad job list");
     if (max_inflight < 1) return fail(nullptr, RISM3D_EINVAL, "max_inflight must be >= 1");
     for (int j = 0; j < n_jobs; ++j) {    // a job that never starts reports ESTATE
@@ -1265,6 +1285,7 @@ static rism3d_status add_device_loop(rism3d_ctx *ctx, cudaGraph_t g, unsigned lo
 }
 
 rism3d_status rism3d_solve_batch_graph(rism3d_batch_job *jobs, int n_jobs, double time_limit_s) {
+    NvtxRange nvtx_("rism3d_solve_batch_graph");
     if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(nullptr, RISM3D_EINVAL, "bad job list");
     if (!(time_limit_s >= 0.0)) return fail(nullptr, RISM3D_EINVAL, "time_limit_s must be >= 0");
     for (int j = 0; j < n_jobs; ++j) {
@@ -1395,6 +1416,7 @@ rism3d_status rism3d_get(rism3d_ctx *ctx, int field, double *dst, size_t count, 
 }
 
 rism3d_status rism3d_get_sfe(rism3d_ctx *ctx, int kind, int pse_order, double *total, double *per_site) {
+    NvtxRange nvtx_("rism3d_get_sfe");
     if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
     if (kind < RISM3D_SFE_KH || kind > RISM3D_SFE_PSE) return fail(ctx, RISM3D_EINVAL, "bad SFE kind %d", kind);
     if (kind == RISM3D_SFE_PSE && pse_order < 1) return fail(ctx, RISM3D_EINVAL, "PSE order must be >= 1");
@@ -1429,6 +1451,7 @@ rism3d_status rism3d_get_sfe(rism3d_ctx *ctx, int kind, int pse_order, double *t
 }
 
 rism3d_status rism3d_get_sfe_finite_size(rism3d_ctx *ctx, double *delta) {
+    NvtxRange nvtx_("rism3d_get_sfe_finite_size");
     if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
     if (!delta) return fail(ctx, RISM3D_EINVAL, "null delta");
     if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "finite-size correction before set_solute");
@@ -1511,6 +1534,7 @@ rism3d_status rism3d_get_pmv(rism3d_ctx *ctx, double kT_chi_T, double *pmv, doub
 }
 
 rism3d_status rism3d_get_sfe_gradient(rism3d_ctx *ctx, double *grad) {
+    NvtxRange nvtx_("rism3d_get_sfe_gradient");
     if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
     if (!grad) return fail(ctx, RISM3D_EINVAL, "null grad");
     if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "get_sfe_gradient before set_solute");
@@ -1608,6 +1632,7 @@ static rism3d_status tune_pencil(rism3d_ctx *ctx, Fields<T> &f, int *chosen, dou
 extern "C" {
 
 rism3d_status rism3d_tune(rism3d_ctx *ctx, int *pencil_width, double *pencil_ms) {
+    NvtxRange nvtx_("rism3d_tune");
     if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");
     if (!ctx->has_solute) return fail(ctx, RISM3D_ESTATE, "tune before set_solute");
     DeviceGuard dg(ctx->device);

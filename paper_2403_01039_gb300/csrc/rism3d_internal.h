@@ -98,6 +98,7 @@ struct Ctrl {
     long long acc_shift;            // stored Y fields rewritten in the new offset on refresh
     long long acc_psi;              // iterations whose pencil pass read Psi
     double B[kMaxHist * kMaxHist];  // Gram matrix indexed by ring slot
+    double anchor_ratio;            // re-anchor when the RMS has fallen by this factor
     unsigned long long deadline;    // device-loop solves: %globaltimer value past which the
                                     // loop stops (0 until the first loop test sets it)
 };

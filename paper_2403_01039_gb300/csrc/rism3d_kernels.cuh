@@ -1366,7 +1366,7 @@ static __device__ void mdiis_pre(Ctrl *ctl, const double *sums, MdiisScratch &sc
     }
     if (rms < ctl->next_refresh) {    // next iteration re-anchors the transform
         ctl->refresh = 1;
-        ctl->next_refresh = rms * 1e-2;
+        ctl->next_refresh = rms * ctl->anchor_ratio;
     }
     const int st = ctl->stage;
     if (rms < ctl->stage_tol[st]) {
