@@ -1130,8 +1130,10 @@ __device__ __forceinline__ void inv_elements(const Fields<T> &f, const InvArgs<T
 
 // Gram row of the new residual, <R, R_i> for each stored residual i, over the block's rows:
 // R from the row buffer, R_i streamed from the ring, one history value at a time (one
-// accumulator in registers, four loads in flight per thread). The warp sums go to
+// accumulator in registers, kGramInFlight loads in flight per thread, issued before the
+// shared-memory reads of R so that only the loads occupy registers). The warp sums go to
 // red[(i + 1) * nw + warp].
+constexpr int kGramInFlight = 8;
 template <typename T>
 __device__ __forceinline__ void gram_row(const Fields<T> &f, const InvArgs<T> &A,
                                          const typename Cx<T>::type *buf, int y0, int nyb, double *red) {
@@ -1146,20 +1148,21 @@ __device__ __forceinline__ void gram_row(const Fields<T> &f, const InvArgs<T> &A
         GramAcc<T> acc;
         acc.zero();
         int e = threadIdx.x;
-        for (; e + 3 * nthr < n; e += 4 * nthr) {
-            V2 qv[4];
-            C rv[4];
+        for (; e + (kGramInFlight - 1) * nthr < n; e += kGramInFlight * nthr) {
+            V2 qv[kGramInFlight];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kGramInFlight; ++u) {
                 const int ei = e + u * nthr;
                 const int y = fdiv(ei, f.dKz), m = ei - y * Kz;
                 qv[u] = ld2(q + (long long)(y0 + y) * f.Nz + 2 * m);
-                rv[u] = buf[y * pitch + m];
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                acc.add(rv[u].x, qv[u].x);
-                acc.add(rv[u].y, qv[u].y);
+            for (int u = 0; u < kGramInFlight; ++u) {
+                const int ei = e + u * nthr;
+                const int y = fdiv(ei, f.dKz), m = ei - y * Kz;
+                const C rv = buf[y * pitch + m];
+                acc.add(rv.x, qv[u].x);
+                acc.add(rv.y, qv[u].y);
             }
         }
         for (; e < n; e += nthr) {
