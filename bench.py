@@ -492,10 +492,16 @@ def run_ours(args):
     it_ms = sum(share_ms[k] for k in it_keys) / stats["iterations"] if stats["iterations"] else None
     iter_bytes = (3 * M + 9) * sb * P
     iter_gbs = iter_bytes / (it_ms / 1e3) / 1e9 if it_ms else None
+    traffic = ncu_traffic(dom, args.workload)
     roofline = dict(bound="hbm", kernel=dom, achieved=achieved, peak=peak, unit="GB/s",
                     frac=achieved / peak, peak_source=peak_src,
                     frac_of_nominal=achieved / NOMINAL_HBM_GBS, nominal_peak=NOMINAL_HBM_GBS,
-                    traffic=ncu_traffic(dom, args.workload),
+                    traffic=traffic,
+                    frac_by_traffic=(traffic / per_launch_s / 1e9 / peak) if traffic and per_launch_s > 0 else None,
+                    model_note=("the (3M+9)s byte model counts 2M history fields for the update of plane_fwd; "
+                                "storing Y = t + eta R lets the kernel read M, so its DRAM traffic is below the "
+                                "model and frac_by_traffic (ncu bytes / launch time) is the bandwidth it sustains"
+                                if dom == "plane_fwd" else None),
                     algorithmic_bytes_per_launch=bytes_per_launch,
                     bytes_model="(3M+9)s per site-point and iteration; %s: %s" % (
                         dom, "%ds" % model_units[dom] if dom in model_units else "library counter"),
