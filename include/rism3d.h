@@ -337,6 +337,20 @@ rism3d_status rism3d_get_sfe_gradient(rism3d_ctx *ctx, double *grad);
  * NULL. No counterpart in the paper. */
 rism3d_status rism3d_tune(rism3d_ctx *ctx, int *pencil_width, double *pencil_ms);
 
+/* Autotune the plane-pass tile before creating a context (no counterpart in the paper):
+ * for each row-chunk shape the grid admits - whole y-z planes or automatic chunks
+ * (slab_rows = 0), and chunks of Ny/2, Ny/4 and Ny/8 rows, each as a thread-block cluster
+ * that does the y transform (ypencil_pass = 0) and with the separate y-pencil pass (1) - a
+ * context is created with opt's other options, given a neutral LJ sphere at the grid centre,
+ * and timed over `iters` iterations (after a first solve that captures its graph). *best
+ * receives opt with the fastest slab_rows and ypencil_pass; ms_per_iter (may be NULL) its
+ * time per iteration. Shapes that cannot be created (shared memory, cluster limits) are
+ * skipped. Every candidate allocates and frees its own workspace, so the call needs the
+ * memory of one context at a time. Results of solves do not depend on the shape beyond
+ * rounding. EINVAL for bad arguments or iters < 2; EUNSUPPORTED when no shape works. */
+rism3d_status rism3d_tune_planes(const rism3d_solvent *solvent, const rism3d_grid *grid, const rism3d_options *opt,
+                                 int iters, rism3d_options *best, double *ms_per_iter);
+
 /* Copy the counters; timing fields are zero unless the context was created with timing = 1. */
 rism3d_status rism3d_get_stats(const rism3d_ctx *ctx, rism3d_stats *out);
 

@@ -97,6 +97,7 @@ def load():
         "rism3d_solve_batch": (c_int, [P(BatchJob), c_int, c_int, c_double]),
         "rism3d_solve_batch_graph": (c_int, [P(BatchJob), c_int, c_double]),
         "rism3d_get_sfe_finite_size": (c_int, [c_void_p, P(c_double)]),
+        "rism3d_tune_planes": (c_int, [c_void_p, c_void_p, P(Options), c_int, P(Options), P(c_double)]),
         "rism3d_tune": (c_int, [c_void_p, P(c_int), P(c_double)]),
         "rism3d_guess_input": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
         "rism3d_guess_target": (c_int, [c_void_p, P(c_int), c_int, c_void_p]),
@@ -298,6 +299,27 @@ def xrism(sites, n_r=2048, dr=0.05, closure="kh", tol=1e-10, charge_steps=10, th
     if thermo:
         return chi, dk.value, its.value, rms.value, dict(c=c_r, pressure=pres.value, kT_chi_T=ktchi.value)
     return chi, dk.value, its.value, rms.value
+
+
+def tune_planes(solvent, grid, precision=32, mdiis_nvec=5, iters=16, kgrid="integer"):
+    """rism3d_tune_planes: the fastest plane-pass tile (slab_rows, ypencil_pass) for this
+    solvent, grid and precision, timed on temporary contexts. Returns dict(slab_rows,
+    ypencil_pass, ms_per_iter), ready to pass to Solver."""
+    lib = load()
+    solv, keep = make_solvent(solvent)
+    gr = make_grid(grid)
+    o = default_options()
+    o.precision = precision
+    o.mdiis_nvec = mdiis_nvec
+    o.kgrid = {"integer": 0, "half": 1}[kgrid]
+    best = Options()
+    ms = c_double()
+    st = lib.rism3d_tune_planes(ctypes.byref(solv), ctypes.byref(gr), ctypes.byref(o), int(iters), ctypes.byref(best),
+                                ctypes.byref(ms))
+    if st != OK:
+        raise RismError(st, lib.rism3d_last_error(None).decode())
+    del keep
+    return dict(slab_rows=best.slab_rows, ypencil_pass=bool(best.ypencil_pass), ms_per_iter=ms.value)
 
 
 def solve_batch(jobs, max_inflight=8, time_limit=0.0, one_graph=False):

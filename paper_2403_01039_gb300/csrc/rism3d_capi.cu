@@ -1631,6 +1631,59 @@ static rism3d_status tune_pencil(rism3d_ctx *ctx, Fields<T> &f, int *chosen, dou
 
 extern "C" {
 
+rism3d_status rism3d_tune_planes(const rism3d_solvent *sv, const rism3d_grid *gr, const rism3d_options *op,
+                                 int iters, rism3d_options *best, double *ms_per_iter) {
+    NvtxRange nvtx_("rism3d_tune_planes");
+    if (!sv || !gr || !op || !best) return fail(nullptr, RISM3D_EINVAL, "null argument");
+    if (iters < 2) return fail(nullptr, RISM3D_EINVAL, "iters must be >= 2");
+    struct Cand {
+        int slab, ypencil;
+    };
+    std::vector<Cand> cands = {{0, 0}};
+    const int Ny = gr->n[1];
+    for (int d : {2, 4, 8})
+        if (Ny % d == 0) {
+            cands.push_back({Ny / d, 0});
+            cands.push_back({Ny / d, 1});
+        }
+    double best_ms = 1e300;
+    bool found = false;
+    rism3d_options chosen = *op;
+    for (const Cand &c : cands) {
+        rism3d_options o = *op;
+        o.slab_rows = c.slab;
+        o.ypencil_pass = c.ypencil;
+        o.max_iter = iters;
+        o.timing = 0;
+        o.workspace = nullptr;          // each candidate allocates its own workspace
+        o.workspace_bytes = 0;
+        rism3d_ctx *ctx = nullptr;
+        if (rism3d_create(sv, gr, &o, &ctx) != RISM3D_OK) continue;   // shape not available here
+        double xyz[3];
+        for (int d = 0; d < 3; ++d) xyz[d] = gr->origin[d] + 0.5 * gr->n[d] * gr->spacing[d];
+        const double q = 0.0, sig = 3.5, eps = 0.2;
+        double ms = 1e300;
+        if (rism3d_set_solute(ctx, 1, xyz, &q, &sig, &eps) == RISM3D_OK) {
+            rism3d_report rep{};
+            rism3d_solve(ctx, RISM3D_KH, 1, 1e-300, &rep);          // graph capture and warm-up
+            const rism3d_status st = rism3d_solve(ctx, RISM3D_KH, 1, 1e-300, &rep);
+            if ((st == RISM3D_OK || st == RISM3D_ENOTCONV) && rep.iterations > 0)
+                ms = rep.seconds_iter * 1e3 / rep.iterations;
+        }
+        rism3d_destroy(ctx);
+        if (ms < best_ms) {
+            best_ms = ms;
+            chosen.slab_rows = c.slab;
+            chosen.ypencil_pass = c.ypencil;
+            found = true;
+        }
+    }
+    if (!found) return fail(nullptr, RISM3D_EUNSUPPORTED, "no plane tile shape could be created and timed");
+    *best = chosen;
+    if (ms_per_iter) *ms_per_iter = best_ms;
+    return RISM3D_OK;
+}
+
 rism3d_status rism3d_tune(rism3d_ctx *ctx, int *pencil_width, double *pencil_ms) {
     NvtxRange nvtx_("rism3d_tune");
     if (!ctx) return fail(nullptr, RISM3D_EINVAL, "null context");

@@ -142,3 +142,21 @@ def test_batch_matches_oracle(water3, precision, one_graph):
     finally:
         for S in solvers:
             S.close()
+
+
+def test_tune_planes_picks_a_working_shape(water_nacl):
+    """rism3d_tune_planes times the plane-pass tiles the grid admits on temporary contexts and
+    returns the fastest; a solve with that tile gives the default tile's result to rounding
+    (FP64: 1e-8 in g) and the same iteration count."""
+    grid = dict(n=(24, 32, 32), spacing=(0.5, 0.5, 0.5), origin=(-6.0, -8.0, -8.0))
+    t = capi.tune_planes(water_nacl, grid, precision=64, mdiis_nvec=5, iters=8)
+    assert t["slab_rows"] in (0, 16, 8, 4) and t["ms_per_iter"] > 0.0, t
+    sol = synth.random_solute(8, 3.0, 11, net_charge=1.0)
+    out = []
+    for kw in (dict(), dict(slab_rows=t["slab_rows"], ypencil_pass=t["ypencil_pass"])):
+        with capi.Solver(water_nacl, grid, precision=64, **kw) as S:
+            S.set_solute(sol["xyz"], sol["q"], sol["sigma"], sol["eps"])
+            rep = S.solve("kh", tol=1e-8)
+            out.append((rep["iterations"], S.get("g")))
+    assert out[0][0] == out[1][0]
+    assert np.max(np.abs(out[0][1] - out[1][1])) <= 1e-8
