@@ -602,9 +602,10 @@ def batch_measure(precision, tol, inflight, steps, warmup, with_clocks=False):
     with factors 2, 3, 5 only) in 3-site water, KH, MDIIS 5. A step is the whole batch: every
     job's set_solute + solve + SFE, once one at a time, once through rism3d_solve_batch (host
     scheduler, ``inflight`` jobs at a time) and once through rism3d_solve_batch_graph (all jobs
-    as device loops in one graph launch). Before timing, the plane-pass tile of each distinct
-    grid is picked by rism3d_tune_planes and the contexts (one per grid) tune their pencil
-    widths."""
+    as device loops in one graph launch). Contexts are created (one per grid) and their pencil
+    tiles tuned before timing; the plane tiles stay the default (tiles picked by
+    rism3d_tune_planes for a grid alone made the batch 5 % slower: a tile that fills the GPU
+    alone is not the one that shares it best)."""
     import numpy as np
     import torch
 
@@ -614,15 +615,7 @@ def batch_measure(precision, tol, inflight, steps, warmup, with_clocks=False):
     chi, dk, _, _ = capi.xrism(sites)
     solv = dict(sites, chi=chi, dk=dk)
     work = synth.batch_workload()
-    # plane-pass tile per distinct grid (rism3d_tune_planes), then the pencil width per context
-    shapes = {}
-    for w in work:
-        key = tuple(w["grid"]["n"])
-        if key not in shapes:
-            shapes[key] = capi.tune_planes(solv, w["grid"], precision=precision, mdiis_nvec=5, iters=8)
-    solvers = [capi.Solver(solv, w["grid"], precision=precision, mdiis_nvec=5,
-                           slab_rows=shapes[tuple(w["grid"]["n"])]["slab_rows"],
-                           ypencil_pass=shapes[tuple(w["grid"]["n"])]["ypencil_pass"]) for w in work]
+    solvers = [capi.Solver(solv, w["grid"], precision=precision, mdiis_nvec=5) for w in work]
     try:
         tuned = []
         for S, w in zip(solvers, work):
@@ -678,10 +671,7 @@ def batch_measure(precision, tol, inflight, steps, warmup, with_clocks=False):
                 batched_iterations=it_bat, one_at_a_time_iterations=it_seq, t_batched_s=t_bat,
                 site_gridpoint_iters_per_s=sum(spi[-steps:]) / t_bat,
                 pencil_widths={str(k): tuned.count(k) for k in sorted(set(tuned))},
-                plane_tiles={"x".join(map(str, k)): "%s%s" % ("whole/auto" if v["slab_rows"] == 0 else
-                                                            "%d rows" % v["slab_rows"],
-                                                            " + y pencils" if v["ypencil_pass"] else "")
-                             for k, v in sorted(shapes.items())}, clocks=clk)
+                clocks=clk)
 
 
 def learned_guess_measure(n_seeds=8, tol=1e-6):

@@ -313,7 +313,7 @@ def tune_planes(solvent, grid, precision=32, mdiis_nvec=5, iters=16, kgrid="inte
     o.mdiis_nvec = mdiis_nvec
     o.kgrid = {"integer": 0, "half": 1}[kgrid]
     best = Options()
-    ms = c_double()
+    ms = ctypes.c_double()
     st = lib.rism3d_tune_planes(ctypes.byref(solv), ctypes.byref(gr), ctypes.byref(o), int(iters), ctypes.byref(best),
                                 ctypes.byref(ms))
     if st != OK:

@@ -234,3 +234,14 @@ def test_workloads_fit_one_gb300(lib):
             nb = ctypes.c_size_t()
             st = lib.rism3d_workspace_bytes(ctypes.byref(s), ctypes.byref(g), ctypes.byref(o), ctypes.byref(nb))
             assert st == capi.OK and 0 < nb.value < 0.6 * hbm, (name, prec, nb.value)
+
+
+def test_tune_planes_validates_before_any_device_work(lib):
+    """rism3d_tune_planes refuses iters < 2 without touching the GPU."""
+    from paper_2403_01039_gb300 import capi, synth
+    d = np.load(os.path.join(ROOT, "tests", "golden", "chi_water3.npz"))
+    s = synth.water_3site()
+    s.update(chi=d["chi"], dk=float(d["dk"]))
+    with pytest.raises(capi.RismError) as e:
+        capi.tune_planes(s, synth.cubic_grid(16, 0.5), iters=1)
+    assert e.value.status == capi.EINVAL
