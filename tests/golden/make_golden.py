@@ -67,17 +67,19 @@ def sample_points(n, count, seed):
 
 def make_full(workload, closures=((cl.KH, 3, "kh"), (cl.PSE, 3, "pse3")), tols=(1e-6, 1e-10)):
     """Oracle solves of a full-size workload; stores the solution at 1024 seeded grid points
-    (all sites) plus SFEs and iteration counts in tests/golden/<workload>_reference.npz."""
+    (all sites), g on the whole x = N/2 plane (all sites; float64 at 1e-6, float32 at tighter
+    tolerances) plus SFEs and iteration counts in tests/golden/<workload>_reference.npz."""
     w = synth.WORKLOADS[workload]
     s = synth.solvent_sites(w["solvent"])
     chi = np.load(os.path.join(HERE, "chi_%s.npz" % w["solvent"]))
     solv = dict(q=s["q"], sigma=s["sigma"], eps=s["eps"], rho=s["rho"],
                 temperature=s["temperature"], chi=chi["chi"], dk=float(chi["dk"]))
     grid = synth.cubic_grid(w["n"], w["spacing"])
-    P = rism3d.Problem(solv, grid, synth.workload_solute(workload))
+    P = rism3d.Problem(solv, grid, synth.workload_solute(workload), workers=8, threads=5)
     pts = sample_points(w["n"], 1024, 7)
     idx = (slice(None), pts[:, 0], pts[:, 1], pts[:, 2])
-    out = dict(points=pts)
+    xp = w["n"] // 2
+    out = dict(points=pts, plane_x=xp)
     for kind, order, tag in closures:
         for tol in tols:
             t0 = time.time()
@@ -95,6 +97,8 @@ def make_full(workload, closures=((cl.KH, 3, "kh"), (cl.PSE, 3, "pse3")), tols=(
             out[key + "_c"] = sol["c"][idx]
             out[key + "_t"] = sol["t"][idx]
             out[key + "_g_max"] = float(sol["g"].max())
+            plane = sol["g"][:, xp]
+            out[key + "_g_plane"] = plane if tol >= 1e-6 else plane.astype(np.float32)
             print(workload, tag, tol, sol["iterations"], sol["converged"], tot,
                   "%.0f s" % (time.time() - t0), flush=True)
             np.savez_compressed(os.path.join(HERE, "%s_reference.npz" % workload), **out)
