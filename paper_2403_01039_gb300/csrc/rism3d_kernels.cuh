@@ -317,7 +317,9 @@ __device__ void fft_p2(C *buf, int es, int nb, int bs, const C *tw, int sign) {
 // Transform the nb sequences. When the plan allows (seq_per_warp > 0), each warp takes its
 // own groups of seq_per_warp sequences and separates stages with warp barriers only;
 // otherwise the whole block takes chunks of `chunk` sequences with block barriers.
-template <typename C, int MAXC>
+// GENERIC = false compiles only the power-of-two lengths 16..256 (the caller guarantees
+// one), which keeps the mixed-radix stages and their registers out of the kernel.
+template <typename C, int MAXC, bool GENERIC = true>
 __device__ void fft_smem(C *buf, const FftPlan &p, int es, int nb, int bs, int chunk, const C *tw,
                          int sign) {
     switch (p.L) {
@@ -328,6 +330,7 @@ __device__ void fft_smem(C *buf, const FftPlan &p, int es, int nb, int bs, int c
         case 256: fft_p2<C, 256>(buf, es, nb, bs, tw, sign); return;
         default: break;
     }
+    if constexpr (!GENERIC) return;
     if (p.seq_per_warp > 0) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         const int S = p.seq_per_warp;
@@ -840,9 +843,9 @@ k_plane_fwd(Fields<T> f) {
     // symmetry of a real sequence's transform: A[k] = (P[k] + conj P[-k]) / 2,
     // B[k] = -i (P[k] - conj P[-k]) / 2.
     if (nyc == 1 && half) {
-        fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, -1);
+        fft_smem<C, MaxC<T>::v, LZ == 0>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, -1);
     } else if (nyc == 1) {
-        fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, -1);
+        fft_smem<C, MaxC<T>::v, LZ == 0>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, -1);
         for (int k = threadIdx.x; k <= Ny / 2; k += blockDim.x) {
             const int k2 = k == 0 ? 0 : Ny - k;
             const C P = buf[k * pitch], Q = buf[k2 * pitch];
@@ -858,7 +861,7 @@ k_plane_fwd(Fields<T> f) {
         // the y transform across the cluster (all Kz + 1 columns, unpacked): the cross-block
         // radix step, then the local length-S transform; row y then holds ky = R y + yc
         cluster_y_step<C>(buf, f.cl, nyb, Kz + 1, pitch, f.dK1, tw_y, -1);
-        fft_smem<C, MaxC<T>::v>(buf, f.pys, pitch, Kz + 1, 1, f.chunk_ys, tw_s, -1);
+        fft_smem<C, MaxC<T>::v, LZ == 0>(buf, f.pys, pitch, Kz + 1, 1, f.chunk_ys, tw_s, -1);
         C *dst = f.spec + ((long long)gam * f.Nx + x) * Ny * Kz;
         for (int idx = threadIdx.x; idx < nyb * Kz; idx += blockDim.x) {
             const int y = fdiv(idx, f.dKz), k = idx - y * Kz;
@@ -883,8 +886,9 @@ k_plane_fwd(Fields<T> f) {
 __device__ __forceinline__ int signed_index(int i, int N) { return (2 * i < N) ? i : i - N; }
 
 // One block per tile of W spectrum columns (all x, all NV sites). NV is a template argument
-// so the contraction unrolls over exactly the solvent sites.
-template <typename T, int NV>
+// so the contraction unrolls over exactly the solvent sites; P2 compiles only the
+// power-of-two x transforms (Nx = 16..256).
+template <typename T, int NV, bool P2>
 __global__ void __launch_bounds__(kThreadsPencil, sizeof(T) == 4 ? RISM_MINBLOCKS_F32 : 2)
 k_pencil(Fields<T> f) {
     typedef typename Cx<T>::type C;
@@ -930,7 +934,7 @@ k_pencil(Fields<T> f) {
     }
     if (sizeof(T) == 4) cp_async_wait();
     __syncthreads();
-    fft_smem<C, MaxC<T>::v>(buf, f.px, 1, NV * W, pp, f.chunk_x, tw_x, -1);
+    fft_smem<C, MaxC<T>::v, !P2>(buf, f.px, 1, NV * W, pp, f.chunk_x, tw_x, -1);
     // contraction (Eq. 13 with Eq. 32): E_g = sum_a D_a A_ag(|k|) [+ Psi A_{nv,g} before the
     // first anchor, after which f~ is part of h_a]
     const C *psi = nyq ? f.psi_nyq : f.psi;
@@ -976,7 +980,7 @@ k_pencil(Fields<T> f) {
         }
     }
     __syncthreads();
-    fft_smem<C, MaxC<T>::v>(buf, f.px, 1, NV * W, pp, f.chunk_x, tw_x, +1);
+    fft_smem<C, MaxC<T>::v, !P2>(buf, f.px, 1, NV * W, pp, f.chunk_x, tw_x, +1);
     C *dst_base = nyq ? f.spec_nyq : f.spec;
     for (int idx = threadIdx.x; idx < nload; idx += blockDim.x) {
         const int rest = fdiv(idx, f.dW), c = idx - rest * W;
@@ -1266,7 +1270,7 @@ k_plane_inv(Fields<T> f) {
     }
     __syncthreads();
     if (nyc == 1 && half) {
-        fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, +1);
+        fft_smem<C, MaxC<T>::v, LZ == 0>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, +1);
     } else if (nyc == 1) {
         // columns kz = 0 and Kz (transforms of real sequences) as one: P = A + iB
         for (int y = threadIdx.x; y < Ny; y += blockDim.x) {
@@ -1274,12 +1278,12 @@ k_plane_inv(Fields<T> f) {
             buf[y * pitch] = cmk(A0.x - B0.y, A0.y + B0.x);
         }
         __syncthreads();
-        fft_smem<C, MaxC<T>::v>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, +1);
+        fft_smem<C, MaxC<T>::v, LZ == 0>(buf, f.py, pitch, Kz, 1, f.chunk_cols_fwd, tw_y, +1);
     } else if (clus) {
         // inverse y transform across the cluster: the local length-S transform (it ends with
         // a block barrier), then the cross-block radix step
         C *tw_s = reinterpret_cast<C *>(red + (kMaxHist + 1) * (kThreadsPlane / 32));
-        fft_smem<C, MaxC<T>::v>(buf, f.pys, pitch, Kz + 1, 1, f.chunk_ys, tw_s, +1);
+        fft_smem<C, MaxC<T>::v, LZ == 0>(buf, f.pys, pitch, Kz + 1, 1, f.chunk_ys, tw_s, +1);
         cluster_y_step<C>(buf, f.cl, nyb, Kz + 1, pitch, f.dK1, tw_y, +1);
     }
 
@@ -2481,10 +2485,15 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 }
 
 // z-row length classes with a specialised plane kernel (FP32 only; FP64 and other lengths
-// take the block-wide form)
+// take the block-wide form). The specialised kernels compile only the power-of-two
+// transforms, so every y transform they run (whole columns of Ny, or the local length of
+// a cluster's row chunks) must be one of those too.
+inline bool p2_length(int L) { return L >= 16 && L <= 256 && (L & (L - 1)) == 0; }
 template <typename T> int plane_lz(const Fields<T> &f) {
-    if (sizeof(T) != 4) return 0;
-    return (f.Kz == 64 || f.Kz == 128) ? f.Kz : 0;
+    if (sizeof(T) != 4 || !(f.Kz == 64 || f.Kz == 128)) return 0;
+    if (f.nyc == 1 && !p2_length(f.py.L)) return 0;
+    if (f.nyc > 1 && f.cl > 1 && !p2_length(f.pys.L)) return 0;
+    return f.Kz;
 }
 
 template <typename T, int LZ> cudaError_t prepare_planes(size_t pl) {
@@ -2520,20 +2529,36 @@ template <typename T> cudaError_t prepare_plane_kernels(const Fields<T> &f) {
     return e;
 }
 
+// The pencil kernel for the x length: the power-of-two form (FP32 only) or the generic one.
+template <typename T> bool pencil_p2(const Fields<T> &f) { return sizeof(T) == 4 && p2_length(f.px.L); }
+template <typename T, int NV> cudaError_t prepare_pencil(const Fields<T> &f, size_t pe) {
+    if constexpr (sizeof(T) == 4)
+        if (pencil_p2(f)) return set_smem(k_pencil<T, NV, true>, pe);
+    return set_smem(k_pencil<T, NV, false>, pe);
+}
+template <typename T, int NV> void pencil_go(const Fields<T> &f, unsigned grid, size_t sm, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4)
+        if (pencil_p2(f)) {
+            k_pencil<T, NV, true><<<grid, kThreadsPencil, sm, s>>>(f);
+            return;
+        }
+    k_pencil<T, NV, false><<<grid, kThreadsPencil, sm, s>>>(f);
+}
+
 template <typename T> cudaError_t prepare_kernels(const Fields<T> &f) {
     const size_t pe = pencil_smem_bytes(f);
     cudaError_t e = prepare_plane_kernels(f);
     if (e == cudaSuccess) e = set_smem(k_ypencil<T>, f.nyc > 1 ? ypencil_smem_bytes(f) : 0);
     if (e != cudaSuccess) return e;
     switch (f.nv) {
-        case 1: return set_smem(k_pencil<T, 1>, pe);
-        case 2: return set_smem(k_pencil<T, 2>, pe);
-        case 3: return set_smem(k_pencil<T, 3>, pe);
-        case 4: return set_smem(k_pencil<T, 4>, pe);
-        case 5: return set_smem(k_pencil<T, 5>, pe);
-        case 6: return set_smem(k_pencil<T, 6>, pe);
-        case 7: return set_smem(k_pencil<T, 7>, pe);
-        case 8: return set_smem(k_pencil<T, 8>, pe);
+        case 1: return prepare_pencil<T, 1>(f, pe);
+        case 2: return prepare_pencil<T, 2>(f, pe);
+        case 3: return prepare_pencil<T, 3>(f, pe);
+        case 4: return prepare_pencil<T, 4>(f, pe);
+        case 5: return prepare_pencil<T, 5>(f, pe);
+        case 6: return prepare_pencil<T, 6>(f, pe);
+        case 7: return prepare_pencil<T, 7>(f, pe);
+        case 8: return prepare_pencil<T, 8>(f, pe);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -2637,14 +2662,14 @@ template <typename T> cudaError_t launch_pencil(const Fields<T> &f, cudaStream_t
     const size_t sm = pencil_smem_bytes(f);
     const unsigned grid = f.tiles_main + f.tiles_nyq;
     switch (f.nv) {
-        case 1: k_pencil<T, 1><<<grid, kThreadsPencil, sm, s>>>(f); break;
-        case 2: k_pencil<T, 2><<<grid, kThreadsPencil, sm, s>>>(f); break;
-        case 3: k_pencil<T, 3><<<grid, kThreadsPencil, sm, s>>>(f); break;
-        case 4: k_pencil<T, 4><<<grid, kThreadsPencil, sm, s>>>(f); break;
-        case 5: k_pencil<T, 5><<<grid, kThreadsPencil, sm, s>>>(f); break;
-        case 6: k_pencil<T, 6><<<grid, kThreadsPencil, sm, s>>>(f); break;
-        case 7: k_pencil<T, 7><<<grid, kThreadsPencil, sm, s>>>(f); break;
-        case 8: k_pencil<T, 8><<<grid, kThreadsPencil, sm, s>>>(f); break;
+        case 1: pencil_go<T, 1>(f, grid, sm, s); break;
+        case 2: pencil_go<T, 2>(f, grid, sm, s); break;
+        case 3: pencil_go<T, 3>(f, grid, sm, s); break;
+        case 4: pencil_go<T, 4>(f, grid, sm, s); break;
+        case 5: pencil_go<T, 5>(f, grid, sm, s); break;
+        case 6: pencil_go<T, 6>(f, grid, sm, s); break;
+        case 7: pencil_go<T, 7>(f, grid, sm, s); break;
+        case 8: pencil_go<T, 8>(f, grid, sm, s); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
