@@ -943,6 +943,60 @@ k_pencil(Fields<T> f) {
     constexpr int rowlen = (NV + 1) * NV;
     const T ks0 = (T)f.ks[0], ks1 = (T)f.ks[1], ks2 = (T)f.ks[2], inv_dk = (T)f.inv_dk;
     const T hs = f.half ? (T)0.5 : (T)0;
+    if constexpr (P2) {
+        // kx and -kx (on the half grid kx and -kx of the shifted frequencies) have the same
+        // |k|: one thread contracts both points (xx, its mirror xp) with one interpolation of
+        // the table. Even Nx: xx = 0 .. Nx/2 on the integer grid (0 and Nx/2 are their own
+        // mirrors), xx = 0 .. Nx/2 - 1 on the half grid.
+        const int nxh = f.half ? Nx / 2 : Nx / 2 + 1;
+        for (int idx = threadIdx.x; idx < nxh * W; idx += blockDim.x) {
+            const int xx = fdiv(idx, f.dW), c = idx - xx * W;
+            if (c >= ncol) continue;
+            const int xp = f.half ? Nx - 1 - xx : (Nx - xx) & (Nx - 1);
+            const bool two = xp != xx;
+            const int yy = nyq ? y0 + c : y;
+            const int kz = nyq ? Kz : kz0 + c;
+            const T kx = ks0 * ((T)signed_index(xx, Nx) + hs);
+            const T ky = ks1 * ((T)signed_index(yy, Ny) + hs);
+            const T kzv = ks2 * ((T)kz + hs);
+            const T xk = sqrt(kx * kx + ky * ky + kzv * kzv) * inv_dk;
+            int j = (int)floor(xk);
+            if (j > f.nk - 2) j = f.nk - 2;
+            T w = xk - (T)j;
+            w = w < (T)0 ? (T)0 : (w > (T)1 ? (T)1 : w);
+            const T *A0 = f.table + (long long)j * rowlen;
+            const T *A1 = A0 + rowlen;
+            C D[NV], E[NV];
+#pragma unroll
+            for (int a = 0; a < NV; ++a) {
+                D[a] = buf[(a * W + c) * pp + xx];
+                E[a] = two ? buf[(a * W + c) * pp + xp] : cmk((T)0, (T)0);
+            }
+            const C Psi = psi_on ? psi[xx * xstride + col_base + c] : cmk((T)0, (T)0);
+            const C Psp = psi_on && two ? psi[xp * xstride + col_base + c] : cmk((T)0, (T)0);
+#pragma unroll
+            for (int g = 0; g < NV; ++g) {
+                T ar = (T)0, ai = (T)0, br = (T)0, bi = (T)0;
+#pragma unroll
+                for (int a = 0; a < NV; ++a) {
+                    const T coef = __ldg(A0 + a * NV + g) * ((T)1 - w) + __ldg(A1 + a * NV + g) * w;
+                    ar += coef * D[a].x;
+                    ai += coef * D[a].y;
+                    br += coef * E[a].x;
+                    bi += coef * E[a].y;
+                }
+                if (psi_on) {
+                    const T coef = __ldg(A0 + NV * NV + g) * ((T)1 - w) + __ldg(A1 + NV * NV + g) * w;
+                    ar += coef * Psi.x;
+                    ai += coef * Psi.y;
+                    br += coef * Psp.x;
+                    bi += coef * Psp.y;
+                }
+                buf[(g * W + c) * pp + xx] = cmk(ar, ai);
+                if (two) buf[(g * W + c) * pp + xp] = cmk(br, bi);
+            }
+        }
+    } else
     for (int idx = threadIdx.x; idx < npts; idx += blockDim.x) {
         const int xx = fdiv(idx, f.dW), c = idx - xx * W;
         if (c >= ncol) continue;
@@ -1134,15 +1188,15 @@ __device__ __forceinline__ void inv_elements(const Fields<T> &f, const InvArgs<T
 
 // Gram row of the new residual, <R, R_i> for each stored residual i, over the block's rows:
 // R from the row buffer, R_i streamed from the ring, one history value at a time (one
-// accumulator in registers, kGramInFlight loads in flight per thread, issued before the
-// shared-memory reads of R so that only the loads occupy registers). The warp sums go to
-// red[(i + 1) * nw + warp].
-constexpr int kGramInFlight = 8;
+// accumulator in registers, G = 16 (FP32) or 8 (FP64) loads in flight per thread, issued
+// before the shared-memory reads of R so that only the loads occupy registers). The warp
+// sums go to red[(i + 1) * nw + warp].
 template <typename T>
 __device__ __forceinline__ void gram_row(const Fields<T> &f, const InvArgs<T> &A,
                                          const typename Cx<T>::type *buf, int y0, int nyb, double *red) {
     typedef typename Cx<T>::type C;
     typedef typename Vec2<T>::type V2;
+    constexpr int G = sizeof(T) == 4 ? 16 : 8;
     const int Kz = f.Kz, pitch = f.pitch;
     const int n = nyb * Kz;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -1151,17 +1205,19 @@ __device__ __forceinline__ void gram_row(const Fields<T> &f, const InvArgs<T> &A
         const T *q = f.R + A.hoff[h];
         GramAcc<T> acc;
         acc.zero();
+        // whole batches of G elements per thread, then the rest one at a time; summed in
+        // element order
         int e = threadIdx.x;
-        for (; e + (kGramInFlight - 1) * nthr < n; e += kGramInFlight * nthr) {
-            V2 qv[kGramInFlight];
+        for (; e + (G - 1) * nthr < n; e += G * nthr) {
+            V2 qv[G];
 #pragma unroll
-            for (int u = 0; u < kGramInFlight; ++u) {
+            for (int u = 0; u < G; ++u) {
                 const int ei = e + u * nthr;
                 const int y = fdiv(ei, f.dKz), m = ei - y * Kz;
                 qv[u] = ld2(q + (long long)(y0 + y) * f.Nz + 2 * m);
             }
 #pragma unroll
-            for (int u = 0; u < kGramInFlight; ++u) {
+            for (int u = 0; u < G; ++u) {
                 const int ei = e + u * nthr;
                 const int y = fdiv(ei, f.dKz), m = ei - y * Kz;
                 const C rv = buf[y * pitch + m];
