@@ -943,16 +943,17 @@ k_pencil(Fields<T> f) {
     constexpr int rowlen = (NV + 1) * NV;
     const T ks0 = (T)f.ks[0], ks1 = (T)f.ks[1], ks2 = (T)f.ks[2], inv_dk = (T)f.inv_dk;
     const T hs = f.half ? (T)0.5 : (T)0;
-    if constexpr (P2) {
+    if (P2 || (Nx & 1) == 0) {
         // kx and -kx (on the half grid kx and -kx of the shifted frequencies) have the same
         // |k|: one thread contracts both points (xx, its mirror xp) with one interpolation of
-        // the table. Even Nx: xx = 0 .. Nx/2 on the integer grid (0 and Nx/2 are their own
-        // mirrors), xx = 0 .. Nx/2 - 1 on the half grid.
+        // the table. Even Nx (always so for the power-of-two form): xx = 0 .. Nx/2 on the
+        // integer grid (0 and Nx/2 are their own mirrors), xx = 0 .. Nx/2 - 1 on the half
+        // grid. Odd Nx takes the per-point loop below.
         const int nxh = f.half ? Nx / 2 : Nx / 2 + 1;
         for (int idx = threadIdx.x; idx < nxh * W; idx += blockDim.x) {
             const int xx = fdiv(idx, f.dW), c = idx - xx * W;
             if (c >= ncol) continue;
-            const int xp = f.half ? Nx - 1 - xx : (Nx - xx) & (Nx - 1);
+            const int xp = f.half ? Nx - 1 - xx : (xx == 0 ? 0 : Nx - xx);
             const bool two = xp != xx;
             const int yy = nyq ? y0 + c : y;
             const int kz = nyq ? Kz : kz0 + c;
