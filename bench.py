@@ -475,7 +475,7 @@ def run_ours(args):
     kd = kern[dom]
     per_launch_s = avg_ms[dom] / 1e3
     total_ms = sum(share_ms.values())
-    # algorithmic bytes of the survey's model (s bytes per real, per site-point and
+    # algorithmic bytes of the iteration's byte model (s bytes per real, per site-point and
     # iteration): closure read 2s, two-pass transform 4s, residual and Gram (M + 2)s, update
     # (2M + 1)s, in all (3M + 9)s; split by kernel as plane_fwd = update + closure + plane
     # write (2M + 4)s, pencil 2s, plane_inv = plane read + residual (M + 3)s, and 2s for each
@@ -537,7 +537,7 @@ def run_ours(args):
             fma = dict(error="%s: %s" % (type(exc).__name__, exc))
     alu = None
     if fma and "fp64_tflops" in fma and args.precision == 64:
-        # the survey's arithmetic model per site-point and iteration: the R2C + C2R pair
+        # the arithmetic model per site-point and iteration: the R2C + C2R pair
         # 5 log2(N^3), closure ~20, contraction 2 n_v, MDIIS ~6M
         flops = 5.0 * np.log2(float(G)) + 20.0 + 2.0 * nv + 6.0 * w["mdiis_nvec"]
         ach = flops * sgi / 1e12
